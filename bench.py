@@ -1,0 +1,314 @@
+"""Benchmark: block-sparse GEMM GFLOP/s and seconds per LNV step on the 4096-atom Si SZP cell.
+
+A step is one Li-Nunes-Vanderbilt step (cq_lnv_step): a full evaluation (7 block products,
+traces, gradients) plus two trial evaluations (5 products each), the line search, the update
+and any electron-number corrections -- every product of the step on FP64 FMAs.  Inputs:
+diamond Si, 8x8x8 conventional cells (4096 atoms, a = 10.26 bohr, seeded 0.1 bohr jitter),
+9 orbitals per atom (36,864 orbitals), S and H from the two-centre model cut at 14 bohr,
+L on a 16-bohr pattern started by Palser-Manolopoulos after Hotelling inversion of S.
+Patterns, task lists, the inverse and the start are built before the timed region.
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank solves its own replica
+of the cell ("replicas only": the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = {"workload": "Si diamond 4096 atoms SZP (9 orb/atom, 36864 orbitals)",
+            "ncell": 8, "a_bohr": 10.26, "sigma_bohr": 0.1, "seed": 2, "r_S": 14.0,
+            "r_L": 16.0, "r_X": 30.0, "r_U": 44.0, "n_electrons": 16384}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cq", choices=["cq", "reference"])
+    ap.add_argument("--ncell", type=int, default=8, help="cells per edge (8 = 4096 atoms)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hotelling-steps", type=int, default=12)
+    return ap.parse_args()
+
+
+def make_inputs(ncell):
+    from paper_2205_08941_gb300 import inputs as I
+    cell = I.diamond_cell(ncell, a=WORKLOAD["a_bohr"], sigma=WORKLOAD["sigma_bohr"],
+                          seed=WORKLOAD["seed"], norb=9)
+    S, H = I.overlap_hamiltonian(cell, I.silicon_model(WORKLOAD["r_S"]))
+    return cell, S, H
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------- oracle sample
+
+def oracle_sample(cell, Spb, Hpb, stride=64, reps=1):
+    """The CPU oracle, as it stands, on a bounded sample of the same workload: the products
+    of one LNV trial evaluation (X = LS, Y = LH in full; U = SX, R1 = UY, R3 = UX on every
+    `stride`-th atom row).  Returns (GFLOP/s, seconds, flops, threads, description)."""
+    import oracle as O
+    from paper_2205_08941_gb300 import inputs as I
+    rS, rL = WORKLOAD["r_S"], WORKLOAD["r_L"]
+    pS, pL = O.Pattern.of_cell(cell, rS), O.Pattern.of_cell(cell, rL)
+    pX, pU = O.Pattern.of_cell(cell, rL + rS), O.Pattern.of_cell(cell, 2 * rS + rL)
+    S, H = O.scatter(pS, Spb), O.scatter(pS, Hpb)
+    L = O.scatter(pL, I.random_blocks(cell, rL, 77)) * 0.01
+    rows = np.arange(0, cell.n_atoms, stride, dtype=np.int32)
+    flops = (O.triplets(pL, pS, pX)[1] * 2 + O.triplets(pS, pX, pU, rows)[1]
+             + 2 * O.triplets(pU, pX, pL, rows)[1])
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        X = O.bsmm(1.0, pL, L, pS, S, 0.0, pX)
+        Y = O.bsmm(1.0, pL, L, pS, H, 0.0, pX)
+        U = O.bsmm(1.0, pS, S, pX, X, 0.0, pU, rows=rows)
+        O.bsmm(1.0, pU, U, pX, Y, 0.0, pL, rows=rows)
+        O.bsmm(1.0, pU, U, pX, X, 0.0, pL, rows=rows)
+        times.append(time.perf_counter() - t0)
+    desc = (f"oracle products of one LNV trial evaluation: X=LS, Y=LH full, U=SX, R1=UY, "
+            f"R3=UX on {rows.shape[0]} of {cell.n_atoms} output atom rows "
+            f"({flops / 1e9:.1f} GFLOP)")
+    return flops / min(times) / 1e9, times, flops, O.num_threads(), desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cell, Spb, Hpb = make_inputs(args.ncell)
+    sample = None
+    vals, secs = [], []
+    for k in range(args.warmup + args.steps):
+        g, t, f, cores, desc = oracle_sample(cell, Spb, Hpb)
+        if k >= args.warmup:
+            vals.append(g)
+            secs.append(t[0])
+        sample = (cores, desc)
+    v = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": "block-sparse GEMM GFLOP/s (useful FP64 flops)",
+            "value": v, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, parallelism="cpu oracle"),
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": sample[0],
+                             "kind": "oracle", "sample": sample[1]},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------- CUDA path
+
+def run_cq(args, rank, world, local_rank):
+    import torch
+
+    from paper_2205_08941_gb300 import build as B
+    B.build()
+    from paper_2205_08941_gb300 import cq
+
+    dev = local_rank
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    cell, Spb, Hpb = make_inputs(args.ncell)
+    ctx = cq.Context(dev)
+    t = lambda a, dt: torch.tensor(a, dtype=dt, device=f"cuda:{dev}")
+    pos, nb = t(cell.pos, torch.float64), t(cell.nb, torch.int32)
+    rS, rL = WORKLOAD["r_S"], WORKLOAD["r_L"]
+    pS = ctx.pattern(pos, cell.box, nb, rS)
+    pL = ctx.pattern(pos, cell.box, nb, rL)
+
+    def up(p, pb):
+        return ctx.scatter(p, t(pb.i, torch.int32), t(pb.j, torch.int32),
+                           t(pb.off, torch.int64), t(pb.values, torch.float64))
+
+    S, H = up(pS, Spb), up(pS, Hpb)
+    T = ctx.zeros(pL)
+    ctx.hotelling_init(pS, S, pL, T)
+    resid = []
+    for _ in range(args.hotelling_steps):
+        resid.append(ctx.hotelling_step(pS, S, pL, T))
+    n_e = 4.0 * cell.n_atoms
+    L = ctx.zeros(pL)
+    ctx.pm_guess(pS, S, H, pL, T, pL, L, n_e / 2.0)
+    del T
+    lnv = ctx.lnv(pS, S, H, pL, L, n_e)
+    peak_fp64 = ctx.peak_fp64()
+
+    for _ in range(args.warmup):
+        lnv.step()
+    ctx.set_timing(True)
+    ctx.kernel_stats()  # reset
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev)
+    barrier()
+    launches0 = cq.kernel_launches()
+    clocks.start()
+    e0.record(stream)
+    reps = [lnv.step() for _ in range(args.steps)]
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = cq.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        tt = torch.tensor([ms], device=f"cuda:{dev}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    n_launch, kern_ms, kern_flops = ctx.kernel_stats()
+    ctx.set_timing(False)
+    flops = sum(r["flops"] for r in reps)
+    value = world * flops / (ms * 1e-3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the public API: each step copies the iterate L in from pinned
+        # host memory, runs cq_lnv_step, and reads L and the step's scalars back
+        L_host = torch.empty(L.shape, dtype=torch.float64, pin_memory=True)
+        L_host.copy_(L)
+        torch.cuda.synchronize()
+        k2 = max(1, min(args.steps, 2))
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e2.record(stream)
+        fl2 = 0.0
+        for _ in range(k2):
+            L.copy_(L_host, non_blocking=True)
+            r = lnv.step()
+            L_host.copy_(L, non_blocking=True)
+            fl2 += r["flops"]
+        e3.record(stream)
+        barrier()
+        ms2 = e2.elapsed_time(e3)
+        e2e = {"value": world * fl2 / (ms2 * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int(L.numel() * 8),
+               "d2h_bytes_per_step": int(L.numel() * 8 + 96),
+               "ms_per_step": ms2 / k2}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g, times, f, cores, desc = oracle_sample(cell, Spb, Hpb)
+        cpu = {"value": g, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": desc, "seconds": min(times)}
+
+    if rank == 0:
+        achieved = kern_flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
+        line = {
+            "metric": "block-sparse GEMM GFLOP/s (useful FP64 flops) & s per LNV step, "
+                      "4096-atom Si SZP, FP64",
+            "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "s_per_lnv_step": ms / args.steps / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": dict(WORKLOAD, n_atoms=cell.n_atoms, parallelism=f"replicas x{world}",
+                           l2="inputs larger than L2 (U, Z 6.9 GB each)",
+                           hotelling_resid=resid[-1] if resid else None),
+            "roofline": {"bound": "alu", "kernel": "k_bsmm_f64_uniform",
+                         "achieved": achieved, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
+                         "frac": (achieved / (peak_fp64 / 1e12)) if achieved else None,
+                         "traffic": None, "peak_source": "in-library FP64 FMA probe",
+                         "launches": n_launch, "kernel_ms": kern_ms,
+                         "kernel_share": kern_ms / ms if ms > 0 else None},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": int(launches),
+            "lnv": [{k: r[k] for k in ("energy", "n_elec", "gnorm", "alpha", "n_corr",
+                                       "n_products")} for r in reps],
+        }
+        print(json.dumps(line), flush=True)
+    lnv.close()
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_cq(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

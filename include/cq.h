@@ -1,0 +1,225 @@
+/*
+ * cq.h -- C ABI of the GB300 block-sparse linear-scaling solver library (libcq.so).
+ *
+ * The paper (Bowler, Miyazaki, Nakata, Truflandier, "The CONQUEST code: large scale and
+ * linear scaling DFT") states the method in words: a linear-scaling ground-state solver
+ * built on "sparse matrix storage and operations to ensure locality" (Background), driven
+ * by "linear scaling optimisation of the density matrix" with a "linear scaling inversion of
+ * the overlap matrix" (Development Priorities), whose first GPU kernel is the sparse matrix
+ * multiplication (Meeting the Exascale Challenges).  The calls below expose exactly that hot
+ * path: range-cutoff patterns, the atom-blocked product kept on C's pattern, traces, the
+ * Hotelling inversion step T <- 2T - TST, the Li-Nunes-Vanderbilt (LNV) density-matrix step
+ * with K = 3LSL - 2LSLSL, its Palser-Manolopoulos start and McWeeny purification.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Units: bohr, hartree.  Matrices are Gamma-point, atom-blocked: block (i, j) is an
+ *  nb[i] x nb[j] row-major FP64 array.  A pattern P_R holds every ordered pair (i, j) whose
+ *  minimum-image distance in the orthorhombic box is below R (i == j always included), so
+ *  every pattern is symmetric.  Its blocks are ordered by atom row i, then column j
+ *  ascending; block b starts at val_off[b] doubles into the value array, and every block
+ *  starts on a 16-byte boundary (its size is padded to an even number of doubles; padding
+ *  values are unspecified).  n_values is the length of a value array on the pattern.
+ *
+ *  Memory: every `const double*` / `double*` value array and every `*_dev` argument is
+ *  caller-owned device memory on the context's device, contiguous, never freed or kept by
+ *  the library past the call.  Host pointers are marked `_host`.  Opaque objects
+ *  (cq_ctx, cq_pattern, cq_lnv) are owned by the library and released by their destroy
+ *  call.  Scratch (task lists, intermediate products) belongs to the context or the LNV
+ *  object; nothing returned needs to be freed by the caller.
+ *
+ *  Streams: all device work is enqueued on the stream given to cq_ctx_create, in order.
+ *  Calls returning host scalars synchronise that stream.
+ *
+ *  Errors: every call returns a cq_status and never aborts or traps; cq_last_error gives
+ *  the context's last message.  Asynchronous CUDA failures surface as CQ_ERR_CUDA at the
+ *  next synchronising call.
+ */
+#ifndef CQ_H
+#define CQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CQ_OK = 0,
+    CQ_ERR_INVALID = 1,       /* bad argument (null pointer, size, range, precision)      */
+    CQ_ERR_PATTERN = 2,       /* patterns of different atoms/basis, or block not in pattern */
+    CQ_ERR_NOMEM = 3,         /* device allocation failed (or the context's limit reached) */
+    CQ_ERR_CUDA = 4,          /* a CUDA runtime call or kernel failed                     */
+    CQ_ERR_NUMERIC = 5,       /* NaN or Inf in a scalar result                            */
+    CQ_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out                       */
+    CQ_ERR_NOT_CONVERGED = 7  /* an iteration hit its limit                               */
+} cq_status;
+
+typedef enum {
+    CQ_FP64 = 0,          /* block products on FP64 FMAs                                   */
+    CQ_SPLIT_BF16X3 = 1   /* products as 3-term split-BF16 on tensor cores, FP32 accumulate */
+} cq_precision;
+
+typedef struct cq_ctx cq_ctx;
+typedef struct cq_pattern cq_pattern;
+typedef struct cq_lnv cq_lnv;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on `device`, enqueuing on `cuda_stream` (a cudaStream_t, borrowed, may
+ * be NULL for the legacy default stream).  *out receives the context. */
+cq_status cq_ctx_create(int device, void *cuda_stream, cq_ctx **out);
+void cq_ctx_destroy(cq_ctx *ctx);
+/* Last error message of the context (never NULL; "" when none). */
+const char *cq_last_error(const cq_ctx *ctx);
+/* Synchronise the context's stream and report any pending asynchronous error. */
+cq_status cq_ctx_sync(cq_ctx *ctx);
+/* Cap the context's own device allocations at `bytes` (0 = no cap); an allocation beyond it
+ * fails with CQ_ERR_NOMEM, as a real out-of-memory would.  Used to test that path. */
+cq_status cq_ctx_set_mem_limit(cq_ctx *ctx, int64_t bytes);
+/* Bytes of device scratch the context currently holds. */
+int64_t cq_ctx_mem_used(const cq_ctx *ctx);
+/* Turn on (1) or off (0) CUDA-event timing of every block-product kernel launch on the
+ * context's stream (for roofline reporting; off by default). */
+cq_status cq_ctx_set_timing(cq_ctx *ctx, int on);
+/* Totals since the last call (then reset): product kernel launches, their summed device
+ * time in ms and their useful flops.  Synchronises. */
+cq_status cq_ctx_kernel_stats(cq_ctx *ctx, int64_t *launches_host, double *ms_host,
+                              double *flops_host);
+/* Measure the device's FP64 FMA throughput (flop/s, an FMA counted as 2) with a register-
+ * resident chain of independent FMAs filling every SM: the FP64 roofline denominator. */
+cq_status cq_peak_fp64(cq_ctx *ctx, double *flops_per_s_host);
+/* Number of CUDA kernels this library has launched in the process. */
+int64_t cq_kernel_launches(void);
+
+/* ---------------------------------------------------------------- patterns */
+
+/*
+ * Build P_range = {(i, j) : d_min(i, j) < range} over n_atoms atoms (Background: locality
+ * through range-cutoff sparse storage).  pos_dev: n_atoms x 3 FP64 positions; box_host:
+ * the three box lengths; nb_dev: orbitals per atom (1..16).  The squared distance is
+ * evaluated in FP64 as ((dx*dx + dy*dy) + dz*dz) with d = (x_j - x_i) - box*rint((x_j -
+ * x_i)/box), without FMA contraction.  The pattern keeps its own copy of the geometry.
+ */
+cq_status cq_pattern_build(cq_ctx *ctx, int32_t n_atoms, const double *pos_dev,
+                           const double *box_host, const int32_t *nb_dev, double range,
+                           cq_pattern **out);
+/* Sizes of a pattern: number of blocks and length of a value array. */
+cq_status cq_pattern_info(const cq_pattern *p, int64_t *n_blocks, int64_t *n_values);
+/* Copy the pattern's index arrays into caller buffers (any may be NULL): row_ptr
+ * (n_atoms + 1, int64), col (n_blocks, int32), val_off (n_blocks, int64, in doubles),
+ * transpose (n_blocks, int64: index of block (j, i)). */
+cq_status cq_pattern_export(cq_ctx *ctx, const cq_pattern *p, int64_t *row_ptr_dev,
+                            int32_t *col_dev, int64_t *val_off_dev, int64_t *transpose_dev);
+void cq_pattern_destroy(cq_pattern *p);
+
+/*
+ * Fill a value array on p from a coordinate list of n_pairs blocks: pair b is block
+ * (pair_i[b], pair_j[b]) with nb[i]*nb[j] row-major values at pair_values + pair_off[b].
+ * Blocks not listed are zero.  A listed block outside p gives CQ_ERR_PATTERN (detected on
+ * the device, reported by this call, which synchronises).
+ */
+cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
+                             const int32_t *pair_i_dev, const int32_t *pair_j_dev,
+                             const int64_t *pair_off_dev, const double *pair_values_dev,
+                             double *out);
+
+/* ---------------------------------------------------------------- products and traces */
+
+/*
+ * C <- beta*C + alpha*mask_{P_C}(A.B): for every block (i, j) of P_C,
+ * C_ij = beta*C_ij + alpha * sum_k A_ik B_kj over the k with (i, k) in P_A and (k, j) in
+ * P_B (the sparse matrix multiplication of the paper's Background and Exascale sections).
+ * With beta == 0 the old C is not read.  The (i, k, j) task list of each (P_A, P_B, P_C)
+ * triple is built on the device on first use and cached in the context.  C must not alias
+ * A or B.  prec selects FP64 FMAs or the split-BF16 tensor-core product.
+ */
+cq_status cq_bsmm(cq_ctx *ctx, double alpha, const cq_pattern *pA, const double *A,
+                  const cq_pattern *pB, const double *B, double beta,
+                  const cq_pattern *pC, double *C, cq_precision prec);
+
+/* Number of (i, k, j) triplets of mask_{P_C}(A.B) and the useful flops
+ * sum 2 n_i n_k n_j (padding never counted).  Builds the task list if needed. */
+cq_status cq_bsmm_work(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
+                       const cq_pattern *pC, int64_t *triplets_host, double *flops_host);
+
+/* Tr(A.B) = sum_{(i,j) in P_A} sum_{a,b} A_ij[a,b] B_ji[b,a] (absent B blocks count zero);
+ * deterministic FP64 two-level reduction.  Synchronises. */
+cq_status cq_trace_prod(cq_ctx *ctx, const cq_pattern *pA, const double *A,
+                        const cq_pattern *pB, const double *B, double *out_host);
+
+/* Frobenius inner product <A, B> over the blocks of p.  Synchronises. */
+cq_status cq_dot(cq_ctx *ctx, const cq_pattern *p, const double *A, const double *B,
+                 double *out_host);
+
+/* ---------------------------------------------------------------- overlap inversion */
+
+/* T_0 = I / sigma on P_T, sigma = max_a sum_b |S_ab| (largest absolute scalar row sum of S,
+ * which bounds its spectrum, so the Hotelling iteration converges).  Synchronises. */
+cq_status cq_hotelling_init(cq_ctx *ctx, const cq_pattern *pS, const double *S,
+                            const cq_pattern *pT, double *T);
+
+/*
+ * One Hotelling step for T ~ S^-1 (Development Priorities: linear-scaling inversion of the
+ * overlap): V = S.T on P_{rS+rT} (the whole product), resid = ||V - I||_F for the incoming
+ * T, then T <- 2T - mask_{P_T}(T.V).  T is updated in place.  Synchronises.
+ */
+cq_status cq_hotelling_step(cq_ctx *ctx, const cq_pattern *pS, const double *S,
+                            const cq_pattern *pT, double *T, double *resid_host);
+
+/* ---------------------------------------------------------------- density matrix */
+
+/*
+ * Palser-Manolopoulos start for the density-matrix optimisation (non-orthogonal form):
+ * L = mask_L[(lambda/N)(mu T - T H T) + (n_occ/N) T], N = number of orbitals,
+ * mu = Tr(TH)/N, lambda = min(n_occ/(h_max - mu), (N - n_occ)/(mu - h_min)) with h_min,
+ * h_max the Gershgorin bounds of TH.  T ~ S^-1 on P_T; H on P_S.  Synchronises.
+ */
+cq_status cq_pm_guess(cq_ctx *ctx, const cq_pattern *pS, const double *S, const double *H,
+                      const cq_pattern *pT, const double *T, const cq_pattern *pL,
+                      double *L, double n_occ);
+
+/* One McWeeny purification step L <- mask_L(3LSL - 2LSLSL), every intermediate kept on its
+ * full range (r_L + r_S, 2 r_S + r_L, 2 r_L) so the masked result is exact. */
+cq_status cq_mcweeny_step(cq_ctx *ctx, const cq_pattern *pS, const double *S,
+                          const cq_pattern *pL, double *L);
+
+/* Per-step record of an LNV step. */
+typedef struct {
+    double energy;      /* E = 2 Tr(K H), hartree                                   */
+    double n_elec;      /* N = 2 Tr(K S)                                            */
+    double mu;          /* chemical potential <G_E,G_N>/<G_N,G_N> at the new L       */
+    double gnorm;       /* RMS of G = G_E - mu G_N over the values of P_L            */
+    double alpha;       /* accepted step length                                     */
+    int32_t restart;    /* 1 if the search direction was reset to -G                */
+    int32_t fallback;   /* 1 if the cubic had no positive minimum (alpha = 2 alpha2) */
+    int32_t n_corr;     /* electron-number corrections applied after the step        */
+    int32_t n_products; /* block products the step ran                              */
+    double flops;       /* useful flops of those products (sum 2 n_i n_k n_j)         */
+} cq_lnv_report;
+
+/*
+ * Li-Nunes-Vanderbilt minimisation (Development Priorities: linear-scaling optimisation of
+ * the density matrix) of E = 2 Tr(K H) at N = 2 Tr(K S) = n_electrons, K = 3LSL - 2LSLSL,
+ * over L on P_L.  S and H share pattern pS; L (in/out, on pL) is the start (e.g. from
+ * cq_pm_guess) and always holds the current iterate.  Create evaluates E, N and the
+ * gradients and applies electron-number corrections; each step then does a Polak-Ribiere
+ * direction projected orthogonal to G_N, an exact cubic line search of E - mu N from two
+ * trial points, the update and at most five corrections while |N - N_e| > 1e-10 N_e.
+ * The object keeps pointers to S, H and L: they must outlive it.  Synchronises.
+ */
+cq_status cq_lnv_create(cq_ctx *ctx, const cq_pattern *pS, const double *S, const double *H,
+                        const cq_pattern *pL, double *L, double n_electrons,
+                        cq_precision prec, cq_lnv **out);
+cq_status cq_lnv_step(cq_lnv *lnv, cq_lnv_report *report_host);
+/* Current E, N, mu and RMS gradient (as after the last evaluation). */
+cq_status cq_lnv_state(const cq_lnv *lnv, cq_lnv_report *report_host);
+/* Useful flops of one LNV step's products (full evaluation + two trial points). */
+cq_status cq_lnv_step_flops(cq_lnv *lnv, double *flops_host);
+void cq_lnv_destroy(cq_lnv *lnv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CQ_H */

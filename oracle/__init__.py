@@ -64,7 +64,9 @@ def _lib():
         lib.orc_bsmm.restype = ctypes.c_int
         lib.orc_triplet_count.argtypes = [ctypes.c_int, _I32P, _I64P, _I32P, _I64P, _I32P,
                                           _I64P, _I32P, ctypes.POINTER(ctypes.c_int64),
-                                          ctypes.POINTER(ctypes.c_double)]
+                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
+                                          ctypes.c_int]
+        lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_trace_prod.argtypes = [ctypes.c_int, _I32P] + pat + [_F64P] + pat + [_F64P]
         lib.orc_trace_prod.restype = ctypes.c_double
         lib.orc_dot.argtypes = [ctypes.c_int64, _F64P, _F64P]
@@ -180,13 +182,22 @@ def bsmm(alpha, pA: Pattern, A, pB: Pattern, B, beta, pC: Pattern, C=None, rows=
     return C
 
 
-def triplets(pA: Pattern, pB: Pattern, pC: Pattern):
-    """(number of (i,k,j) triplets, useful flops = sum 2 n_i n_k n_j) of mask_{P_C}(A B)."""
+def triplets(pA: Pattern, pB: Pattern, pC: Pattern, rows=None):
+    """(number of (i,k,j) triplets, useful flops = sum 2 n_i n_k n_j) of mask_{P_C}(A B),
+    over all rows or the listed output rows."""
     t = ctypes.c_int64()
     f = ctypes.c_double()
+    r = None if rows is None else np.ascontiguousarray(rows, dtype=np.int32)
     _lib().orc_triplet_count(pA.n, pA.nb, pA.rp, pA.col, pB.rp, pB.col, pC.rp, pC.col,
-                             ctypes.byref(t), ctypes.byref(f))
+                             ctypes.byref(t), ctypes.byref(f),
+                             None if r is None else r.ctypes.data,
+                             0 if r is None else int(r.shape[0]))
     return int(t.value), float(f.value)
+
+
+def num_threads() -> int:
+    """Threads the oracle's OpenMP loops use."""
+    return int(_lib().orc_num_threads())
 
 
 def trace_prod(pA: Pattern, A, pB: Pattern, B) -> float:

@@ -24,9 +24,24 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define ORC_MAXB 32 /* largest orbital count per atom the oracle accepts */
 
-/* ---- pattern: P_R = {(i,j) : d_min(i,j)^2 < R^2}, minimum image in an orthorhombic box ---- */
+/* Threads the oracle's parallel loops use. */
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---- pattern: P_R = {(i,j) : d_min(i,j)^2 < R^2} plus every (i,i), minimum image in an
+ *      orthorhombic box ---- */
 
 /* Minimum-image squared distance, evaluated as ((dx*dx + dy*dy) + dz*dz) with
  * d_c = (x_j - x_i) - box_c * rint((x_j - x_i) / box_c).  Compiled without FMA contraction. */
@@ -50,7 +65,7 @@ void orc_pattern_count(int n, const double *pos, const double *box, double range
     for (int i = 0; i < n; ++i) {
         int64_t c = 0;
         for (int j = 0; j < n; ++j)
-            if (min_image_d2(pos, box, i, j) < r2)
+            if (j == i || min_image_d2(pos, box, i, j) < r2)
                 ++c;
         row_count[i] = c;
     }
@@ -65,7 +80,7 @@ void orc_pattern_fill(int n, const double *pos, const double *box, double range,
     for (int i = 0; i < n; ++i) {
         int64_t w = row_ptr[i];
         for (int j = 0; j < n; ++j)
-            if (min_image_d2(pos, box, i, j) < r2)
+            if (j == i || min_image_d2(pos, box, i, j) < r2)
                 col[w++] = j;
     }
 }
@@ -138,17 +153,20 @@ int orc_bsmm(int n, const int32_t *nb,
     return 0;
 }
 
-/* Number of (i, k, j) triplets of the masked product and their useful flop count. */
+/* Number of (i, k, j) triplets of the masked product and their useful flop count, over
+ * every row (rows == NULL) or the n_rows listed rows. */
 void orc_triplet_count(int n, const int32_t *nb,
                        const int64_t *a_rp, const int32_t *a_col,
                        const int64_t *b_rp, const int32_t *b_col,
                        const int64_t *c_rp, const int32_t *c_col,
-                       int64_t *triplets, double *flops)
+                       int64_t *triplets, double *flops, const int32_t *rows, int n_rows)
 {
     int64_t t_all = 0;
     double f_all = 0.0;
+    const int count = rows ? n_rows : n;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : t_all, f_all)
-    for (int i = 0; i < n; ++i)
+    for (int t = 0; t < count; ++t) {
+        const int i = rows ? rows[t] : t;
         for (int64_t c = c_rp[i]; c < c_rp[i + 1]; ++c) {
             const int j = c_col[c];
             for (int64_t a = a_rp[i]; a < a_rp[i + 1]; ++a) {
@@ -159,6 +177,7 @@ void orc_triplet_count(int n, const int32_t *nb,
                 }
             }
         }
+    }
     *triplets = t_all;
     *flops = f_all;
 }

@@ -1,0 +1,304 @@
+"""Thin ctypes binding of libcq.so: the C-ABI calls under the same names, plus small
+wrappers that marshal torch CUDA tensors (device memory, streams) into them.
+
+No arithmetic of the method happens here: every step runs in the library's CUDA kernels.
+If libcq.so is missing the import fails loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcq.so")
+
+CQ_OK = 0
+CQ_FP64 = 0
+CQ_SPLIT_BF16X3 = 1
+STATUS = {0: "CQ_OK", 1: "CQ_ERR_INVALID", 2: "CQ_ERR_PATTERN", 3: "CQ_ERR_NOMEM",
+          4: "CQ_ERR_CUDA", 5: "CQ_ERR_NUMERIC", 6: "CQ_ERR_TIMEOUT", 7: "CQ_ERR_NOT_CONVERGED"}
+
+
+class CQError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class LnvReport(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("n_elec", ctypes.c_double),
+                ("mu", ctypes.c_double), ("gnorm", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("restart", ctypes.c_int32),
+                ("fallback", ctypes.c_int32), ("n_corr", ctypes.c_int32),
+                ("n_products", ctypes.c_int32), ("flops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_d = ctypes.c_double
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_st = ctypes.c_int
+
+# name -> (restype, argtypes): one line per entry point declared in include/cq.h
+SIGNATURES = {
+    "cq_ctx_create": (_st, [ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "cq_ctx_destroy": (None, [_vp]),
+    "cq_last_error": (ctypes.c_char_p, [_vp]),
+    "cq_ctx_sync": (_st, [_vp]),
+    "cq_ctx_set_mem_limit": (_st, [_vp, _i64]),
+    "cq_ctx_mem_used": (_i64, [_vp]),
+    "cq_pattern_build": (_st, [_vp, _i32, _vp, ctypes.POINTER(_d), _vp, _d,
+                               ctypes.POINTER(_vp)]),
+    "cq_pattern_info": (_st, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "cq_pattern_export": (_st, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "cq_pattern_destroy": (None, [_vp]),
+    "cq_pattern_scatter": (_st, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
+    "cq_bsmm": (_st, [_vp, _d, _vp, _vp, _vp, _vp, _d, _vp, _vp, ctypes.c_int]),
+    "cq_bsmm_work": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(_d)]),
+    "cq_trace_prod": (_st, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d)]),
+    "cq_dot": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(_d)]),
+    "cq_hotelling_init": (_st, [_vp, _vp, _vp, _vp, _vp]),
+    "cq_hotelling_step": (_st, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d)]),
+    "cq_pm_guess": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d]),
+    "cq_mcweeny_step": (_st, [_vp, _vp, _vp, _vp, _vp]),
+    "cq_lnv_create": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _d, ctypes.c_int,
+                            ctypes.POINTER(_vp)]),
+    "cq_lnv_step": (_st, [_vp, ctypes.POINTER(LnvReport)]),
+    "cq_lnv_state": (_st, [_vp, ctypes.POINTER(LnvReport)]),
+    "cq_lnv_step_flops": (_st, [_vp, ctypes.POINTER(_d)]),
+    "cq_lnv_destroy": (None, [_vp]),
+    "cq_kernel_launches": (_i64, []),
+    "cq_ctx_set_timing": (_st, [_vp, ctypes.c_int]),
+    "cq_ctx_kernel_stats": (_st, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_d),
+                                  ctypes.POINTER(_d)]),
+    "cq_peak_fp64": (_st, [_vp, ctypes.POINTER(_d)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libcq.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} missing: run python -m paper_2205_08941_gb300.build")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = h
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A libcq context bound to a device and a torch CUDA stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.device = device
+        self.stream = stream or torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        self._check(lib().cq_ctx_create(device, ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(h)), ctx=None)
+        self.h = h
+
+    def _check(self, st, ctx="self"):
+        if st != CQ_OK:
+            msg = lib().cq_last_error(self.h if ctx == "self" else None)
+            raise CQError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cq_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        self._check(lib().cq_ctx_sync(self.h))
+
+    def set_mem_limit(self, nbytes: int):
+        self._check(lib().cq_ctx_set_mem_limit(self.h, int(nbytes)))
+
+    def mem_used(self) -> int:
+        return int(lib().cq_ctx_mem_used(self.h))
+
+    def set_timing(self, on: bool):
+        self._check(lib().cq_ctx_set_timing(self.h, 1 if on else 0))
+
+    def kernel_stats(self):
+        n, ms, fl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        self._check(lib().cq_ctx_kernel_stats(self.h, ctypes.byref(n), ctypes.byref(ms),
+                                              ctypes.byref(fl)))
+        return int(n.value), float(ms.value), float(fl.value)
+
+    def peak_fp64(self) -> float:
+        out = ctypes.c_double()
+        self._check(lib().cq_peak_fp64(self.h, ctypes.byref(out)))
+        return float(out.value)
+
+    # ------------------------------------------------------------ patterns
+    def pattern(self, pos: torch.Tensor, box, nb: torch.Tensor, rng: float) -> "Pattern":
+        return Pattern(self, pos, box, nb, rng)
+
+    def zeros(self, p: "Pattern") -> torch.Tensor:
+        return torch.zeros(p.n_values, dtype=torch.float64, device=f"cuda:{self.device}")
+
+    def empty(self, p: "Pattern") -> torch.Tensor:
+        return torch.empty(p.n_values, dtype=torch.float64, device=f"cuda:{self.device}")
+
+    def scatter(self, p: "Pattern", i, j, off, values, out=None) -> torch.Tensor:
+        out = self.empty(p) if out is None else out
+        self._check(lib().cq_pattern_scatter(self.h, p.h, int(i.shape[0]), _ptr(i), _ptr(j),
+                                             _ptr(off), _ptr(values), _ptr(out)))
+        return out
+
+    # ------------------------------------------------------------ products and traces
+    def bsmm(self, alpha, pA, A, pB, B, beta, pC, C, prec=CQ_FP64):
+        self._check(lib().cq_bsmm(self.h, float(alpha), pA.h, _ptr(A), pB.h, _ptr(B),
+                                  float(beta), pC.h, _ptr(C), int(prec)))
+        return C
+
+    def bsmm_work(self, pA, pB, pC):
+        t, f = ctypes.c_int64(), ctypes.c_double()
+        self._check(lib().cq_bsmm_work(self.h, pA.h, pB.h, pC.h, ctypes.byref(t),
+                                       ctypes.byref(f)))
+        return int(t.value), float(f.value)
+
+    def trace_prod(self, pA, A, pB, B) -> float:
+        out = ctypes.c_double()
+        self._check(lib().cq_trace_prod(self.h, pA.h, _ptr(A), pB.h, _ptr(B),
+                                        ctypes.byref(out)))
+        return float(out.value)
+
+    def dot(self, p, A, B) -> float:
+        out = ctypes.c_double()
+        self._check(lib().cq_dot(self.h, p.h, _ptr(A), _ptr(B), ctypes.byref(out)))
+        return float(out.value)
+
+    # ------------------------------------------------------------ drivers
+    def hotelling_init(self, pS, S, pT, T):
+        self._check(lib().cq_hotelling_init(self.h, pS.h, _ptr(S), pT.h, _ptr(T)))
+        return T
+
+    def hotelling_step(self, pS, S, pT, T) -> float:
+        r = ctypes.c_double()
+        self._check(lib().cq_hotelling_step(self.h, pS.h, _ptr(S), pT.h, _ptr(T),
+                                            ctypes.byref(r)))
+        return float(r.value)
+
+    def pm_guess(self, pS, S, H, pT, T, pL, L, n_occ: float):
+        self._check(lib().cq_pm_guess(self.h, pS.h, _ptr(S), _ptr(H), pT.h, _ptr(T), pL.h,
+                                      _ptr(L), float(n_occ)))
+        return L
+
+    def mcweeny_step(self, pS, S, pL, L):
+        self._check(lib().cq_mcweeny_step(self.h, pS.h, _ptr(S), pL.h, _ptr(L)))
+        return L
+
+    def lnv(self, pS, S, H, pL, L, n_electrons, prec=CQ_FP64) -> "Lnv":
+        return Lnv(self, pS, S, H, pL, L, n_electrons, prec)
+
+
+class Pattern:
+    """Range-cutoff pattern built on the device by cq_pattern_build."""
+
+    def __init__(self, ctx: Context, pos: torch.Tensor, box, nb: torch.Tensor, rng: float):
+        self.ctx = ctx
+        self._pos, self._nb = pos, nb
+        box_arr = (ctypes.c_double * 3)(*[float(b) for b in box])
+        h = ctypes.c_void_p()
+        ctx._check(lib().cq_pattern_build(ctx.h, int(pos.shape[0]), _ptr(pos), box_arr,
+                                          _ptr(nb), float(rng), ctypes.byref(h)))
+        self.h = h
+        self.range = float(rng)
+        nbk, nv = ctypes.c_int64(), ctypes.c_int64()
+        lib().cq_pattern_info(h, ctypes.byref(nbk), ctypes.byref(nv))
+        self.n_blocks, self.n_values = int(nbk.value), int(nv.value)
+        self.n_atoms = int(pos.shape[0])
+
+    def export(self):
+        """(row_ptr, col, val_off, transpose) as CUDA tensors."""
+        dev = self._pos.device
+        rp = torch.empty(self.n_atoms + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(max(self.n_blocks, 1), dtype=torch.int32, device=dev)
+        off = torch.empty(max(self.n_blocks, 1), dtype=torch.int64, device=dev)
+        tr = torch.empty(max(self.n_blocks, 1), dtype=torch.int64, device=dev)
+        self.ctx._check(lib().cq_pattern_export(self.ctx.h, self.h, _ptr(rp), _ptr(col),
+                                                _ptr(off), _ptr(tr)))
+        self.ctx.sync()
+        n = self.n_blocks
+        return rp, col[:n], off[:n], tr[:n]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cq_pattern_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Lnv:
+    """LNV minimisation state (cq_lnv_create / cq_lnv_step)."""
+
+    def __init__(self, ctx, pS, S, H, pL, L, n_electrons, prec=CQ_FP64):
+        self.ctx = ctx
+        self._keep = (pS, S, H, pL, L)
+        h = ctypes.c_void_p()
+        ctx._check(lib().cq_lnv_create(ctx.h, pS.h, _ptr(S), _ptr(H), pL.h, _ptr(L),
+                                       float(n_electrons), int(prec), ctypes.byref(h)))
+        self.h = h
+
+    def step(self) -> dict:
+        rep = LnvReport()
+        self.ctx._check(lib().cq_lnv_step(self.h, ctypes.byref(rep)))
+        return rep.as_dict()
+
+    def state(self) -> dict:
+        rep = LnvReport()
+        self.ctx._check(lib().cq_lnv_state(self.h, ctypes.byref(rep)))
+        return rep.as_dict()
+
+    def step_flops(self) -> float:
+        f = ctypes.c_double()
+        self.ctx._check(lib().cq_lnv_step_flops(self.h, ctypes.byref(f)))
+        return float(f.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cq_lnv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kernel_launches() -> int:
+    return int(lib().cq_kernel_launches())

@@ -1,0 +1,218 @@
+// FP64 block-sparse product C <- beta C + alpha mask_{P_C}(A.B) on FP64 FMAs.
+//
+// Work decomposition: an "item" is one scalar row r of one C block c; Q adjacent lanes of
+// a warp share an item and split its task segment (lane q takes tasks q, q+Q, ...), each
+// keeping the item's NB partial sums in registers; the Q partials are then combined by a
+// fixed xor-shuffle tree, so every C row has exactly one writer (no atomics) and the
+// summation order is fixed (deterministic).  Q is picked from the mean segment length so
+// that long segments (k-sums of ~800 blocks) keep all 32 lanes busy and short ones (~13)
+// do not idle lanes.  The B block of a task is read by the NB lanes that own the rows of
+// the same C block, so it is served from L1 after the first touch.
+#include "cq_internal.cuh"
+
+namespace {
+
+template <int NB, int Q>
+__global__ void __launch_bounds__(256)
+k_bsmm_f64_uniform(int64_t n_items, const int64_t *__restrict__ seg,
+                   const int2 *__restrict__ tasks, const double *__restrict__ A,
+                   const double *__restrict__ B, double *__restrict__ C, int stride,
+                   double alpha, double beta)
+{
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t item = gt / Q;
+    const int q = (int)(gt % Q);
+    const bool active = item < n_items;
+    const int64_t c = active ? item / NB : 0;
+    const int r = (int)(item % NB);
+    double acc[NB];
+#pragma unroll
+    for (int x = 0; x < NB; ++x) acc[x] = 0.0;
+    if (active) {
+        const int64_t t1 = seg[c + 1];
+        for (int64_t t = seg[c] + q; t < t1; t += Q) {
+            const int2 tk = __ldg(&tasks[t]);
+            const double *a = A + (int64_t)tk.x * stride + r * NB;
+            const double *b = B + (int64_t)tk.y * stride;
+            double av[NB];
+#pragma unroll
+            for (int m = 0; m < NB; ++m) av[m] = __ldg(a + m);
+#pragma unroll
+            for (int m = 0; m < NB; ++m)
+#pragma unroll
+                for (int x = 0; x < NB; ++x) acc[x] = fma(av[m], __ldg(b + m * NB + x), acc[x]);
+        }
+    }
+#pragma unroll
+    for (int o = Q >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int x = 0; x < NB; ++x) acc[x] += __shfl_xor_sync(0xffffffffu, acc[x], o);
+    if (active && q == 0) {
+        double *cp = C + c * stride + r * NB;
+        if (beta == 0.0) {
+#pragma unroll
+            for (int x = 0; x < NB; ++x) cp[x] = alpha * acc[x];
+        } else {
+#pragma unroll
+            for (int x = 0; x < NB; ++x) cp[x] = beta * cp[x] + alpha * acc[x];
+        }
+    }
+}
+
+// Mixed orbital counts (1..16 per atom): item -> C block by binary search over the prefix
+// of block row counts; block offsets from the patterns' val_off.
+template <int Q>
+__global__ void __launch_bounds__(256)
+k_bsmm_f64_generic(int64_t n_items, int64_t n_c, const int64_t *__restrict__ rowitem,
+                   const int64_t *__restrict__ seg, const int2 *__restrict__ tasks,
+                   const int32_t *__restrict__ nb, const int32_t *__restrict__ c_row,
+                   const int32_t *__restrict__ c_col, const int32_t *__restrict__ a_col,
+                   const int64_t *__restrict__ a_off, const int64_t *__restrict__ b_off,
+                   const int64_t *__restrict__ c_off, const double *__restrict__ A,
+                   const double *__restrict__ B, double *__restrict__ C, double alpha,
+                   double beta)
+{
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t item = gt / Q;
+    const int q = (int)(gt % Q);
+    const bool active = item < n_items;
+    int64_t c = 0;
+    int r = 0, nj = 0, ni = 0;
+    if (active) {
+        int64_t lo = 0, hi = n_c;  // largest c with rowitem[c] <= item
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (rowitem[mid] <= item)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        c = lo;
+        r = (int)(item - rowitem[c]);
+        ni = nb[c_row[c]];
+        nj = nb[c_col[c]];
+    }
+    double acc[CQ_MAX_NB];
+#pragma unroll
+    for (int x = 0; x < CQ_MAX_NB; ++x) acc[x] = 0.0;
+    if (active) {
+        const int64_t t1 = seg[c + 1];
+        for (int64_t t = seg[c] + q; t < t1; t += Q) {
+            const int2 tk = __ldg(&tasks[t]);
+            const int nk = nb[a_col[tk.x]];
+            const double *a = A + a_off[tk.x] + (int64_t)r * nk;
+            const double *b = B + b_off[tk.y];
+            for (int m = 0; m < nk; ++m) {
+                const double av = __ldg(a + m);
+#pragma unroll
+                for (int x = 0; x < CQ_MAX_NB; ++x)
+                    if (x < nj) acc[x] = fma(av, __ldg(b + m * nj + x), acc[x]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = Q >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int x = 0; x < CQ_MAX_NB; ++x) acc[x] += __shfl_xor_sync(0xffffffffu, acc[x], o);
+    if (active && q == 0 && r < ni) {
+        double *cp = C + c_off[c] + (int64_t)r * nj;
+#pragma unroll
+        for (int x = 0; x < CQ_MAX_NB; ++x)
+            if (x < nj) cp[x] = (beta == 0.0) ? alpha * acc[x] : beta * cp[x] + alpha * acc[x];
+    }
+}
+
+int pick_q(const TaskList *tl)
+{
+    const double avg = tl->n_c ? (double)tl->n_tasks / (double)tl->n_c : 0.0;
+    int q = 1;
+    while (q < 32 && q * 8 <= avg) q <<= 1;
+    return q;
+}
+
+template <int NB>
+void launch_uniform(int q, unsigned grid, cudaStream_t s, int64_t n_items, const TaskList *tl,
+                    const double *A, const double *B, double *C, int stride, double alpha,
+                    double beta)
+{
+    const int64_t *seg = tl->seg.as<int64_t>();
+    const int2 *tk = tl->tasks.as<int2>();
+#define CQ_LAUNCH(QQ)                                                                      \
+    k_bsmm_f64_uniform<NB, QQ><<<grid, 256, 0, s>>>(n_items, seg, tk, A, B, C, stride, alpha, \
+                                                    beta)
+    switch (q) {
+    case 1: CQ_LAUNCH(1); break;
+    case 2: CQ_LAUNCH(2); break;
+    case 4: CQ_LAUNCH(4); break;
+    case 8: CQ_LAUNCH(8); break;
+    case 16: CQ_LAUNCH(16); break;
+    default: CQ_LAUNCH(32); break;
+    }
+#undef CQ_LAUNCH
+}
+
+}  // namespace
+
+cq_status cq_bsmm_f64(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pattern *pA,
+                      const double *A, const cq_pattern *pB, const double *B, double beta,
+                      const cq_pattern *pC, double *C)
+{
+    if (tl->n_c == 0) return CQ_OK;
+    const int q = pick_q(tl);
+    const int nbu = pC->geo->uniform_nb;
+    cudaStream_t s = ctx->stream;
+    if (nbu == 9 || nbu == 4) {
+        const int64_t n_items = tl->n_c * nbu;
+        const int64_t threads = n_items * q;
+        const unsigned grid = (unsigned)((threads + 255) / 256);
+        cq_timing_begin(ctx, tl->flops);
+        if (nbu == 9)
+            launch_uniform<9>(q, grid, s, n_items, tl, A, B, C, pC->uniform, alpha, beta);
+        else
+            launch_uniform<4>(q, grid, s, n_items, tl, A, B, C, pC->uniform, alpha, beta);
+        cq_timing_end(ctx);
+        cq_count_launch();
+        return cq_check_cuda(ctx, cudaGetLastError(), "bsmm_f64");
+    }
+    // general basis: rowitem prefix exists for non-uniform patterns; build one on the fly
+    // for uniform bases other than 4 and 9
+    const int64_t *rowitem = tl->c_rowitem.ptr ? tl->c_rowitem.as<int64_t>() : nullptr;
+    DevBuf tmp;
+    int64_t n_items = 0;
+    if (!rowitem) {
+        std::vector<int64_t> h(tl->n_c + 1);
+        for (int64_t c = 0; c <= tl->n_c; ++c) h[c] = c * nbu;
+        cq_status st = cq_alloc(ctx, tmp, sizeof(int64_t) * h.size());
+        if (st != CQ_OK) return st;
+        cudaMemcpyAsync(tmp.ptr, h.data(), sizeof(int64_t) * h.size(), cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+        rowitem = tmp.as<int64_t>();
+        n_items = tl->n_c * nbu;
+    } else {
+        cudaMemcpyAsync(&n_items, rowitem + tl->n_c, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+    }
+    const unsigned grid = (unsigned)((n_items * q + 255) / 256);
+    const int32_t *nb = pC->geo->nb.as<int32_t>();
+    cq_timing_begin(ctx, tl->flops);
+#define CQ_GEN(QQ)                                                                            \
+    k_bsmm_f64_generic<QQ><<<grid, 256, 0, s>>>(                                              \
+        n_items, tl->n_c, rowitem, tl->seg.as<int64_t>(), tl->tasks.as<int2>(), nb,           \
+        pC->row.as<int32_t>(), pC->col.as<int32_t>(), pA->col.as<int32_t>(),                  \
+        pA->val_off.as<int64_t>(), pB->val_off.as<int64_t>(), pC->val_off.as<int64_t>(), A, B, \
+        C, alpha, beta)
+    switch (q) {
+    case 1: CQ_GEN(1); break;
+    case 2: CQ_GEN(2); break;
+    case 4: CQ_GEN(4); break;
+    case 8: CQ_GEN(8); break;
+    case 16: CQ_GEN(16); break;
+    default: CQ_GEN(32); break;
+    }
+#undef CQ_GEN
+    cq_timing_end(ctx);
+    cq_count_launch();
+    cq_status st = cq_check_cuda(ctx, cudaGetLastError(), "bsmm_f64_generic");
+    if (tmp.ptr) cudaStreamSynchronize(s);
+    return st;
+}
