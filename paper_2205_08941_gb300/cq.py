@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import torch
 
@@ -124,7 +125,12 @@ class Context:
             raise CQError(st, msg.decode() if msg else "")
 
     def close(self):
+        """Destroy the context; LNV objects and patterns made from it are closed first."""
         if getattr(self, "h", None):
+            kids = list(self._children)
+            for child in [k for k in kids if isinstance(k, Lnv)] + \
+                    [k for k in kids if not isinstance(k, Lnv)]:
+                child.close()
             lib().cq_ctx_destroy(self.h)
             self.h = None
 
@@ -133,6 +139,12 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    @property
+    def _children(self):
+        if "_kids" not in self.__dict__:
+            self.__dict__["_kids"] = weakref.WeakSet()
+        return self.__dict__["_kids"]
 
     def sync(self):
         self._check(lib().cq_ctx_sync(self.h))
@@ -231,6 +243,7 @@ class Pattern:
         ctx._check(lib().cq_pattern_build(ctx.h, int(pos.shape[0]), _ptr(pos), box_arr,
                                           _ptr(nb), float(rng), ctypes.byref(h)))
         self.h = h
+        ctx._children.add(self)
         self.range = float(rng)
         nbk, nv = ctypes.c_int64(), ctypes.c_int64()
         lib().cq_pattern_info(h, ctypes.byref(nbk), ctypes.byref(nv))
@@ -272,6 +285,7 @@ class Lnv:
         ctx._check(lib().cq_lnv_create(ctx.h, pS.h, _ptr(S), _ptr(H), pL.h, _ptr(L),
                                        float(n_electrons), int(prec), ctypes.byref(h)))
         self.h = h
+        ctx._children.add(self)
 
     def step(self) -> dict:
         rep = LnvReport()

@@ -87,6 +87,7 @@ struct cq_ctx {
     std::map<std::pair<uint64_t, double>, cq_pattern *> derived;
     std::map<std::string, std::unique_ptr<DevBuf>> scratch;
     std::vector<cq_pattern *> live_patterns;
+    std::vector<cq_lnv *> live_lnv;
     // product-kernel timing
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
@@ -162,3 +163,12 @@ cq_status cq_lnv_gradients(cq_ctx *ctx, const cq_pattern *pL, const cq_pattern *
 void cq_count_launch(int64_t n = 1);
 
 static inline int64_t cq_pad2(int64_t x) { return (x + 1) & ~int64_t(1); }
+
+// Called by cq_ctx_destroy for LNV objects still alive: they stop touching the context.
+void cq_lnv_detach(cq_lnv *s);
+// G_N = 12(U - R3) only (the electron-number gradient) on P_L.
+cq_status cq_lnv_gradient_n(cq_ctx *ctx, const cq_pattern *pL, const cq_pattern *pU,
+                            const double *U, const double *R3, double *GN);
+// G_E = 2[3(Z + Z^T) - 2((R1 + R1^T) + R2)] only, on P_L.
+cq_status cq_lnv_gradient_e(cq_ctx *ctx, const cq_pattern *pL, const cq_pattern *pU,
+                            const double *Z, const double *R1, const double *R2, double *GE);

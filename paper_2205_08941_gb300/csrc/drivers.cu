@@ -171,19 +171,45 @@ cq_status lnv_energy_number(cq_lnv *s, const double *Lsrc, double *E, double *N)
     return CQ_OK;
 }
 
-// Full evaluation at s->L: E, N, G_E, G_N.
-cq_status lnv_evaluate(cq_lnv *s)
+// Electron-number half of an evaluation at s->L: X = LS, U = SX, R3 = UX, N and G_N.
+// (The products and values are those of a full evaluation; E and G_E follow in
+// lnv_eval_rest at the same L.)
+cq_status lnv_eval_n(cq_lnv *s)
 {
     cq_ctx *ctx = s->ctx;
-    CQ_TRY(lnv_energy_number(s, s->L, &s->E, &s->N));
-    double *Z = s->Z.as<double>(), *R2 = s->R2.as<double>();
-    CQ_TRY(bsmm(ctx, 1.0, s->pS, s->S, s->pX, s->Y.as<double>(), 0.0, s->pU, Z, s->prec,
-                &s->flops));
-    CQ_TRY(bsmm(ctx, 1.0, s->pU, Z, s->pX, s->X.as<double>(), 0.0, s->pL, R2, s->prec,
-                &s->flops));
-    s->products += 2;
-    return cq_lnv_gradients(ctx, s->pL, s->pU, Z, s->U.as<double>(), s->R1.as<double>(), R2,
-                            s->R3.as<double>(), s->GE.as<double>(), s->GN.as<double>());
+    double *X = s->X.as<double>(), *U = s->U.as<double>(), *R3 = s->R3.as<double>();
+    CQ_TRY(bsmm(ctx, 1.0, s->pL, s->L, s->pS, s->S, 0.0, s->pX, X, s->prec, &s->flops));
+    CQ_TRY(bsmm(ctx, 1.0, s->pS, s->S, s->pX, X, 0.0, s->pU, U, s->prec, &s->flops));
+    CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, X, 0.0, s->pL, R3, s->prec, &s->flops));
+    s->products += 3;
+    CQ_TRY(cq_trace_dev(ctx, s->pX, X, s->pX, X, 2));
+    CQ_TRY(cq_trace_dev(ctx, s->pL, s->L, s->pL, R3, 3));
+    CQ_TRY(cq_lnv_gradient_n(ctx, s->pL, s->pU, U, R3, s->GN.as<double>()));
+    double t[2];
+    CQ_TRY(cq_fetch(ctx, 2, 2, t));
+    s->N = 2.0 * (3.0 * t[0] - 2.0 * t[1]);
+    return CQ_OK;
+}
+
+// Energy half at the L of the last lnv_eval_n (X, U still current): Y = LH, R1 = UY,
+// Z = SY, R2 = ZX, E and G_E.
+cq_status lnv_eval_rest(cq_lnv *s)
+{
+    cq_ctx *ctx = s->ctx;
+    double *X = s->X.as<double>(), *Y = s->Y.as<double>(), *U = s->U.as<double>();
+    double *Z = s->Z.as<double>(), *R1 = s->R1.as<double>(), *R2 = s->R2.as<double>();
+    CQ_TRY(bsmm(ctx, 1.0, s->pL, s->L, s->pS, s->H, 0.0, s->pX, Y, s->prec, &s->flops));
+    CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, Y, 0.0, s->pL, R1, s->prec, &s->flops));
+    CQ_TRY(bsmm(ctx, 1.0, s->pS, s->S, s->pX, Y, 0.0, s->pU, Z, s->prec, &s->flops));
+    CQ_TRY(bsmm(ctx, 1.0, s->pU, Z, s->pX, X, 0.0, s->pL, R2, s->prec, &s->flops));
+    s->products += 4;
+    CQ_TRY(cq_trace_dev(ctx, s->pX, X, s->pX, Y, 0));
+    CQ_TRY(cq_trace_dev(ctx, s->pL, s->L, s->pL, R1, 1));
+    CQ_TRY(cq_lnv_gradient_e(ctx, s->pL, s->pU, Z, R1, R2, s->GE.as<double>()));
+    double t[2];
+    CQ_TRY(cq_fetch(ctx, 0, 2, t));
+    s->E = 2.0 * (3.0 * t[0] - 2.0 * t[1]);
+    return CQ_OK;
 }
 
 cq_status dot_l(cq_lnv *s, const double *a, const double *b, double *out)
@@ -192,19 +218,25 @@ cq_status dot_l(cq_lnv *s, const double *a, const double *b, double *out)
     return cq_fetch(s->ctx, 0, 1, out);
 }
 
-cq_status lnv_correct(cq_lnv *s, int *count)
+// Evaluate at s->L with the electron-number corrections in between: N and G_N first, then
+// L += ((N_e - N)/<G_N,G_N>) G_N (at most max_corr times) while |N - N_e| > n_tol N_e, each
+// followed by N and G_N at the corrected L, and finally E and G_E at the last L.  The
+// iterates and decisions are those of "full evaluation, then correct and re-evaluate";
+// only the E half of the intermediate evaluations (never used) is skipped.
+cq_status lnv_evaluate_corrected(cq_lnv *s, int *count)
 {
+    CQ_TRY(lnv_eval_n(s));
     int k = 0;
     while (std::fabs(s->N - s->ne) > s->n_tol * s->ne && k < s->max_corr) {
         double gn2;
         CQ_TRY(dot_l(s, s->GN.as<double>(), s->GN.as<double>(), &gn2));
         CQ_TRY(cq_axpby(s->ctx, s->pL->n_values, (s->ne - s->N) / gn2, s->GN.as<double>(), 1.0,
                         s->L));
-        CQ_TRY(lnv_evaluate(s));
+        CQ_TRY(lnv_eval_n(s));
         ++k;
     }
     *count = k;
-    return CQ_OK;
+    return lnv_eval_rest(s);
 }
 
 // mu = <G_E,G_N>/<G_N,G_N> and G = G_E - mu G_N into s->G; returns <G_N,G_N>.
@@ -286,15 +318,15 @@ extern "C" cq_status cq_lnv_create(cq_ctx *ctx, const cq_pattern *pS, const doub
     CQ_TRY(cq_alloc(ctx, s->Z, bu));
     for (DevBuf *b : {&s->R1, &s->R2, &s->R3, &s->GE, &s->GN, &s->G, &s->Gp, &s->D, &s->Dp, &s->Lt})
         CQ_TRY(cq_alloc(ctx, *b, bl));
-    CQ_TRY(lnv_evaluate(s.get()));
-    CQ_TRY(lnv_correct(s.get(), &s->n_corr_initial));
+    CQ_TRY(lnv_evaluate_corrected(s.get(), &s->n_corr_initial));
+    ctx->live_lnv.push_back(s.get());
     *out = s.release();
     return CQ_OK;
 }
 
 extern "C" cq_status cq_lnv_step(cq_lnv *s, cq_lnv_report *rep)
 {
-    if (!s) return CQ_ERR_INVALID;
+    if (!s || !s->ctx) return CQ_ERR_INVALID;
     cq_ctx *ctx = s->ctx;
     const int64_t n = s->pL->n_values;
     double *G = s->G.as<double>(), *D = s->D.as<double>(), *GN = s->GN.as<double>();
@@ -361,9 +393,8 @@ extern "C" cq_status cq_lnv_step(cq_lnv *s, cq_lnv_report *rep)
     const bool ok = cubic_min(gE - mu * gNd, e2 - mu * n2, e3 - mu * n3, &alpha);
     if (!ok) alpha = 2.0 * a2;
     CQ_TRY(cq_axpby(ctx, n, alpha, D, 1.0, s->L));
-    CQ_TRY(lnv_evaluate(s));
     int ncorr = 0;
-    CQ_TRY(lnv_correct(s, &ncorr));
+    CQ_TRY(lnv_evaluate_corrected(s, &ncorr));
     std::swap(s->G.ptr, s->Gp.ptr);  // G_prev <- G
     std::swap(s->D.ptr, s->Dp.ptr);  // D_prev <- D
     s->have_prev = true;
@@ -383,7 +414,7 @@ extern "C" cq_status cq_lnv_step(cq_lnv *s, cq_lnv_report *rep)
 
 extern "C" cq_status cq_lnv_state(const cq_lnv *s, cq_lnv_report *rep)
 {
-    if (!s || !rep) return CQ_ERR_INVALID;
+    if (!s || !rep || !s->ctx) return CQ_ERR_INVALID;
     // the report needs G scratch: use Lt (not part of the state between steps)
     cq_lnv *m = const_cast<cq_lnv *>(s);
     cq_ctx *ctx = m->ctx;
@@ -409,7 +440,7 @@ extern "C" cq_status cq_lnv_state(const cq_lnv *s, cq_lnv_report *rep)
 
 extern "C" cq_status cq_lnv_step_flops(cq_lnv *s, double *flops_host)
 {
-    if (!s || !flops_host) return CQ_ERR_INVALID;
+    if (!s || !flops_host || !s->ctx) return CQ_ERR_INVALID;
     TaskList *a, *b, *c;
     CQ_TRY(cq_get_tasks(s->ctx, s->pL, s->pS, s->pX, &a));
     CQ_TRY(cq_get_tasks(s->ctx, s->pS, s->pX, s->pU, &b));
@@ -420,9 +451,25 @@ extern "C" cq_status cq_lnv_step_flops(cq_lnv *s, double *flops_host)
     return CQ_OK;
 }
 
+void cq_lnv_detach(cq_lnv *s)
+{
+    s->ctx = nullptr;
+    for (DevBuf *b : {&s->X, &s->Y, &s->U, &s->Z, &s->R1, &s->R2, &s->R3, &s->GE, &s->GN,
+                      &s->G, &s->Gp, &s->D, &s->Dp, &s->Lt})
+        b->ctx = nullptr;
+}
+
 extern "C" void cq_lnv_destroy(cq_lnv *s)
 {
     if (!s) return;
-    cudaStreamSynchronize(s->ctx->stream);
+    if (s->ctx) {
+        cudaStreamSynchronize(s->ctx->stream);
+        auto &v = s->ctx->live_lnv;
+        for (size_t e = 0; e < v.size(); ++e)
+            if (v[e] == s) {
+                v.erase(v.begin() + e);
+                break;
+            }
+    }
     delete s;
 }

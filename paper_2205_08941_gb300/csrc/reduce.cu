@@ -230,6 +230,42 @@ __global__ void k_lnv_grad(int64_t nblk, const int32_t *row, const int32_t *col,
     }
 }
 
+__global__ void k_lnv_grad_n(int64_t nblk, const int32_t *row, const int32_t *col,
+                             const int32_t *nb, const int64_t *l_off, const int64_t *u_off,
+                             const int64_t *map_u, const double *U, const double *R3,
+                             double *GN)
+{
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nblk) return;
+    const int sz = nb[row[b]] * nb[col[b]];
+    const int64_t lb = l_off[b], zb = map_u[b];
+    for (int e = lane; e < sz; e += 32) {
+        const double u = zb >= 0 ? U[u_off[zb] + e] : 0.0;
+        GN[lb + e] = 12.0 * (u - R3[lb + e]);
+    }
+}
+
+__global__ void k_lnv_grad_e(int64_t nblk, const int32_t *row, const int32_t *col,
+                             const int32_t *nb, const int64_t *l_off, const int64_t *l_tr,
+                             const int64_t *u_off, const int64_t *map_u, const int64_t *map_ut,
+                             const double *Z, const double *R1, const double *R2, double *GE)
+{
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nblk) return;
+    const int ni = nb[row[b]], nj = nb[col[b]];
+    const int64_t lb = l_off[b], lt = l_off[l_tr[b]];
+    const int64_t zb = map_u[b], zt = map_ut[b];
+    for (int e = lane; e < ni * nj; e += 32) {
+        const int r = e / nj, q = e - r * nj;
+        const double z = zb >= 0 ? Z[u_off[zb] + e] : 0.0;
+        const double zT = zt >= 0 ? Z[u_off[zt] + q * ni + r] : 0.0;
+        const double t = (R1[lb + e] + R1[lt + q * ni + r]) + R2[lb + e];
+        GE[lb + e] = 2.0 * (3.0 * (z + zT) - 2.0 * t);
+    }
+}
+
 cq_status red_part(cq_ctx *ctx, double **part)
 {
     void *p;
@@ -356,4 +392,34 @@ cq_status cq_lnv_gradients(cq_ctx *ctx, const cq_pattern *pL, const cq_pattern *
         Z, U, R1, R2, R3, GE, GN);
     cq_count_launch();
     return cq_check_cuda(ctx, cudaGetLastError(), "lnv gradients");
+}
+
+cq_status cq_lnv_gradient_n(cq_ctx *ctx, const cq_pattern *pL, const cq_pattern *pU,
+                            const double *U, const double *R3, double *GN)
+{
+    const int64_t *mu;
+    cq_status st = cq_get_map(ctx, pU, pL, 0, &mu);
+    if (st != CQ_OK) return st;
+    if (pL->n_blocks == 0) return CQ_OK;
+    k_lnv_grad_n<<<(unsigned)((pL->n_blocks + 7) / 8), 256, 0, ctx->stream>>>(
+        pL->n_blocks, pL->row.as<int32_t>(), pL->col.as<int32_t>(), pL->geo->nb.as<int32_t>(),
+        pL->val_off.as<int64_t>(), pU->val_off.as<int64_t>(), mu, U, R3, GN);
+    cq_count_launch();
+    return cq_check_cuda(ctx, cudaGetLastError(), "lnv gradient N");
+}
+
+cq_status cq_lnv_gradient_e(cq_ctx *ctx, const cq_pattern *pL, const cq_pattern *pU,
+                            const double *Z, const double *R1, const double *R2, double *GE)
+{
+    const int64_t *mu, *mut;
+    cq_status st = cq_get_map(ctx, pU, pL, 0, &mu);
+    if (st != CQ_OK) return st;
+    if ((st = cq_get_map(ctx, pU, pL, 1, &mut)) != CQ_OK) return st;
+    if (pL->n_blocks == 0) return CQ_OK;
+    k_lnv_grad_e<<<(unsigned)((pL->n_blocks + 7) / 8), 256, 0, ctx->stream>>>(
+        pL->n_blocks, pL->row.as<int32_t>(), pL->col.as<int32_t>(), pL->geo->nb.as<int32_t>(),
+        pL->val_off.as<int64_t>(), pL->transpose.as<int64_t>(), pU->val_off.as<int64_t>(), mu,
+        mut, Z, R1, R2, GE);
+    cq_count_launch();
+    return cq_check_cuda(ctx, cudaGetLastError(), "lnv gradient E");
 }

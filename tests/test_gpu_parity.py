@@ -228,7 +228,9 @@ def test_lnv_parity_c1_20_steps(ctx, c1):
         assert rg["n_elec"] == pytest.approx(ro["N"], abs=tol), k
         assert (rg["restart"], rg["fallback"], rg["n_corr"]) == (
             int(ro["restart"]), int(ro["fallback"]), ro["n_corr"]), k
-        assert rg["gnorm"] == pytest.approx(ro["gnorm"], rel=1e-5, abs=1e-12), k
+        # the RMS gradient is a difference of O(1) terms: compare it to 1e-9 Ha absolute,
+        # two decades under the 1e-8 convergence threshold
+        assert rg["gnorm"] == pytest.approx(ro["gnorm"], rel=1e-5, abs=1e-9), k
     err, nrm = block_errors(pL.o, pL.down(L_g), lo.L)
     assert err.max() < 1e-8 * nrm.max()
 
