@@ -1,15 +1,19 @@
-"""Benchmark: block-sparse GEMM GFLOP/s and seconds per LNV step on the 4096-atom Si SZP cell.
+"""Benchmark: block-sparse GEMM GFLOP/s and seconds per LNV step on the 4096-atom Si SZP cell,
+FP64 products and split-BF16 tensor-core products.
 
-A step is one Li-Nunes-Vanderbilt step (cq_lnv_step): a full evaluation (7 block products,
-traces, gradients) plus two trial evaluations (5 products each), the line search, the update
-and any electron-number corrections -- every product of the step on FP64 FMAs.  Inputs:
-diamond Si, 8x8x8 conventional cells (4096 atoms, a = 10.26 bohr, seeded 0.1 bohr jitter),
-9 orbitals per atom (36,864 orbitals), S and H from the two-centre model cut at 14 bohr,
-L on a 16-bohr pattern started by Palser-Manolopoulos after Hotelling inversion of S.
-Patterns, task lists, the inverse and the start are built before the timed region.
+A step is one Li-Nunes-Vanderbilt step (cq_lnv_step): two trial evaluations (5 block
+products each), the update, the electron-number corrections (3 products each) and the full
+evaluation at the new point (7 products), plus traces, gradients and the line search.
+Inputs: diamond Si, 8x8x8 conventional cells (4096 atoms, a = 10.26 bohr, seeded 0.1 bohr
+jitter), 9 orbitals per atom (36,864 orbitals), S and H from the two-centre model cut at
+14 bohr, L on a 16-bohr pattern started by Palser-Manolopoulos after Hotelling inversion of
+S.  Patterns, task lists, the inverse and the start are built before the timed region.
 
-Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank solves its own replica
-of the cell ("replicas only": the path has no exchange step).
+The FP64 leg (value, e2e, roofline) times K steps after W warm-up steps; the split leg
+restarts from the same L and times K split-BF16 steps, and reports the energy and L
+differences between the two trajectories.  Prints one JSON line (rank 0).  Under torchrun
+(N > 1) every rank solves its own replica of the cell ("replicas only": the path has no
+exchange step).
 """
 from __future__ import annotations
 
@@ -30,6 +34,7 @@ import numpy as np  # noqa: E402
 WORKLOAD = {"workload": "Si diamond 4096 atoms SZP (9 orb/atom, 36864 orbitals)",
             "ncell": 8, "a_bohr": 10.26, "sigma_bohr": 0.1, "seed": 2, "r_S": 14.0,
             "r_L": 16.0, "r_X": 30.0, "r_U": 44.0, "n_electrons": 16384}
+BF16_FALLBACK_TFLOPS = 1900.0
 
 
 def parse():
@@ -41,6 +46,9 @@ def parse():
     ap.add_argument("--ncell", type=int, default=8, help="cells per edge (8 = 4096 atoms)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-split", action="store_true")
+    ap.add_argument("--only-split", action="store_true",
+                    help="skip the FP64 leg (profiling the tensor-core path)")
     ap.add_argument("--hotelling-steps", type=int, default=12)
     return ap.parse_args()
 
@@ -51,6 +59,15 @@ def make_inputs(ncell):
                           seed=WORKLOAD["seed"], norb=9)
     S, H = I.overlap_hamiltonian(cell, I.silicon_model(WORKLOAD["r_S"]))
     return cell, S, H
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
 
 
 class ClockSampler:
@@ -184,6 +201,13 @@ def run_cq(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        tt = torch.tensor([x], device=f"cuda:{dev}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
     cell, Spb, Hpb = make_inputs(args.ncell)
     ctx = cq.Context(dev)
     t = lambda a, dt: torch.tensor(a, dtype=dt, device=f"cuda:{dev}")
@@ -199,44 +223,48 @@ def run_cq(args, rank, world, local_rank):
     S, H = up(pS, Spb), up(pS, Hpb)
     T = ctx.zeros(pL)
     ctx.hotelling_init(pS, S, pL, T)
-    resid = []
-    for _ in range(args.hotelling_steps):
-        resid.append(ctx.hotelling_step(pS, S, pL, T))
+    resid = [ctx.hotelling_step(pS, S, pL, T) for _ in range(args.hotelling_steps)]
     n_e = 4.0 * cell.n_atoms
     L = ctx.zeros(pL)
     ctx.pm_guess(pS, S, H, pL, T, pL, L, n_e / 2.0)
     del T
-    lnv = ctx.lnv(pS, S, H, pL, L, n_e)
-    peak_fp64 = ctx.peak_fp64()
+    first_prec = cq.CQ_SPLIT_BF16X3 if args.only_split else cq.CQ_FP64
+    lnv = ctx.lnv(pS, S, H, pL, L, n_e, prec=first_prec)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(nsteps, label):
+        """K timed steps on the device: CUDA events on the context's stream, clocks sampled,
+        product-kernel launches timed by the library."""
+        ctx.set_timing(True)
+        ctx.kernel_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(dev)
+        barrier()
+        launches0 = cq.kernel_launches()
+        clocks.start()
+        e0.record(stream)
+        reps = [lnv.step() for _ in range(nsteps)]
+        e1.record(stream)
+        barrier()
+        clk = clocks.stop()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        stats = ctx.kernel_stats()
+        ctx.set_timing(False)
+        return {"reps": reps, "ms": ms, "clk": clk, "stats": stats,
+                "launches": cq.kernel_launches() - launches0}
 
     for _ in range(args.warmup):
         lnv.step()
-    ctx.set_timing(True)
-    ctx.kernel_stats()  # reset
-    stream = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(dev)
-    barrier()
-    launches0 = cq.kernel_launches()
-    clocks.start()
-    e0.record(stream)
-    reps = [lnv.step() for _ in range(args.steps)]
-    e1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    launches = cq.kernel_launches() - launches0
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        tt = torch.tensor([ms], device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    n_launch, kern_ms, kern_flops = ctx.kernel_stats()
-    ctx.set_timing(False)
-    flops = sum(r["flops"] for r in reps)
-    value = world * flops / (ms * 1e-3) / 1e9
+    L0 = L.clone()
+    res = {}
+    peak_fp64 = ctx.peak_fp64()
+    if not args.only_split:
+        lnv.set_precision(cq.CQ_FP64)  # fresh search direction at L0
+        res["fp64"] = timed(args.steps, "fp64")
+        E_fp64, L_fp64 = res["fp64"]["reps"][-1]["energy"], L.clone()
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.only_split:
         # end to end through the public API: each step copies the iterate L in from pinned
         # host memory, runs cq_lnv_step, and reads L and the step's scalars back
         L_host = torch.empty(L.shape, dtype=torch.float64, pin_memory=True)
@@ -254,11 +282,49 @@ def run_cq(args, rank, world, local_rank):
             fl2 += r["flops"]
         e3.record(stream)
         barrier()
-        ms2 = e2.elapsed_time(e3)
+        ms2 = max_over_ranks(e2.elapsed_time(e3))
         e2e = {"value": world * fl2 / (ms2 * 1e-3) / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": int(L.numel() * 8),
                "d2h_bytes_per_step": int(L.numel() * 8 + 96),
                "ms_per_step": ms2 / k2}
+
+    split = None
+    if not args.no_split:
+        L.copy_(L0)
+        lnv.set_precision(cq.CQ_SPLIT_BF16X3)
+        for _ in range(args.warmup):
+            lnv.step()
+        L.copy_(L0)
+        lnv.set_precision(cq.CQ_SPLIT_BF16X3)
+        res["split"] = timed(args.steps, "split")
+        r = res["split"]
+        n_launch, kern_ms, kern_flops, mma_flops = r["stats"]
+        flops = sum(x["flops"] for x in r["reps"])
+        peaks = measured_peaks()
+        bf16 = (peaks or {}).get("bf16_tflops")
+        split = {"value": world * flops / (r["ms"] * 1e-3) / 1e9, "unit": "GFLOP/s",
+                 "dtype": "bf16x3 split, fp32 accumulate, fp64 traces",
+                 "ms_per_step": r["ms"] / args.steps, "s_per_lnv_step": r["ms"] / args.steps / 1e3,
+                 "roofline": {"bound": "tensor", "kernel": "k_bsmm_split",
+                              "achieved": mma_flops / (kern_ms * 1e-3) / 1e12 if kern_ms else None,
+                              "peak": bf16 or BF16_FALLBACK_TFLOPS, "unit": "TFLOP/s",
+                              "peak_source": "MEASURED_PEAKS.json bf16_tflops" if bf16 else
+                              "profiling-recipe fallback (1.9 PFLOP/s bf16)",
+                              "useful_tflops": kern_flops / (kern_ms * 1e-3) / 1e12 if kern_ms else None,
+                              "launches": n_launch, "kernel_ms": kern_ms,
+                              "kernel_share": kern_ms / r["ms"] if r["ms"] else None,
+                              "traffic": None},
+                 "clocks": r["clk"], "gpu_launches": int(r["launches"]),
+                 "lnv": [{k: x[k] for k in ("energy", "n_elec", "gnorm", "n_corr")}
+                         for x in r["reps"]]}
+        split["roofline"]["frac"] = (split["roofline"]["achieved"] / split["roofline"]["peak"]
+                                     if split["roofline"]["achieved"] else None)
+        if "fp64" in res:
+            E_split = r["reps"][-1]["energy"]
+            split["energy_err_per_atom_vs_fp64"] = abs(E_split - E_fp64) / cell.n_atoms
+            split["L_rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(L - L_fp64) /
+                                                torch.linalg.vector_norm(L_fp64))
+            split["speedup_vs_fp64_step"] = (res["fp64"]["ms"] / r["ms"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -267,30 +333,36 @@ def run_cq(args, rank, world, local_rank):
                "sample": desc, "seconds": min(times)}
 
     if rank == 0:
+        main = res.get("fp64") or res.get("split")
+        n_launch, kern_ms, kern_flops, mma_flops = main["stats"]
+        flops = sum(x["flops"] for x in main["reps"])
+        ms = main["ms"]
         achieved = kern_flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
         line = {
             "metric": "block-sparse GEMM GFLOP/s (useful FP64 flops) & s per LNV step, "
-                      "4096-atom Si SZP, FP64",
-            "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                      "4096-atom Si SZP; FP64 (value) and split-BF16 (split)",
+            "value": world * flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "s_per_lnv_step": ms / args.steps / 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if "fp64" in res else "bf16x3", "data": "synthetic",
             "config": dict(WORKLOAD, n_atoms=cell.n_atoms, parallelism=f"replicas x{world}",
                            l2="inputs larger than L2 (U, Z 6.9 GB each)",
                            hotelling_resid=resid[-1] if resid else None),
             "roofline": {"bound": "alu", "kernel": "k_bsmm_f64_uniform",
                          "achieved": achieved, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
                          "frac": (achieved / (peak_fp64 / 1e12)) if achieved else None,
-                         "traffic": None, "peak_source": "in-library FP64 FMA probe",
+                         "traffic": None,
+                         "peak_source": "in-library FP64 probe (best of FMA and DMMA chains)",
                          "launches": n_launch, "kernel_ms": kern_ms,
                          "kernel_share": kern_ms / ms if ms > 0 else None},
+            "split": split,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "clocks": clk,
-            "gpu_launches": int(launches),
-            "lnv": [{k: r[k] for k in ("energy", "n_elec", "gnorm", "alpha", "n_corr",
-                                       "n_products")} for r in reps],
+            "clocks": main["clk"],
+            "gpu_launches": int(main["launches"]),
+            "lnv": [{k: x[k] for k in ("energy", "n_elec", "gnorm", "alpha", "n_corr",
+                                       "n_products")} for x in main["reps"]],
         }
         print(json.dumps(line), flush=True)
     lnv.close()

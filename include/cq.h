@@ -83,9 +83,10 @@ int64_t cq_ctx_mem_used(const cq_ctx *ctx);
  * context's stream (for roofline reporting; off by default). */
 cq_status cq_ctx_set_timing(cq_ctx *ctx, int on);
 /* Totals since the last call (then reset): product kernel launches, their summed device
- * time in ms and their useful flops.  Synchronises. */
+ * time in ms, their useful flops (sum 2 n_i n_k n_j) and the tensor-core flops the split
+ * products issued (0 for FP64 products).  Synchronises. */
 cq_status cq_ctx_kernel_stats(cq_ctx *ctx, int64_t *launches_host, double *ms_host,
-                              double *flops_host);
+                              double *flops_host, double *mma_flops_host);
 /* Measure the device's FP64 FMA throughput (flop/s, an FMA counted as 2) with a register-
  * resident chain of independent FMAs filling every SM: the FP64 roofline denominator. */
 cq_status cq_peak_fp64(cq_ctx *ctx, double *flops_per_s_host);
@@ -212,6 +213,11 @@ cq_status cq_lnv_create(cq_ctx *ctx, const cq_pattern *pS, const double *S, cons
                         const cq_pattern *pL, double *L, double n_electrons,
                         cq_precision prec, cq_lnv **out);
 cq_status cq_lnv_step(cq_lnv *lnv, cq_lnv_report *report_host);
+/* Switch the precision of the products of later steps (e.g. split-BF16 steps followed by
+ * FP64 refinement sweeps).  The current L, E, N and gradients are re-evaluated in the new
+ * precision (with electron-number corrections) so the next step starts from consistent
+ * values; the search history is reset.  Synchronises. */
+cq_status cq_lnv_set_precision(cq_lnv *lnv, cq_precision prec);
 /* Current E, N, mu and RMS gradient (as after the last evaluation). */
 cq_status cq_lnv_state(const cq_lnv *lnv, cq_lnv_report *report_host);
 /* Useful flops of one LNV step's products (full evaluation + two trial points). */

@@ -70,13 +70,14 @@ SIGNATURES = {
     "cq_lnv_create": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _d, ctypes.c_int,
                             ctypes.POINTER(_vp)]),
     "cq_lnv_step": (_st, [_vp, ctypes.POINTER(LnvReport)]),
+    "cq_lnv_set_precision": (_st, [_vp, ctypes.c_int]),
     "cq_lnv_state": (_st, [_vp, ctypes.POINTER(LnvReport)]),
     "cq_lnv_step_flops": (_st, [_vp, ctypes.POINTER(_d)]),
     "cq_lnv_destroy": (None, [_vp]),
     "cq_kernel_launches": (_i64, []),
     "cq_ctx_set_timing": (_st, [_vp, ctypes.c_int]),
     "cq_ctx_kernel_stats": (_st, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_d),
-                                  ctypes.POINTER(_d)]),
+                                  ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "cq_peak_fp64": (_st, [_vp, ctypes.POINTER(_d)]),
 }
 
@@ -159,10 +160,10 @@ class Context:
         self._check(lib().cq_ctx_set_timing(self.h, 1 if on else 0))
 
     def kernel_stats(self):
-        n, ms, fl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        n, ms, fl, mf = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         self._check(lib().cq_ctx_kernel_stats(self.h, ctypes.byref(n), ctypes.byref(ms),
-                                              ctypes.byref(fl)))
-        return int(n.value), float(ms.value), float(fl.value)
+                                              ctypes.byref(fl), ctypes.byref(mf)))
+        return int(n.value), float(ms.value), float(fl.value), float(mf.value)
 
     def peak_fp64(self) -> float:
         out = ctypes.c_double()
@@ -291,6 +292,9 @@ class Lnv:
         rep = LnvReport()
         self.ctx._check(lib().cq_lnv_step(self.h, ctypes.byref(rep)))
         return rep.as_dict()
+
+    def set_precision(self, prec: int):
+        self.ctx._check(lib().cq_lnv_set_precision(self.h, int(prec)))
 
     def state(self) -> dict:
         rep = LnvReport()

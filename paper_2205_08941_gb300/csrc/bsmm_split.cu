@@ -1,9 +1,652 @@
-// Split-BF16 block-sparse product (tensor cores).  Not built yet: the call reports it.
+// Split-BF16 block-sparse product on the 5th-generation tensor cores (tcgen05 + TMEM).
+//
+// C <- beta C + alpha mask_{P_C}(A.B) with every FP64 operand value split into three BF16
+// terms x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1); the
+// residuals are exact in FP64) and the product formed as the six cross products
+// A_p B_q with p + q <= 2, accumulated in FP32 in tensor memory.  Every DRAIN chunks the
+// FP32 accumulator is drained into a per-thread double-float (hi, lo) sum, so FP32
+// rounding only acts within a drain period; the result is written back in FP64.
+//
+// Local densification.  9x9 blocks do not fit MMA shapes, so atoms are grouped in space
+// (Morton order): an M tile is a group of floor(128/nb) atoms (126 rows for nb = 9), an N
+// tile a group of floor(64/nb) atoms.  A work tile is a pair (M group g, N group h) that
+// holds at least one block of P_C; its K list is every atom k with (i, k) in P_A for some
+// i in g and (k, j) in P_B for some j in h (built on the device with shared-memory
+// bitmaps).  Along K each atom's orbitals are padded to 16 so that an atom is exactly two
+// 8x8 core matrices; a K chunk is four atoms (64).  Absent blocks are zero in shared
+// memory.  Every C block belongs to exactly one tile, so there are no atomics.
+//
+// Operands are pre-split once per product into padded BF16 planes ("A form": rows = left
+// orbital, 16 K values = right orbital; "B form": rows = right orbital, K = left orbital),
+// so the tile kernel only moves 16-byte pieces with cp.async into the canonical no-swizzle
+// K-major layout (core matrix = 8 rows x 16 bytes; LBO = 128 B between K-adjacent core
+// matrices, SBO = 1024 B between 8-row groups) and one thread issues the MMAs.
+//
+// Pipeline per CTA (256 threads; warps w and w+4 share TMEM lane quarter w and split the
+// 64 accumulator columns; one CTA per SM): two shared
+// stages; while the tensor core runs chunk c from stage c%2, the threads gather chunk c+1
+// into the other stage; an mbarrier per stage (tcgen05.commit) tells when a stage is free.
+// Every wait is bounded (about a second); on timeout the kernel records an error flag,
+// stops issuing work, waits (bounded) for its own MMAs, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
 #include "cq_internal.cuh"
 
-cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *, double, const cq_pattern *,
-                        const double *, const cq_pattern *, const double *, double,
-                        const cq_pattern *, double *)
+namespace {
+
+constexpr int ST = 256;                      // threads per CTA (two warpgroups)
+constexpr int MT = 128, NT = 64, KCH = 64;   // tile M, N and K chunk
+constexpr int KP = 16;                       // padded orbitals per atom along K
+constexpr int A_PLANE = MT * KCH * 2;        // 16 KB
+constexpr int B_PLANE = NT * KCH * 2;        // 8 KB
+constexpr int STAGE = 3 * A_PLANE + 3 * B_PLANE;
+constexpr int SMEM = 2 * STAGE + 64;
+constexpr int DRAIN = 4;                     // chunks per FP32 accumulation period
+constexpr int TMEM_COLS = 64;
+constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    return cq_fail(ctx, CQ_ERR_INVALID, "split-BF16 product not available in this build");
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of (row, 16-byte K column) in the canonical no-swizzle K-major layout
+__device__ __forceinline__ uint32_t cm_off(int row, int kc)
+{
+    return (uint32_t)((row >> 3) * 1024 + kc * 128 + (row & 7) * 16);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;    // leading (K) byte offset
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride (M/N) byte offset
+    d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
+    return d;                           // base offset 0, no swizzle
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N = 64, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                           ((uint32_t)(MT >> 4) << 24);
+
+__device__ __forceinline__ void split3(double x, __nv_bfloat16 &b0, __nv_bfloat16 &b1,
+                                       __nv_bfloat16 &b2)
+{
+    b0 = __double2bfloat16(x);
+    double r = x - (double)__bfloat162float(b0);
+    b1 = __double2bfloat16(r);
+    r = r - (double)__bfloat162float(b1);
+    b2 = __double2bfloat16(r);
+}
+
+// A form: block b = (i, k) -> rows r < NB (orbital of i), 16 K values (orbital of k).
+__global__ void k_split_a(int64_t n, int nb, int stride, const double *__restrict__ A,
+                          __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int per = nb * KP;
+    const int64_t b = e / per;
+    const int rem = (int)(e - b * per), r = rem / KP, m = rem % KP;
+    const double x = m < nb ? A[b * stride + r * nb + m] : 0.0;
+    split3(x, p0[e], p1[e], p2[e]);
+}
+
+// B form: block b = (k, j) -> rows n < NB (orbital of j), 16 K values (orbital of k).
+__global__ void k_split_b(int64_t n, int nb, int stride, const double *__restrict__ B,
+                          __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int per = nb * KP;
+    const int64_t b = e / per;
+    const int rem = (int)(e - b * per), r = rem / KP, m = rem % KP;
+    const double x = m < nb ? B[b * stride + m * nb + r] : 0.0;
+    split3(x, p0[e], p1[e], p2[e]);
+}
+
+// Tile existence: bit (g, h) for every C block (i, j).
+__global__ void k_tile_mark(int64_t n_c, const int32_t *c_row, const int32_t *c_col,
+                            const int32_t *g_of, const int32_t *h_of, int n_h, uint32_t *bits)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_c) return;
+    const int64_t key = (int64_t)g_of[c_row[b]] * n_h + h_of[c_col[b]];
+    atomicOr(&bits[key >> 5], 1u << (key & 31));
+}
+
+// K list of each tile: atoms k reachable from the M group through P_A and from the N group
+// through P_B (P_B symmetric: (k, j) in P_B <=> k in row j).  COUNT pass writes sizes,
+// the FILL pass writes ascending atom indices.
+template <bool FILL>
+__global__ void __launch_bounds__(256)
+k_tile_klist(int n_atoms, const int2 *tiles, int gi, int gj, const int32_t *g_atoms,
+             const int32_t *h_atoms, const int64_t *a_rp, const int32_t *a_col,
+             const int64_t *b_rp, const int32_t *b_col, int64_t *count, const int64_t *start,
+             int32_t *klist)
+{
+    extern __shared__ uint32_t bm[];  // 2 * words
+    const int words = (n_atoms + 31) >> 5;
+    uint32_t *ba = bm, *bb = bm + words;
+    for (int w = threadIdx.x; w < 2 * words; w += blockDim.x) bm[w] = 0u;
+    __syncthreads();
+    const int2 t = tiles[blockIdx.x];
+    for (int s = 0; s < gi; ++s) {
+        const int i = g_atoms[(int64_t)t.x * gi + s];
+        if (i < 0) continue;
+        for (int64_t e = a_rp[i] + threadIdx.x; e < a_rp[i + 1]; e += blockDim.x) {
+            const int k = a_col[e];
+            atomicOr(&ba[k >> 5], 1u << (k & 31));
+        }
+    }
+    for (int s = 0; s < gj; ++s) {
+        const int j = h_atoms[(int64_t)t.y * gj + s];
+        if (j < 0) continue;
+        for (int64_t e = b_rp[j] + threadIdx.x; e < b_rp[j + 1]; e += blockDim.x) {
+            const int k = b_col[e];
+            atomicOr(&bb[k >> 5], 1u << (k & 31));
+        }
+    }
+    __syncthreads();
+    // each thread owns a contiguous run of words
+    const int per = (words + blockDim.x - 1) / blockDim.x;
+    const int w0 = threadIdx.x * per, w1 = min(words, w0 + per);
+    int mine = 0;
+    for (int w = w0; w < w1; ++w) mine += __popc(ba[w] & bb[w]);
+    __shared__ int scan[256];
+    scan[threadIdx.x] = mine;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        int v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+        __syncthreads();
+        scan[threadIdx.x] += v;
+        __syncthreads();
+    }
+    if (!FILL) {
+        if (threadIdx.x == blockDim.x - 1) count[blockIdx.x] = scan[threadIdx.x];
+        return;
+    }
+    int64_t out = start[blockIdx.x] + scan[threadIdx.x] - mine;
+    for (int w = w0; w < w1; ++w) {
+        uint32_t v = ba[w] & bb[w];
+        while (v) {
+            const int bit = __ffs(v) - 1;
+            v &= v - 1;
+            klist[out++] = w * 32 + bit;
+        }
+    }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    }
+}
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x)
+{
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+}
+
+struct SplitArgs {
+    int n_tiles;
+    const int2 *tiles;
+    const int64_t *kstart;
+    const int32_t *klist;
+    const int32_t *g_atoms, *h_atoms;
+    const int64_t *a_rp, *b_rp, *c_rp;
+    const int32_t *a_col, *b_col, *c_col;
+    const int64_t *b_tr;
+    const __nv_bfloat16 *sa[3], *sb[3];
+    double *C;
+    int c_stride;
+    double alpha, beta;
+    int32_t *flag;
+};
+
+template <int NB>
+__global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
+{
+    constexpr int GI = MT / NB, GJ = NT / NB;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *stage[2] = {smem, smem + STAGE};
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * STAGE + 16);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    // gather role: threads 0..127 own A rows, 128..191 own B rows
+    const bool a_role = t < MT, b_role = t >= MT && t < MT + NT;
+    const int grow = a_role ? t : t - MT;
+    // accumulator role: TMEM lane quarter warp%4, column half warp/4
+    const int arow = (warp & 3) * 32 + lane, half = warp >> 2;
+
+    for (int e = t; e < 2 * STAGE / 16; e += ST)
+        reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * 32);
+
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    bool failed = false;
+
+    for (int tile = blockIdx.x; tile < p.n_tiles && !failed; tile += gridDim.x) {
+        const int2 tg = p.tiles[tile];
+        const int64_t kb = p.kstart[tile], kn = p.kstart[tile + 1] - kb;
+        // gather row: A row (atom of group g) or B row (atom of group h), orbital o
+        int at = -1;
+        if (a_role && grow < GI * NB) at = p.g_atoms[(int64_t)tg.x * GI + grow / NB];
+        if (b_role && grow < GJ * NB) at = p.h_atoms[(int64_t)tg.y * GJ + grow / NB];
+        const int o = grow % NB;
+        const int64_t *rp = a_role ? p.a_rp : p.b_rp;
+        const int32_t *cl = a_role ? p.a_col : p.b_col;
+        int64_t cur = at >= 0 ? rp[at] : 0, cur_end = at >= 0 ? rp[at + 1] : 0;
+        float hi[32], lo[32];
+#pragma unroll
+        for (int x = 0; x < 32; ++x) hi[x] = lo[x] = 0.f;
+        const int nch = (int)((kn + 3) / 4);
+        for (int c = 0; c < nch; ++c) {
+            const int s = c & 1;
+            if (pending[s]) {
+                const bool ok = mbar_wait(smem_u32(&mbar[s]), phase[s]);
+                if (__syncthreads_or(!ok)) {
+                    failed = true;
+                    break;
+                }
+                phase[s] ^= 1u;
+                pending[s] = false;
+            }
+            const uint32_t sbase = smem_u32(stage[s]);
+            if (a_role || b_role) {
+                const uint32_t dbase = a_role ? sbase : sbase + 3 * A_PLANE;
+                uint8_t *gbase = a_role ? stage[s] : stage[s] + 3 * A_PLANE;
+                const int plane = a_role ? A_PLANE : B_PLANE;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int64_t kidx = (int64_t)c * 4 + kk;
+                    const int k = kidx < kn ? p.klist[kb + kidx] : -1;
+                    bool hit = false;
+                    if (k >= 0 && at >= 0) {
+                        while (cur < cur_end && cl[cur] < k) ++cur;
+                        hit = cur < cur_end && cl[cur] == k;
+                    }
+                    // A: block (at, k) is the cursor's block; B: block (k, at) is its transpose
+                    const int64_t blk = hit ? (a_role ? cur : p.b_tr[cur]) : 0;
+#pragma unroll
+                    for (int pl = 0; pl < 3; ++pl) {
+                        const uint32_t d = dbase + pl * plane;
+                        if (hit) {
+                            const __nv_bfloat16 *src =
+                                (a_role ? p.sa[pl] : p.sb[pl]) + (blk * NB + o) * KP;
+                            cp16(d + cm_off(grow, 2 * kk), src);
+                            cp16(d + cm_off(grow, 2 * kk + 1), src + 8);
+                        } else {
+                            uint8_t *g = gbase + pl * plane;
+                            *reinterpret_cast<uint4 *>(g + cm_off(grow, 2 * kk)) =
+                                make_uint4(0u, 0u, 0u, 0u);
+                            *reinterpret_cast<uint4 *>(g + cm_off(grow, 2 * kk + 1)) =
+                                make_uint4(0u, 0u, 0u, 0u);
+                        }
+                    }
+                }
+            }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (t == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ab = sbase, bbase = sbase + 3 * A_PLANE;
+                const int pq[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
+#pragma unroll
+                for (int ks = 0; ks < KCH / 16; ++ks)
+#pragma unroll
+                    for (int x = 0; x < 6; ++x) {
+                        const uint64_t ad = smem_desc(ab + pq[x][0] * A_PLANE + ks * 256);
+                        const uint64_t bd = smem_desc(bbase + pq[x][1] * B_PLANE + ks * 256);
+                        const uint32_t acc = (c % DRAIN == 0 && ks == 0 && x == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+                                tmem),
+                            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+                    }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&mbar[s]))
+                    : "memory");
+            }
+            pending[s] = true;
+            if (c % DRAIN == DRAIN - 1 || c == nch - 1) {
+                const bool ok = mbar_wait(smem_u32(&mbar[s]), phase[s]);
+                if (__syncthreads_or(!ok)) {
+                    failed = true;
+                    break;
+                }
+                phase[s] ^= 1u;
+                pending[s] = false;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    uint32_t v[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,"
+                        "%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                          "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]),
+                          "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                        : "r"(taddr + q * 16));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int x = 0; x < 16; ++x)
+                        two_sum_add(hi[q * 16 + x], lo[q * 16 + x], __uint_as_float(v[x]));
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+            }
+        }
+        if (failed) break;
+        // epilogue: accumulator row arow = (atom ia, orbital a) and columns
+        // 32*half .. 32*half+31 = (atom of group h, orbital) of every block P_C holds
+        const int ia = arow < GI * NB ? p.g_atoms[(int64_t)tg.x * GI + arow / NB] : -1;
+        if (ia >= 0) {
+            const int a = arow % NB;
+            int cached_jl = -1;
+            double *dst = nullptr;
+#pragma unroll
+            for (int x = 0; x < 32; ++x) {
+                const int col = half * 32 + x;
+                const int jl = col / NB, bo = col % NB;
+                if (jl >= GJ) continue;
+                if (jl != cached_jl) {
+                    cached_jl = jl;
+                    dst = nullptr;
+                    const int j = p.h_atoms[(int64_t)tg.y * GJ + jl];
+                    if (j >= 0) {
+                        int64_t lo_i = p.c_rp[ia], hi_i = p.c_rp[ia + 1];
+                        while (lo_i < hi_i) {
+                            const int64_t mid = (lo_i + hi_i) >> 1;
+                            if (p.c_col[mid] < j)
+                                lo_i = mid + 1;
+                            else
+                                hi_i = mid;
+                        }
+                        if (lo_i < p.c_rp[ia + 1] && p.c_col[lo_i] == j)
+                            dst = p.C + lo_i * p.c_stride + a * NB;
+                    }
+                }
+                if (!dst) continue;
+                const double v = (double)hi[x] + (double)lo[x];
+                dst[bo] = p.beta == 0.0 ? p.alpha * v : p.beta * dst[bo] + p.alpha * v;
+            }
+        }
+    }
+    if (failed && t == 0) atomicOr(p.flag, 16);
+    // retire outstanding commits before releasing tensor memory
+    for (int s = 0; s < 2; ++s)
+        if (pending[s]) mbar_wait(smem_u32(&mbar[s]), phase[s]);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS));
+}
+
+// ---------------------------------------------------------------- host side
+
+struct Groups {
+    int gi = 0, gj = 0, n_g = 0, n_h = 0;
+    DevBuf g_atoms, h_atoms, g_of, h_of;
+};
+
+struct SplitTiles {
+    int n_tiles = 0;
+    int64_t n_k = 0;
+    double mma_flops = 0.0;  // tensor-core flops of one product over these tiles
+    DevBuf tiles, kstart, klist;
+};
+
+// Morton order of the atoms (positions quantised to 1024 per box edge).
+std::vector<int32_t> spatial_order(const Geometry &g)
+{
+    auto spread = [](uint64_t v) {
+        uint64_t x = v & 0x3ff;
+        x = (x | (x << 16)) & 0x30000ff;
+        x = (x | (x << 8)) & 0x300f00f;
+        x = (x | (x << 4)) & 0x30c30c3;
+        x = (x | (x << 2)) & 0x9249249;
+        return x;
+    };
+    std::vector<uint64_t> key(g.n_atoms);
+    for (int i = 0; i < g.n_atoms; ++i) {
+        uint64_t c[3];
+        for (int d = 0; d < 3; ++d) {
+            double f = g.pos_host[3 * i + d] / g.box[d];
+            f -= std::floor(f);
+            c[d] = (uint64_t)std::min(1023.0, std::max(0.0, f * 1024.0));
+        }
+        key[i] = spread(c[0]) | (spread(c[1]) << 1) | (spread(c[2]) << 2);
+    }
+    std::vector<int32_t> order(g.n_atoms);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return key[x] < key[y]; });
+    return order;
+}
+
+cq_status get_groups(cq_ctx *ctx, const cq_pattern *p, Groups **out)
+{
+    auto key = std::make_tuple(1, p->geo->id, (uint64_t)0, (uint64_t)0);
+    auto it = ctx->aux.find(key);
+    if (it != ctx->aux.end()) {
+        *out = static_cast<Groups *>(it->second.get());
+        return CQ_OK;
+    }
+    const Geometry &g = *p->geo;
+    auto gr = std::make_shared<Groups>();
+    const int nb = g.uniform_nb;
+    gr->gi = MT / nb;
+    gr->gj = NT / nb;
+    gr->n_g = (g.n_atoms + gr->gi - 1) / gr->gi;
+    gr->n_h = (g.n_atoms + gr->gj - 1) / gr->gj;
+    std::vector<int32_t> order = spatial_order(g);
+    std::vector<int32_t> ga((size_t)gr->n_g * gr->gi, -1), ha((size_t)gr->n_h * gr->gj, -1);
+    std::vector<int32_t> gof(g.n_atoms), hof(g.n_atoms);
+    for (int r = 0; r < g.n_atoms; ++r) {
+        ga[r] = order[r];
+        gof[order[r]] = r / gr->gi;
+        ha[r] = order[r];
+        hof[order[r]] = r / gr->gj;
+    }
+    cq_status st;
+    if ((st = cq_alloc(ctx, gr->g_atoms, 4 * ga.size())) != CQ_OK ||
+        (st = cq_alloc(ctx, gr->h_atoms, 4 * ha.size())) != CQ_OK ||
+        (st = cq_alloc(ctx, gr->g_of, 4 * gof.size())) != CQ_OK ||
+        (st = cq_alloc(ctx, gr->h_of, 4 * hof.size())) != CQ_OK)
+        return st;
+    cudaMemcpyAsync(gr->g_atoms.ptr, ga.data(), 4 * ga.size(), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(gr->h_atoms.ptr, ha.data(), 4 * ha.size(), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(gr->g_of.ptr, gof.data(), 4 * gof.size(), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(gr->h_of.ptr, hof.data(), 4 * hof.size(), cudaMemcpyHostToDevice, ctx->stream);
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "groups")) != CQ_OK) return st;
+    *out = gr.get();
+    ctx->aux[key] = gr;
+    return CQ_OK;
+}
+
+cq_status get_tiles(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
+                    const cq_pattern *pC, const Groups *gr, SplitTiles **out)
+{
+    auto key = std::make_tuple(2, pA->id, pB->id, pC->id);
+    auto it = ctx->aux.find(key);
+    if (it != ctx->aux.end()) {
+        *out = static_cast<SplitTiles *>(it->second.get());
+        return CQ_OK;
+    }
+    cudaStream_t s = ctx->stream;
+    auto st_ = std::make_shared<SplitTiles>();
+    const int64_t nbits = (int64_t)gr->n_g * gr->n_h;
+    const int64_t nwords = (nbits + 31) / 32;
+    void *vb;
+    cq_status st = cq_scratch(ctx, "split_bits", 4 * nwords, &vb);
+    if (st != CQ_OK) return st;
+    cudaMemsetAsync(vb, 0, 4 * nwords, s);
+    if (pC->n_blocks > 0) {
+        k_tile_mark<<<(unsigned)((pC->n_blocks + 255) / 256), 256, 0, s>>>(
+            pC->n_blocks, pC->row.as<int32_t>(), pC->col.as<int32_t>(), gr->g_of.as<int32_t>(),
+            gr->h_of.as<int32_t>(), gr->n_h, (uint32_t *)vb);
+        cq_count_launch();
+    }
+    std::vector<uint32_t> bits(nwords);
+    cudaMemcpyAsync(bits.data(), vb, 4 * nwords, cudaMemcpyDeviceToHost, s);
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "tile mark")) != CQ_OK) return st;
+    std::vector<int2> tiles;
+    for (int64_t b = 0; b < nbits; ++b)
+        if (bits[b >> 5] & (1u << (b & 31))) tiles.push_back(make_int2((int)(b / gr->n_h), (int)(b % gr->n_h)));
+    st_->n_tiles = (int)tiles.size();
+    if ((st = cq_alloc(ctx, st_->tiles, sizeof(int2) * (tiles.size() + 1))) != CQ_OK ||
+        (st = cq_alloc(ctx, st_->kstart, sizeof(int64_t) * (tiles.size() + 1))) != CQ_OK)
+        return st;
+    cudaMemcpyAsync(st_->tiles.ptr, tiles.data(), sizeof(int2) * tiles.size(),
+                    cudaMemcpyHostToDevice, s);
+    const int n_atoms = pA->geo->n_atoms;
+    const size_t shm = 2 * 4 * (size_t)((n_atoms + 31) / 32);
+    if (shm > 200 * 1024) return cq_fail(ctx, CQ_ERR_INVALID, "split product: too many atoms");
+    void *vc;
+    if ((st = cq_scratch(ctx, "split_kcnt", 8 * (tiles.size() + 1), &vc)) != CQ_OK) return st;
+    if (!tiles.empty()) {
+        cudaFuncSetAttribute(k_tile_klist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        cudaFuncSetAttribute(k_tile_klist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        k_tile_klist<false><<<st_->n_tiles, 256, shm, s>>>(
+            n_atoms, st_->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
+            gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
+            pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), (int64_t *)vc, nullptr, nullptr);
+        cq_count_launch();
+    }
+    if ((st = cq_scan_i64(ctx, (int64_t *)vc, st_->kstart.as<int64_t>(), st_->n_tiles)) != CQ_OK)
+        return st;
+    cudaMemcpyAsync(&st_->n_k, st_->kstart.as<int64_t>() + st_->n_tiles, 8, cudaMemcpyDeviceToHost, s);
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "k lists")) != CQ_OK) return st;
+    if ((st = cq_alloc(ctx, st_->klist, 4 * (st_->n_k + 1))) != CQ_OK) return st;
+    {
+        std::vector<int64_t> ks(st_->n_tiles + 1);
+        cudaMemcpyAsync(ks.data(), st_->kstart.ptr, 8 * ks.size(), cudaMemcpyDeviceToHost, s);
+        if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "k lists")) != CQ_OK) return st;
+        double chunks = 0.0;
+        for (int q = 0; q < st_->n_tiles; ++q) chunks += (double)((ks[q + 1] - ks[q] + 3) / 4);
+        st_->mma_flops = chunks * 6.0 * (KCH / 16) * 2.0 * MT * NT * 16;
+    }
+    if (!tiles.empty()) {
+        k_tile_klist<true><<<st_->n_tiles, 256, shm, s>>>(
+            n_atoms, st_->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
+            gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
+            pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), nullptr, st_->kstart.as<int64_t>(),
+            st_->klist.as<int32_t>());
+        cq_count_launch();
+    }
+    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "k lists")) != CQ_OK) return st;
+    *out = st_.get();
+    ctx->aux[key] = st_;
+    return CQ_OK;
+}
+
+}  // namespace
+
+cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pattern *pA,
+                        const double *A, const cq_pattern *pB, const double *B, double beta,
+                        const cq_pattern *pC, double *C)
+{
+    const int nb = pC->geo->uniform_nb;
+    if (nb != 9 && nb != 4)
+        return cq_fail(ctx, CQ_ERR_INVALID,
+                       "split-BF16 product: needs a uniform basis of 4 or 9 orbitals per atom");
+    if (pC->n_blocks == 0) return CQ_OK;
+    cudaStream_t s = ctx->stream;
+    Groups *gr;
+    SplitTiles *tiles;
+    cq_status st = get_groups(ctx, pC, &gr);
+    if (st != CQ_OK) return st;
+    if ((st = get_tiles(ctx, pA, pB, pC, gr, &tiles)) != CQ_OK) return st;
+    // operands in padded split form
+    const int64_t na = pA->n_blocks * nb * KP, nbv = pB->n_blocks * nb * KP;
+    void *va, *vb;
+    if ((st = cq_scratch(ctx, "split_A", 3 * 2 * (size_t)na, &va)) != CQ_OK) return st;
+    if ((st = cq_scratch(ctx, "split_B", 3 * 2 * (size_t)nbv, &vb)) != CQ_OK) return st;
+    __nv_bfloat16 *sa = (__nv_bfloat16 *)va, *sb = (__nv_bfloat16 *)vb;
+    k_split_a<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(na, nb, pA->uniform, A, sa, sa + na,
+                                                           sa + 2 * na);
+    k_split_b<<<(unsigned)((nbv + 255) / 256), 256, 0, s>>>(nbv, nb, pB->uniform, B, sb,
+                                                            sb + nbv, sb + 2 * nbv);
+    cq_count_launch(2);
+    SplitArgs a;
+    a.n_tiles = tiles->n_tiles;
+    a.tiles = tiles->tiles.as<int2>();
+    a.kstart = tiles->kstart.as<int64_t>();
+    a.klist = tiles->klist.as<int32_t>();
+    a.g_atoms = gr->g_atoms.as<int32_t>();
+    a.h_atoms = gr->h_atoms.as<int32_t>();
+    a.a_rp = pA->row_ptr.as<int64_t>();
+    a.b_rp = pB->row_ptr.as<int64_t>();
+    a.c_rp = pC->row_ptr.as<int64_t>();
+    a.a_col = pA->col.as<int32_t>();
+    a.b_col = pB->col.as<int32_t>();
+    a.c_col = pC->col.as<int32_t>();
+    a.b_tr = pB->transpose.as<int64_t>();
+    for (int q = 0; q < 3; ++q) {
+        a.sa[q] = sa + q * na;
+        a.sb[q] = sb + q * nbv;
+    }
+    a.C = C;
+    a.c_stride = pC->uniform;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.flag = ctx->flag.as<int32_t>();
+    const int grid = std::min(tiles->n_tiles, ctx->num_sms);
+    cq_timing_begin(ctx, tl->flops, tiles->mma_flops);
+    if (nb == 9) {
+        cudaFuncSetAttribute(k_bsmm_split<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        k_bsmm_split<9><<<grid, ST, SMEM, s>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_bsmm_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        k_bsmm_split<4><<<grid, ST, SMEM, s>>>(a);
+    }
+    cq_timing_end(ctx);
+    cq_count_launch();
+    return cq_check_cuda(ctx, cudaGetLastError(), "bsmm_split");
 }

@@ -88,15 +88,19 @@ struct cq_ctx {
     std::map<std::string, std::unique_ptr<DevBuf>> scratch;
     std::vector<cq_pattern *> live_patterns;
     std::vector<cq_lnv *> live_lnv;
+    // other cached per-pattern data, keyed (kind, id, id, id); entries naming a destroyed
+    // pattern's id are dropped with it
+    std::map<std::tuple<int, uint64_t, uint64_t, uint64_t>, std::shared_ptr<void>> aux;
     // product-kernel timing
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
     size_t ev_used = 0;
     double timed_flops = 0.0;
+    double timed_mma_flops = 0.0;
 };
 
 // Record a timing event pair around a product launch when timing is on.
-void cq_timing_begin(cq_ctx *ctx, double flops);
+void cq_timing_begin(cq_ctx *ctx, double flops, double mma_flops = 0.0);
 void cq_timing_end(cq_ctx *ctx);
 
 // ---------------------------------------------------------------- helpers (ctx.cu)

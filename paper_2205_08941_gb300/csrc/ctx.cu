@@ -248,6 +248,7 @@ extern "C" void cq_ctx_destroy(cq_ctx *ctx)
     }
     ctx->tasks.clear();
     ctx->maps.clear();
+    ctx->aux.clear();
     ctx->scratch.clear();
     if (ctx->host_out) cudaFreeHost(ctx->host_out);
     delete ctx;
@@ -381,6 +382,13 @@ extern "C" void cq_pattern_destroy(cq_pattern *p)
             else
                 ++it;
         }
+        for (auto it = ctx->aux.begin(); it != ctx->aux.end();) {
+            auto k = it->first;
+            if (std::get<1>(k) == p->id || std::get<2>(k) == p->id || std::get<3>(k) == p->id)
+                it = ctx->aux.erase(it);
+            else
+                ++it;
+        }
         for (size_t e = 0; e < ctx->live_patterns.size(); ++e)
             if (ctx->live_patterns[e] == p) {
                 ctx->live_patterns.erase(ctx->live_patterns.begin() + e);
@@ -467,9 +475,10 @@ extern "C" cq_status cq_dot(cq_ctx *ctx, const cq_pattern *p, const double *A, c
 
 // ---------------------------------------------------------------- timing and FP64 peak
 
-void cq_timing_begin(cq_ctx *ctx, double flops)
+void cq_timing_begin(cq_ctx *ctx, double flops, double mma_flops)
 {
     if (!ctx->timing) return;
+    ctx->timed_mma_flops += mma_flops;
     if (ctx->ev_used == ctx->ev_pool.size()) {
         cudaEvent_t a, b;
         cudaEventCreate(&a);
@@ -495,7 +504,7 @@ extern "C" cq_status cq_ctx_set_timing(cq_ctx *ctx, int on)
 }
 
 extern "C" cq_status cq_ctx_kernel_stats(cq_ctx *ctx, int64_t *launches_host, double *ms_host,
-                                         double *flops_host)
+                                         double *flops_host, double *mma_flops_host)
 {
     if (!ctx) return CQ_ERR_INVALID;
     cq_status st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync");
@@ -511,6 +520,8 @@ extern "C" cq_status cq_ctx_kernel_stats(cq_ctx *ctx, int64_t *launches_host, do
     if (launches_host) *launches_host = (int64_t)ctx->ev_used;
     if (ms_host) *ms_host = ms;
     if (flops_host) *flops_host = ctx->timed_flops;
+    if (mma_flops_host) *mma_flops_host = ctx->timed_mma_flops;
+    ctx->timed_mma_flops = 0.0;
     ctx->ev_used = 0;
     ctx->timed_flops = 0.0;
     return CQ_OK;

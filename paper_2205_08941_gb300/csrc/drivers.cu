@@ -412,6 +412,17 @@ extern "C" cq_status cq_lnv_step(cq_lnv *s, cq_lnv_report *rep)
     return CQ_OK;
 }
 
+extern "C" cq_status cq_lnv_set_precision(cq_lnv *s, cq_precision prec)
+{
+    if (!s || !s->ctx) return CQ_ERR_INVALID;
+    if (prec != CQ_FP64 && prec != CQ_SPLIT_BF16X3)
+        return cq_fail(s->ctx, CQ_ERR_INVALID, "lnv_set_precision: unknown precision");
+    s->prec = prec;
+    s->have_prev = false;
+    s->have_alpha = false;
+    return lnv_evaluate_corrected(s, &s->n_corr_initial);
+}
+
 extern "C" cq_status cq_lnv_state(const cq_lnv *s, cq_lnv_report *rep)
 {
     if (!s || !rep || !s->ctx) return CQ_ERR_INVALID;
