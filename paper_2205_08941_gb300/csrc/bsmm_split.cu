@@ -23,9 +23,10 @@
 // matrices, SBO = 1024 B between 8-row groups) and one thread issues the MMAs.
 //
 // Pipeline per CTA (256 threads; warps w and w+4 share TMEM lane quarter w and split the
-// 64 accumulator columns; one CTA per SM): two shared
-// stages; while the tensor core runs chunk c from stage c%2, the threads gather chunk c+1
-// into the other stage; an mbarrier per stage (tcgen05.commit) tells when a stage is free.
+// 64 accumulator columns; one CTA per SM): three shared stages; while the tensor core runs
+// chunk c, the gathers of chunks c+1 and c+2 are in flight; an mbarrier per stage
+// (tcgen05.commit) tells when a stage is free.  Gathers read per-tile block-index tables,
+// so no load in the hot loop depends on another.
 // Every wait is bounded (about a second); on timeout the kernel records an error flag,
 // stops issuing work, waits (bounded) for its own MMAs, frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -44,7 +45,7 @@ constexpr int KP = 16;                       // padded orbitals per atom along K
 constexpr int A_PLANE = MT * KCH * 2;        // 16 KB
 constexpr int B_PLANE = NT * KCH * 2;        // 8 KB
 constexpr int STAGE = 3 * A_PLANE + 3 * B_PLANE;
-constexpr int SMEM = 2 * STAGE + 64;
+constexpr int SMEM = 3 * STAGE + 64;  // three pipeline stages + barriers
 constexpr int DRAIN = 4;                     // chunks per FP32 accumulation period
 constexpr int TMEM_COLS = 64;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
@@ -181,6 +182,42 @@ k_tile_klist(int n_atoms, const int2 *tiles, int gi, int gj, const int32_t *g_at
     }
 }
 
+// Block-index table of each tile: for every K-list entry k and every slot s of the tile's
+// groups, the index of block (i_s, k) in P_A (s < gi) or of block (k, j_s) in P_B, else -1.
+// Built once per pattern triple so the product kernel's gather has no dependent searches.
+__global__ void __launch_bounds__(256)
+k_tile_index(const int2 *tiles, int gi, int gj, const int32_t *g_atoms, const int32_t *h_atoms,
+             const int64_t *a_rp, const int32_t *a_col, const int64_t *b_rp,
+             const int32_t *b_col, const int64_t *b_tr, const int64_t *kstart,
+             const int32_t *klist, int32_t *table)
+{
+    const int2 t = tiles[blockIdx.x];
+    const int64_t kb = kstart[blockIdx.x], kn = kstart[blockIdx.x + 1] - kb;
+    const int w = gi + gj;
+    for (int s = 0; s < w; ++s) {
+        const bool left = s < gi;
+        const int atom = left ? g_atoms[(int64_t)t.x * gi + s] : h_atoms[(int64_t)t.y * gj + s - gi];
+        const int64_t *rp = left ? a_rp : b_rp;
+        const int32_t *cl = left ? a_col : b_col;
+        for (int64_t q = threadIdx.x; q < kn; q += blockDim.x) {
+            int32_t idx = -1;
+            if (atom >= 0) {
+                const int k = klist[kb + q];
+                int64_t lo = rp[atom], hi = rp[atom + 1];
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (cl[mid] < k)
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                if (lo < rp[atom + 1] && cl[lo] == k) idx = (int32_t)(left ? lo : b_tr[lo]);
+            }
+            table[(kb + q) * w + s] = idx;
+        }
+    }
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
 {
     const long long t0 = clock64();
@@ -217,6 +254,7 @@ struct SplitArgs {
     const int2 *tiles;
     const int64_t *kstart;
     const int32_t *klist;
+    const int32_t *table;
     const int32_t *g_atoms, *h_atoms;
     const int64_t *a_rp, *b_rp, *c_rp;
     const int32_t *a_col, *b_col, *c_col;
@@ -228,205 +266,7 @@ struct SplitArgs {
     int32_t *flag;
 };
 
-template <int NB>
-__global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
-{
-    constexpr int GI = MT / NB, GJ = NT / NB;
-    extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *stage[2] = {smem, smem + STAGE};
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * STAGE + 16);
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    // gather role: threads 0..127 own A rows, 128..191 own B rows
-    const bool a_role = t < MT, b_role = t >= MT && t < MT + NT;
-    const int grow = a_role ? t : t - MT;
-    // accumulator role: TMEM lane quarter warp%4, column half warp/4
-    const int arow = (warp & 3) * 32 + lane, half = warp >> 2;
-
-    for (int e = t; e < 2 * STAGE / 16; e += ST)
-        reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
-    if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * 32);
-
-    uint32_t phase[2] = {0u, 0u};
-    bool pending[2] = {false, false};
-    bool failed = false;
-
-    for (int tile = blockIdx.x; tile < p.n_tiles && !failed; tile += gridDim.x) {
-        const int2 tg = p.tiles[tile];
-        const int64_t kb = p.kstart[tile], kn = p.kstart[tile + 1] - kb;
-        // gather row: A row (atom of group g) or B row (atom of group h), orbital o
-        int at = -1;
-        if (a_role && grow < GI * NB) at = p.g_atoms[(int64_t)tg.x * GI + grow / NB];
-        if (b_role && grow < GJ * NB) at = p.h_atoms[(int64_t)tg.y * GJ + grow / NB];
-        const int o = grow % NB;
-        const int64_t *rp = a_role ? p.a_rp : p.b_rp;
-        const int32_t *cl = a_role ? p.a_col : p.b_col;
-        int64_t cur = at >= 0 ? rp[at] : 0, cur_end = at >= 0 ? rp[at + 1] : 0;
-        float hi[32], lo[32];
-#pragma unroll
-        for (int x = 0; x < 32; ++x) hi[x] = lo[x] = 0.f;
-        const int nch = (int)((kn + 3) / 4);
-        for (int c = 0; c < nch; ++c) {
-            const int s = c & 1;
-            if (pending[s]) {
-                const bool ok = mbar_wait(smem_u32(&mbar[s]), phase[s]);
-                if (__syncthreads_or(!ok)) {
-                    failed = true;
-                    break;
-                }
-                phase[s] ^= 1u;
-                pending[s] = false;
-            }
-            const uint32_t sbase = smem_u32(stage[s]);
-            if (a_role || b_role) {
-                const uint32_t dbase = a_role ? sbase : sbase + 3 * A_PLANE;
-                uint8_t *gbase = a_role ? stage[s] : stage[s] + 3 * A_PLANE;
-                const int plane = a_role ? A_PLANE : B_PLANE;
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const int64_t kidx = (int64_t)c * 4 + kk;
-                    const int k = kidx < kn ? p.klist[kb + kidx] : -1;
-                    bool hit = false;
-                    if (k >= 0 && at >= 0) {
-                        while (cur < cur_end && cl[cur] < k) ++cur;
-                        hit = cur < cur_end && cl[cur] == k;
-                    }
-                    // A: block (at, k) is the cursor's block; B: block (k, at) is its transpose
-                    const int64_t blk = hit ? (a_role ? cur : p.b_tr[cur]) : 0;
-#pragma unroll
-                    for (int pl = 0; pl < 3; ++pl) {
-                        const uint32_t d = dbase + pl * plane;
-                        if (hit) {
-                            const __nv_bfloat16 *src =
-                                (a_role ? p.sa[pl] : p.sb[pl]) + (blk * NB + o) * KP;
-                            cp16(d + cm_off(grow, 2 * kk), src);
-                            cp16(d + cm_off(grow, 2 * kk + 1), src + 8);
-                        } else {
-                            uint8_t *g = gbase + pl * plane;
-                            *reinterpret_cast<uint4 *>(g + cm_off(grow, 2 * kk)) =
-                                make_uint4(0u, 0u, 0u, 0u);
-                            *reinterpret_cast<uint4 *>(g + cm_off(grow, 2 * kk + 1)) =
-                                make_uint4(0u, 0u, 0u, 0u);
-                        }
-                    }
-                }
-            }
-            asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (t == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ab = sbase, bbase = sbase + 3 * A_PLANE;
-                const int pq[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
-#pragma unroll
-                for (int ks = 0; ks < KCH / 16; ++ks)
-#pragma unroll
-                    for (int x = 0; x < 6; ++x) {
-                        const uint64_t ad = smem_desc(ab + pq[x][0] * A_PLANE + ks * 256);
-                        const uint64_t bd = smem_desc(bbase + pq[x][1] * B_PLANE + ks * 256);
-                        const uint32_t acc = (c % DRAIN == 0 && ks == 0 && x == 0) ? 0u : 1u;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
-                                tmem),
-                            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
-                    }
-                asm volatile(
-                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        smem_u32(&mbar[s]))
-                    : "memory");
-            }
-            pending[s] = true;
-            if (c % DRAIN == DRAIN - 1 || c == nch - 1) {
-                const bool ok = mbar_wait(smem_u32(&mbar[s]), phase[s]);
-                if (__syncthreads_or(!ok)) {
-                    failed = true;
-                    break;
-                }
-                phase[s] ^= 1u;
-                pending[s] = false;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    uint32_t v[16];
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,"
-                        "%10,%11,%12,%13,%14,%15}, [%16];"
-                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                          "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]),
-                          "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                        : "r"(taddr + q * 16));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int x = 0; x < 16; ++x)
-                        two_sum_add(hi[q * 16 + x], lo[q * 16 + x], __uint_as_float(v[x]));
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncthreads();
-            }
-        }
-        if (failed) break;
-        // epilogue: accumulator row arow = (atom ia, orbital a) and columns
-        // 32*half .. 32*half+31 = (atom of group h, orbital) of every block P_C holds
-        const int ia = arow < GI * NB ? p.g_atoms[(int64_t)tg.x * GI + arow / NB] : -1;
-        if (ia >= 0) {
-            const int a = arow % NB;
-            int cached_jl = -1;
-            double *dst = nullptr;
-#pragma unroll
-            for (int x = 0; x < 32; ++x) {
-                const int col = half * 32 + x;
-                const int jl = col / NB, bo = col % NB;
-                if (jl >= GJ) continue;
-                if (jl != cached_jl) {
-                    cached_jl = jl;
-                    dst = nullptr;
-                    const int j = p.h_atoms[(int64_t)tg.y * GJ + jl];
-                    if (j >= 0) {
-                        int64_t lo_i = p.c_rp[ia], hi_i = p.c_rp[ia + 1];
-                        while (lo_i < hi_i) {
-                            const int64_t mid = (lo_i + hi_i) >> 1;
-                            if (p.c_col[mid] < j)
-                                lo_i = mid + 1;
-                            else
-                                hi_i = mid;
-                        }
-                        if (lo_i < p.c_rp[ia + 1] && p.c_col[lo_i] == j)
-                            dst = p.C + lo_i * p.c_stride + a * NB;
-                    }
-                }
-                if (!dst) continue;
-                const double v = (double)hi[x] + (double)lo[x];
-                dst[bo] = p.beta == 0.0 ? p.alpha * v : p.beta * dst[bo] + p.alpha * v;
-            }
-        }
-    }
-    if (failed && t == 0) atomicOr(p.flag, 16);
-    // retire outstanding commits before releasing tensor memory
-    for (int s = 0; s < 2; ++s)
-        if (pending[s]) mbar_wait(smem_u32(&mbar[s]), phase[s]);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TMEM_COLS));
-}
+#include "bsmm_split_kernel.cuh"
 
 // ---------------------------------------------------------------- host side
 
@@ -439,7 +279,7 @@ struct SplitTiles {
     int n_tiles = 0;
     int64_t n_k = 0;
     double mma_flops = 0.0;  // tensor-core flops of one product over these tiles
-    DevBuf tiles, kstart, klist;
+    DevBuf tiles, kstart, klist, table;
 };
 
 // Morton order of the atoms (positions quantised to 1024 per box edge).
@@ -581,6 +421,17 @@ cq_status get_tiles(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
         cq_count_launch();
     }
     if ((st = cq_check_cuda(ctx, cudaGetLastError(), "k lists")) != CQ_OK) return st;
+    const int w = gr->gi + gr->gj;
+    if ((st = cq_alloc(ctx, st_->table, 4 * (size_t)(st_->n_k + 1) * w)) != CQ_OK) return st;
+    if (!tiles.empty()) {
+        k_tile_index<<<st_->n_tiles, 256, 0, s>>>(
+            st_->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
+            gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
+            pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), pB->transpose.as<int64_t>(),
+            st_->kstart.as<int64_t>(), st_->klist.as<int32_t>(), st_->table.as<int32_t>());
+        cq_count_launch();
+    }
+    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "tile index")) != CQ_OK) return st;
     *out = st_.get();
     ctx->aux[key] = st_;
     return CQ_OK;
@@ -619,6 +470,7 @@ cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_
     a.tiles = tiles->tiles.as<int2>();
     a.kstart = tiles->kstart.as<int64_t>();
     a.klist = tiles->klist.as<int32_t>();
+    a.table = tiles->table.as<int32_t>();
     a.g_atoms = gr->g_atoms.as<int32_t>();
     a.h_atoms = gr->h_atoms.as<int32_t>();
     a.a_rp = pA->row_ptr.as<int64_t>();

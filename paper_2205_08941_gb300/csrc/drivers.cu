@@ -140,6 +140,7 @@ struct cq_lnv {
     bool have_prev = false, have_alpha = false;
     double alpha_prev = 0.0;
     double n_tol = 1e-10;
+    double n_tol_split = 1e-9;
     int max_corr = 5;
     double flops = 0.0;
     int products = 0;
@@ -227,7 +228,9 @@ cq_status lnv_evaluate_corrected(cq_lnv *s, int *count)
 {
     CQ_TRY(lnv_eval_n(s));
     int k = 0;
-    while (std::fabs(s->N - s->ne) > s->n_tol * s->ne && k < s->max_corr) {
+    // split-BF16 products resolve N to ~1e-10 relative, so their corrections stop at 1e-9
+    const double tol = s->prec == CQ_SPLIT_BF16X3 ? s->n_tol_split : s->n_tol;
+    while (std::fabs(s->N - s->ne) > tol * s->ne && k < s->max_corr) {
         double gn2;
         CQ_TRY(dot_l(s, s->GN.as<double>(), s->GN.as<double>(), &gn2));
         CQ_TRY(cq_axpby(s->ctx, s->pL->n_values, (s->ne - s->N) / gn2, s->GN.as<double>(), 1.0,
