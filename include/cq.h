@@ -105,6 +105,20 @@ int64_t cq_kernel_launches(void);
 cq_status cq_pattern_build(cq_ctx *ctx, int32_t n_atoms, const double *pos_dev,
                            const double *box_host, const int32_t *nb_dev, double range,
                            cq_pattern **out);
+/*
+ * Batch of n_cells independent periodic cells (up to 1024) as one pattern: the atoms of
+ * cell c are cell_start_host[c] .. cell_start_host[c+1]-1 (cell_start_host[0] = 0, no empty
+ * cell), cell c has box boxes_host[3c..3c+2] and range ranges_host[c]; pairs never cross
+ * cells.  Products over a batch pattern compute every cell in one launch; traces, dots and
+ * the LNV / Hotelling / PM scalars are kept per cell (the *_cells entry points).  Blocks of
+ * a cell are contiguous in the pattern (its rows are).
+ */
+cq_status cq_pattern_build_batch(cq_ctx *ctx, int32_t n_cells, const int32_t *cell_start_host,
+                                 const double *pos_dev, const double *boxes_host,
+                                 const int32_t *nb_dev, const double *ranges_host,
+                                 cq_pattern **out);
+/* Number of cells of a pattern (1 unless built by cq_pattern_build_batch). */
+int32_t cq_pattern_cells(const cq_pattern *p);
 /* Sizes of a pattern: number of blocks and length of a value array. */
 cq_status cq_pattern_info(const cq_pattern *p, int64_t *n_blocks, int64_t *n_values);
 /* Copy the pattern's index arrays into caller buffers (any may be NULL): row_ptr
@@ -180,6 +194,12 @@ cq_status cq_pm_guess(cq_ctx *ctx, const cq_pattern *pS, const double *S, const 
                       const cq_pattern *pT, const double *T, const cq_pattern *pL,
                       double *L, double n_occ);
 
+/* The same for a batch: n_occ_host[c] occupied states in cell c, and mu, lambda, the
+ * Gershgorin bounds and N per cell.  cq_pm_guess is this call on a one-cell pattern. */
+cq_status cq_pm_guess_cells(cq_ctx *ctx, const cq_pattern *pS, const double *S,
+                            const double *H, const cq_pattern *pT, const double *T,
+                            const cq_pattern *pL, double *L, const double *n_occ_host);
+
 /* One McWeeny purification step L <- mask_L(3LSL - 2LSLSL), every intermediate kept on its
  * full range (r_L + r_S, 2 r_S + r_L, 2 r_L) so the masked result is exact. */
 cq_status cq_mcweeny_step(cq_ctx *ctx, const cq_pattern *pS, const double *S,
@@ -212,13 +232,23 @@ typedef struct {
 cq_status cq_lnv_create(cq_ctx *ctx, const cq_pattern *pS, const double *S, const double *H,
                         const cq_pattern *pL, double *L, double n_electrons,
                         cq_precision prec, cq_lnv **out);
+/* Batch version: n_electrons_host[c] electrons in cell c; every scalar of the minimisation
+ * (mu, CG coefficients, line search, corrections) is per cell, the products are shared
+ * launches.  cq_lnv_create is this call on a one-cell pattern. */
+cq_status cq_lnv_create_cells(cq_ctx *ctx, const cq_pattern *pS, const double *S,
+                              const double *H, const cq_pattern *pL, double *L,
+                              const double *n_electrons_host, cq_precision prec,
+                              cq_lnv **out);
+/* One step; report_host receives one cq_lnv_report per cell (one for a single cell). */
 cq_status cq_lnv_step(cq_lnv *lnv, cq_lnv_report *report_host);
+/* Number of cells of the LNV object. */
+int32_t cq_lnv_cells(const cq_lnv *lnv);
 /* Switch the precision of the products of later steps (e.g. split-BF16 steps followed by
  * FP64 refinement sweeps).  The current L, E, N and gradients are re-evaluated in the new
  * precision (with electron-number corrections) so the next step starts from consistent
  * values; the search history is reset.  Synchronises. */
 cq_status cq_lnv_set_precision(cq_lnv *lnv, cq_precision prec);
-/* Current E, N, mu and RMS gradient (as after the last evaluation). */
+/* Current E, N, mu and RMS gradient (as after the last evaluation), one report per cell. */
 cq_status cq_lnv_state(const cq_lnv *lnv, cq_lnv_report *report_host);
 /* Useful flops of one LNV step's products (full evaluation + two trial points). */
 cq_status cq_lnv_step_flops(cq_lnv *lnv, double *flops_host);

@@ -69,9 +69,9 @@ SIGNATURES = {
     "cq_mcweeny_step": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "cq_lnv_create": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _d, ctypes.c_int,
                             ctypes.POINTER(_vp)]),
-    "cq_lnv_step": (_st, [_vp, ctypes.POINTER(LnvReport)]),
+    "cq_lnv_step": (_st, [_vp, _vp]),
     "cq_lnv_set_precision": (_st, [_vp, ctypes.c_int]),
-    "cq_lnv_state": (_st, [_vp, ctypes.POINTER(LnvReport)]),
+    "cq_lnv_state": (_st, [_vp, _vp]),
     "cq_lnv_step_flops": (_st, [_vp, ctypes.POINTER(_d)]),
     "cq_lnv_destroy": (None, [_vp]),
     "cq_kernel_launches": (_i64, []),
@@ -79,7 +79,23 @@ SIGNATURES = {
     "cq_ctx_kernel_stats": (_st, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_d),
                                   ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "cq_peak_fp64": (_st, [_vp, ctypes.POINTER(_d)]),
+    "cq_pattern_build_batch": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp,
+                                     ctypes.POINTER(_vp)]),
+    "cq_pattern_cells": (_i32, [_vp]),
+    "cq_pm_guess_cells": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "cq_lnv_create_cells": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                  ctypes.POINTER(_vp)]),
+    "cq_lnv_cells": (_i32, [_vp]),
 }
+
+
+def _host_f64(values):
+    arr = (ctypes.c_double * len(values))(*[float(v) for v in values])
+    return arr
+
+
+def _host_i32(values):
+    return (ctypes.c_int32 * len(values))(*[int(v) for v in values])
 
 _lib = None
 
@@ -232,20 +248,44 @@ class Context:
     def lnv(self, pS, S, H, pL, L, n_electrons, prec=CQ_FP64) -> "Lnv":
         return Lnv(self, pS, S, H, pL, L, n_electrons, prec)
 
+    # ------------------------------------------------------------ batches
+    def pattern_batch(self, pos, cell_start, boxes, nb, ranges) -> "Pattern":
+        """Pattern over several cells (atoms of cell c: cell_start[c]..cell_start[c+1]-1)."""
+        return Pattern(self, pos, None, nb, None, batch=(cell_start, boxes, ranges))
+
+    def pm_guess_cells(self, pS, S, H, pT, T, pL, L, n_occ):
+        self._check(lib().cq_pm_guess_cells(self.h, pS.h, _ptr(S), _ptr(H), pT.h, _ptr(T),
+                                            pL.h, _ptr(L), _host_f64(n_occ)))
+        return L
+
+    def lnv_cells(self, pS, S, H, pL, L, n_electrons, prec=CQ_FP64) -> "Lnv":
+        return Lnv(self, pS, S, H, pL, L, list(n_electrons), prec)
+
 
 class Pattern:
     """Range-cutoff pattern built on the device by cq_pattern_build."""
 
-    def __init__(self, ctx: Context, pos: torch.Tensor, box, nb: torch.Tensor, rng: float):
+    def __init__(self, ctx: Context, pos: torch.Tensor, box, nb: torch.Tensor, rng,
+                 batch=None):
         self.ctx = ctx
         self._pos, self._nb = pos, nb
-        box_arr = (ctypes.c_double * 3)(*[float(b) for b in box])
         h = ctypes.c_void_p()
-        ctx._check(lib().cq_pattern_build(ctx.h, int(pos.shape[0]), _ptr(pos), box_arr,
-                                          _ptr(nb), float(rng), ctypes.byref(h)))
+        if batch is None:
+            box_arr = (ctypes.c_double * 3)(*[float(b) for b in box])
+            ctx._check(lib().cq_pattern_build(ctx.h, int(pos.shape[0]), _ptr(pos), box_arr,
+                                              _ptr(nb), float(rng), ctypes.byref(h)))
+            self.range = float(rng)
+        else:
+            cell_start, boxes, ranges = batch
+            n_cells = len(ranges)
+            flat_boxes = [float(x) for b in boxes for x in b]
+            ctx._check(lib().cq_pattern_build_batch(
+                ctx.h, n_cells, _host_i32(cell_start), _ptr(pos), _host_f64(flat_boxes),
+                _ptr(nb), _host_f64(ranges), ctypes.byref(h)))
+            self.range = [float(r) for r in ranges]
         self.h = h
         ctx._children.add(self)
-        self.range = float(rng)
+        self.n_cells = int(lib().cq_pattern_cells(h))
         nbk, nv = ctypes.c_int64(), ctypes.c_int64()
         lib().cq_pattern_info(h, ctypes.byref(nbk), ctypes.byref(nv))
         self.n_blocks, self.n_values = int(nbk.value), int(nv.value)
@@ -277,29 +317,41 @@ class Pattern:
 
 
 class Lnv:
-    """LNV minimisation state (cq_lnv_create / cq_lnv_step)."""
+    """LNV minimisation state (cq_lnv_create(_cells) / cq_lnv_step).
+
+    For a single cell, step() and state() return one dict; for a batch (n_electrons given
+    as a list) they return one dict per cell."""
 
     def __init__(self, ctx, pS, S, H, pL, L, n_electrons, prec=CQ_FP64):
         self.ctx = ctx
         self._keep = (pS, S, H, pL, L)
         h = ctypes.c_void_p()
-        ctx._check(lib().cq_lnv_create(ctx.h, pS.h, _ptr(S), _ptr(H), pL.h, _ptr(L),
-                                       float(n_electrons), int(prec), ctypes.byref(h)))
+        self.batch = isinstance(n_electrons, (list, tuple))
+        if self.batch:
+            ctx._check(lib().cq_lnv_create_cells(ctx.h, pS.h, _ptr(S), _ptr(H), pL.h, _ptr(L),
+                                                 _host_f64(n_electrons), int(prec),
+                                                 ctypes.byref(h)))
+        else:
+            ctx._check(lib().cq_lnv_create(ctx.h, pS.h, _ptr(S), _ptr(H), pL.h, _ptr(L),
+                                           float(n_electrons), int(prec), ctypes.byref(h)))
         self.h = h
         ctx._children.add(self)
+        self.n_cells = int(lib().cq_lnv_cells(h))
 
-    def step(self) -> dict:
-        rep = LnvReport()
-        self.ctx._check(lib().cq_lnv_step(self.h, ctypes.byref(rep)))
-        return rep.as_dict()
+    def _reports(self, fn):
+        reps = (LnvReport * self.n_cells)()
+        self.ctx._check(fn(self.h, reps))
+        out = [r.as_dict() for r in reps]
+        return out if self.batch else out[0]
+
+    def step(self):
+        return self._reports(lib().cq_lnv_step)
 
     def set_precision(self, prec: int):
         self.ctx._check(lib().cq_lnv_set_precision(self.h, int(prec)))
 
-    def state(self) -> dict:
-        rep = LnvReport()
-        self.ctx._check(lib().cq_lnv_state(self.h, ctypes.byref(rep)))
-        return rep.as_dict()
+    def state(self):
+        return self._reports(lib().cq_lnv_state)
 
     def step_flops(self) -> float:
         f = ctypes.c_double()

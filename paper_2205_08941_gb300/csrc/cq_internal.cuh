@@ -14,6 +14,8 @@
 
 #define CQ_MAX_NB 16          // largest orbital count per atom on the device path
 #define CQ_ROW_CAP 8192       // largest number of blocks in one pattern row
+#define CQ_RED_SLOTS 8192     // device scalar slots (8 per cell for up to 1024 cells)
+#define CQ_MAX_CELLS 1024
 
 struct cq_ctx;
 
@@ -39,6 +41,13 @@ struct Geometry {
     int64_t n_orb = 0;
     int uniform_nb = 0;             // orbital count if every atom has the same, else 0
     DevBuf pos, nb;                 // device copies
+    // batches: n_cells independent periodic cells, atoms of cell c = [cell_start[c],
+    // cell_start[c+1]), each with its own box (boxes[3c..3c+2]); one cell otherwise
+    int n_cells = 1;
+    std::vector<int32_t> cell_start;  // n_cells + 1
+    std::vector<double> boxes;        // 3 * n_cells
+    std::vector<int64_t> cell_orb;    // orbitals per cell
+    DevBuf cell_of, boxes_dev, cell_start_dev;
 };
 
 // (i, k, j) task list of mask_{P_C}(A.B), sorted by C block then k ascending.
@@ -68,6 +77,12 @@ struct cq_pattern {
     DevBuf transpose;                // int64 [n_blocks]
     std::vector<int64_t> row_ptr_host;
     bool owned_by_ctx = false;
+    // per-cell range and the block / value segments of each cell (contiguous, since the
+    // cells' atoms are)
+    std::vector<double> ranges;
+    std::vector<int64_t> seg_blk, seg_val, seg_scalars;  // n_cells + 1 / n_cells
+    DevBuf seg_blk_dev, seg_val_dev;
+    int n_cells() const { return (int)ranges.size(); }
 };
 
 struct cq_ctx {
@@ -84,7 +99,7 @@ struct cq_ctx {
     double *host_out = nullptr;      // pinned host scalars
     std::map<std::tuple<uint64_t, uint64_t, uint64_t>, std::unique_ptr<TaskList>> tasks;
     std::map<std::tuple<uint64_t, uint64_t, int>, std::unique_ptr<DevBuf>> maps;
-    std::map<std::pair<uint64_t, double>, cq_pattern *> derived;
+    std::map<std::pair<uint64_t, std::vector<double>>, cq_pattern *> derived;
     std::map<std::string, std::unique_ptr<DevBuf>> scratch;
     std::vector<cq_pattern *> live_patterns;
     std::vector<cq_lnv *> live_lnv;
@@ -115,10 +130,12 @@ cq_status cq_scan_i64(cq_ctx *ctx, const int64_t *in, int64_t *out, int64_t n);
 cq_status cq_read_flag(cq_ctx *ctx, int32_t *flag);
 
 // ---------------------------------------------------------------- patterns (pattern.cu)
-cq_status cq_pattern_build_geo(cq_ctx *ctx, std::shared_ptr<Geometry> geo, double range,
-                               cq_pattern **out);
-// Pattern of the same geometry at another range, owned and cached by the context.
-cq_status cq_pattern_derived(cq_ctx *ctx, const cq_pattern *base, double range,
+cq_status cq_pattern_build_geo(cq_ctx *ctx, std::shared_ptr<Geometry> geo,
+                               const std::vector<double> &ranges, cq_pattern **out);
+// Pattern of the same geometry with per-cell range ca*range_a[c] + cb*range_b[c], owned and
+// cached by the context.
+cq_status cq_pattern_derived(cq_ctx *ctx, const cq_pattern *base, double ca,
+                             const cq_pattern *pa, double cb, const cq_pattern *pb,
                              cq_pattern **out);
 bool cq_same_atoms(const cq_pattern *a, const cq_pattern *b);
 
@@ -162,6 +179,20 @@ cq_status cq_set_identity(cq_ctx *ctx, const cq_pattern *p, double *M, double s)
 cq_status cq_lnv_gradients(cq_ctx *ctx, const cq_pattern *pL, const cq_pattern *pU,
                            const double *Z, const double *U, const double *R1,
                            const double *R2, const double *R3, double *GE, double *GN);
+
+// ---------------------------------------------------------------- per-cell (batches)
+// One result per cell into red_out[slot + c] (n_cells > 1; contiguous segments).
+cq_status cq_trace_seg_dev(cq_ctx *ctx, const cq_pattern *pA, const double *A,
+                           const cq_pattern *pB, const double *B, int slot);
+cq_status cq_dot_seg_dev(cq_ctx *ctx, const cq_pattern *p, const double *A, const double *B,
+                         int slot);
+// per cell: [slot + 3c] = min(centre - radius), [+1] = max(centre + radius), [+2] = max |row|
+cq_status cq_row_bounds_seg_dev(cq_ctx *ctx, const cq_pattern *p, const double *M, int slot);
+// y <- a[c]*x + b[c]*y on each cell's values (coefficients copied from the host)
+cq_status cq_axpby_seg(cq_ctx *ctx, const cq_pattern *p, const double *a, const double *x,
+                       const double *b, double *y);
+// M <- s[c] * I on each cell's diagonal blocks, zero elsewhere
+cq_status cq_set_identity_seg(cq_ctx *ctx, const cq_pattern *p, double *M, const double *s);
 
 // Launch-count bookkeeping (kernels this library launched; read by the bench).
 void cq_count_launch(int64_t n = 1);

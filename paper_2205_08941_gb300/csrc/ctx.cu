@@ -216,13 +216,14 @@ extern "C" cq_status cq_ctx_create(int device, void *cuda_stream, cq_ctx **out)
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (cq_alloc(ctx, ctx->flag, 16) != CQ_OK || cq_alloc(ctx, ctx->red_out, 64 * 8) != CQ_OK ||
-        cudaMallocHost(&ctx->host_out, 64 * sizeof(double)) != cudaSuccess) {
+    if (cq_alloc(ctx, ctx->flag, 16) != CQ_OK ||
+        cq_alloc(ctx, ctx->red_out, CQ_RED_SLOTS * 8) != CQ_OK ||
+        cudaMallocHost(&ctx->host_out, CQ_RED_SLOTS * sizeof(double)) != cudaSuccess) {
         delete ctx;
         return CQ_ERR_NOMEM;
     }
     cudaMemsetAsync(ctx->flag.ptr, 0, 16, ctx->stream);
-    cudaMemsetAsync(ctx->red_out.ptr, 0, 64 * 8, ctx->stream);
+    cudaMemsetAsync(ctx->red_out.ptr, 0, CQ_RED_SLOTS * 8, ctx->stream);
     *out = ctx;
     return CQ_OK;
 }
@@ -321,13 +322,78 @@ extern "C" cq_status cq_pattern_build(cq_ctx *ctx, int32_t n_atoms, const double
                     cudaMemcpyDeviceToDevice, ctx->stream);
     cudaMemcpyAsync(geo->nb.ptr, nb_dev, sizeof(int32_t) * n_atoms, cudaMemcpyDeviceToDevice,
                     ctx->stream);
+    geo->n_cells = 1;
+    geo->cell_start = {0, n_atoms};
+    geo->boxes.assign(box_host, box_host + 3);
+    geo->cell_orb = {geo->n_orb};
     cq_pattern *p = nullptr;
-    st = cq_pattern_build_geo(ctx, geo, range, &p);
+    st = cq_pattern_build_geo(ctx, geo, std::vector<double>{range}, &p);
     if (st != CQ_OK) return st;
     ctx->live_patterns.push_back(p);
     *out = p;
     return CQ_OK;
 }
+
+extern "C" cq_status cq_pattern_build_batch(cq_ctx *ctx, int32_t n_cells,
+                                            const int32_t *cell_start_host,
+                                            const double *pos_dev, const double *boxes_host,
+                                            const int32_t *nb_dev, const double *ranges_host,
+                                            cq_pattern **out)
+{
+    if (!ctx || !out) return CQ_ERR_INVALID;
+    *out = nullptr;
+    if (n_cells < 1 || !cell_start_host || !boxes_host || !ranges_host || !pos_dev || !nb_dev)
+        return cq_fail(ctx, CQ_ERR_INVALID, "pattern_build_batch: bad argument");
+    if (cell_start_host[0] != 0)
+        return cq_fail(ctx, CQ_ERR_INVALID, "pattern_build_batch: cell_start[0] must be 0");
+    for (int c = 0; c < n_cells; ++c) {
+        if (cell_start_host[c + 1] <= cell_start_host[c])
+            return cq_fail(ctx, CQ_ERR_INVALID, "pattern_build_batch: empty or unordered cell");
+        if (!(ranges_host[c] >= 0.0) || !std::isfinite(ranges_host[c]))
+            return cq_fail(ctx, CQ_ERR_INVALID, "pattern_build_batch: bad range");
+        for (int d = 0; d < 3; ++d)
+            if (!(boxes_host[3 * c + d] > 0.0) || !std::isfinite(boxes_host[3 * c + d]))
+                return cq_fail(ctx, CQ_ERR_INVALID, "pattern_build_batch: box lengths must be > 0");
+    }
+    const int32_t n_atoms = cell_start_host[n_cells];
+    // geometry of the first cell's box for the shared fields; per-cell data below
+    cq_pattern *tmp = nullptr;
+    cq_status st = cq_pattern_build(ctx, n_atoms, pos_dev, boxes_host, nb_dev, 0.0, &tmp);
+    if (st != CQ_OK) return st;
+    std::shared_ptr<Geometry> geo = tmp->geo;
+    cq_pattern_destroy(tmp);
+    geo->id = ctx->next_id++;
+    geo->n_cells = n_cells;
+    geo->cell_start.assign(cell_start_host, cell_start_host + n_cells + 1);
+    geo->boxes.assign(boxes_host, boxes_host + 3 * n_cells);
+    geo->cell_orb.assign(n_cells, 0);
+    std::vector<int32_t> cell_of(n_atoms);
+    for (int c = 0; c < n_cells; ++c)
+        for (int i = cell_start_host[c]; i < cell_start_host[c + 1]; ++i) {
+            cell_of[i] = c;
+            geo->cell_orb[c] += geo->nb_host[i];
+        }
+    if ((st = cq_alloc(ctx, geo->cell_of, sizeof(int32_t) * n_atoms)) != CQ_OK ||
+        (st = cq_alloc(ctx, geo->boxes_dev, sizeof(double) * 3 * n_cells)) != CQ_OK ||
+        (st = cq_alloc(ctx, geo->cell_start_dev, sizeof(int32_t) * (n_cells + 1))) != CQ_OK)
+        return st;
+    cudaMemcpyAsync(geo->cell_of.ptr, cell_of.data(), sizeof(int32_t) * n_atoms,
+                    cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(geo->boxes_dev.ptr, geo->boxes.data(), sizeof(double) * 3 * n_cells,
+                    cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(geo->cell_start_dev.ptr, geo->cell_start.data(),
+                    sizeof(int32_t) * (n_cells + 1), cudaMemcpyHostToDevice, ctx->stream);
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "batch geometry")) != CQ_OK)
+        return st;
+    cq_pattern *p = nullptr;
+    st = cq_pattern_build_geo(ctx, geo, std::vector<double>(ranges_host, ranges_host + n_cells), &p);
+    if (st != CQ_OK) return st;
+    ctx->live_patterns.push_back(p);
+    *out = p;
+    return CQ_OK;
+}
+
+extern "C" int32_t cq_pattern_cells(const cq_pattern *p) { return p ? p->n_cells() : 0; }
 
 extern "C" cq_status cq_pattern_info(const cq_pattern *p, int64_t *n_blocks, int64_t *n_values)
 {

@@ -2,6 +2,12 @@
 // Li-Nunes-Vanderbilt minimisation.  All matrix work runs in the library's kernels; the
 // host only does scalar arithmetic between phases (chemical potential, CG coefficients, the
 // cubic line search) on FP64 scalars read back from device reductions.
+//
+// Batches (patterns over several independent cells): every scalar is per cell -- traces,
+// dots and Gershgorin bounds are segmented reductions over the cells' contiguous blocks,
+// and every update L += alpha_c D uses the cell's own coefficient -- while each block
+// product covers all cells in one launch.  A single cell uses the unsegmented kernels.
+#include <algorithm>
 #include <cmath>
 
 #include "cq_internal.cuh"
@@ -34,6 +40,46 @@ cq_status bsmm(cq_ctx *ctx, double alpha, const cq_pattern *pA, const double *A,
         if (_st != CQ_OK) return _st;      \
     } while (0)
 
+// Quantity q of a per-cell reduction lands in slots [q*nc, q*nc + nc).
+cq_status dot_q(cq_ctx *ctx, const cq_pattern *p, const double *a, const double *b, int q)
+{
+    const int nc = p->n_cells();
+    return nc == 1 ? cq_dot_dev(ctx, p, a, b, q) : cq_dot_seg_dev(ctx, p, a, b, q * nc);
+}
+
+cq_status trace_q(cq_ctx *ctx, const cq_pattern *pA, const double *A, const cq_pattern *pB,
+                  const double *B, int q)
+{
+    const int nc = pA->n_cells();
+    return nc == 1 ? cq_trace_dev(ctx, pA, A, pB, B, q)
+                   : cq_trace_seg_dev(ctx, pA, A, pB, B, q * nc);
+}
+
+// nq quantities of nc cells: out[q][c]
+cq_status fetch_q(cq_ctx *ctx, int nc, int nq, std::vector<std::vector<double>> &out)
+{
+    std::vector<double> flat(nq * nc);
+    CQ_TRY(cq_fetch(ctx, 0, nq * nc, flat.data()));
+    out.assign(nq, std::vector<double>(nc));
+    for (int q = 0; q < nq; ++q)
+        for (int c = 0; c < nc; ++c) out[q][c] = flat[q * nc + c];
+    return CQ_OK;
+}
+
+// y <- a_c x + b_c y on every cell of p
+cq_status axpby_c(cq_ctx *ctx, const cq_pattern *p, const std::vector<double> &a,
+                  const double *x, const std::vector<double> &b, double *y)
+{
+    if (p->n_cells() == 1) return cq_axpby(ctx, p->n_values, a[0], x, b[0], y);
+    return cq_axpby_seg(ctx, p, a.data(), x, b.data(), y);
+}
+
+cq_status copy_vals(cq_ctx *ctx, double *dst, const double *src, int64_t n)
+{
+    return cq_check_cuda(ctx, cudaMemcpyAsync(dst, src, sizeof(double) * n,
+                                              cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- Hotelling
@@ -43,11 +89,23 @@ extern "C" cq_status cq_hotelling_init(cq_ctx *ctx, const cq_pattern *pS, const 
 {
     if (!ctx || !S || !T) return CQ_ERR_INVALID;
     CQ_TRY(same_ctx(ctx, pS, pT));
-    CQ_TRY(cq_row_bounds_dev(ctx, pS, S, 0));
-    double b[3];
-    CQ_TRY(cq_fetch(ctx, 0, 3, b));
-    if (!(b[2] > 0.0)) return cq_fail(ctx, CQ_ERR_NUMERIC, "hotelling_init: S has a zero row");
-    return cq_set_identity(ctx, pT, T, 1.0 / b[2]);
+    const int nc = pS->n_cells();
+    if (nc == 1) {
+        CQ_TRY(cq_row_bounds_dev(ctx, pS, S, 0));
+        double b[3];
+        CQ_TRY(cq_fetch(ctx, 0, 3, b));
+        if (!(b[2] > 0.0)) return cq_fail(ctx, CQ_ERR_NUMERIC, "hotelling_init: S has a zero row");
+        return cq_set_identity(ctx, pT, T, 1.0 / b[2]);
+    }
+    CQ_TRY(cq_row_bounds_seg_dev(ctx, pS, S, 0));
+    std::vector<double> b(3 * nc), inv(nc);
+    CQ_TRY(cq_fetch(ctx, 0, 3 * nc, b.data()));
+    for (int c = 0; c < nc; ++c) {
+        if (!(b[3 * c + 2] > 0.0))
+            return cq_fail(ctx, CQ_ERR_NUMERIC, "hotelling_init: S has a zero row");
+        inv[c] = 1.0 / b[3 * c + 2];
+    }
+    return cq_set_identity_seg(ctx, pT, T, inv.data());
 }
 
 extern "C" cq_status cq_hotelling_step(cq_ctx *ctx, const cq_pattern *pS, const double *S,
@@ -56,7 +114,7 @@ extern "C" cq_status cq_hotelling_step(cq_ctx *ctx, const cq_pattern *pS, const 
     if (!ctx || !S || !T) return CQ_ERR_INVALID;
     CQ_TRY(same_ctx(ctx, pS, pT));
     cq_pattern *pV = nullptr;
-    CQ_TRY(cq_pattern_derived(ctx, pS, pS->range + pT->range, &pV));
+    CQ_TRY(cq_pattern_derived(ctx, pS, 1.0, pS, 1.0, pT, &pV));
     void *v, *w;
     CQ_TRY(cq_scratch(ctx, "hot_V", sizeof(double) * pV->n_values, &v));
     CQ_TRY(cq_scratch(ctx, "hot_W", sizeof(double) * pT->n_values, &w));
@@ -73,31 +131,68 @@ extern "C" cq_status cq_hotelling_step(cq_ctx *ctx, const cq_pattern *pS, const 
 
 // ---------------------------------------------------------------- PM start, McWeeny
 
-extern "C" cq_status cq_pm_guess(cq_ctx *ctx, const cq_pattern *pS, const double *S,
-                                 const double *H, const cq_pattern *pT, const double *T,
-                                 const cq_pattern *pL, double *L, double n_occ)
+extern "C" cq_status cq_pm_guess_cells(cq_ctx *ctx, const cq_pattern *pS, const double *S,
+                                       const double *H, const cq_pattern *pT, const double *T,
+                                       const cq_pattern *pL, double *L,
+                                       const double *n_occ_host)
 {
-    if (!ctx || !S || !H || !T || !L) return CQ_ERR_INVALID;
+    if (!ctx || !S || !H || !T || !L || !n_occ_host) return CQ_ERR_INVALID;
     CQ_TRY(same_ctx(ctx, pS, pT));
     CQ_TRY(same_ctx(ctx, pS, pL));
-    const double n_orb = (double)pS->geo->n_orb;
-    if (!(n_occ > 0.0 && n_occ < n_orb))
-        return cq_fail(ctx, CQ_ERR_INVALID, "pm_guess: n_occ outside (0, N)");
+    const int nc = pS->n_cells();
+    for (int c = 0; c < nc; ++c) {
+        const double n_orb = (double)pS->geo->cell_orb[c];
+        if (!(n_occ_host[c] > 0.0 && n_occ_host[c] < n_orb))
+            return cq_fail(ctx, CQ_ERR_INVALID, "pm_guess: n_occ outside (0, N)");
+    }
     cq_pattern *pX = nullptr;
-    CQ_TRY(cq_pattern_derived(ctx, pS, pT->range + pS->range, &pX));
+    CQ_TRY(cq_pattern_derived(ctx, pS, 1.0, pT, 1.0, pS, &pX));
     void *th;
     CQ_TRY(cq_scratch(ctx, "pm_TH", sizeof(double) * pX->n_values, &th));
     double *TH = (double *)th;
     CQ_TRY(bsmm(ctx, 1.0, pT, T, pS, H, 0.0, pX, TH, CQ_FP64));
-    CQ_TRY(cq_trace_dev(ctx, pT, T, pS, H, 0));
-    CQ_TRY(cq_row_bounds_dev(ctx, pX, TH, 1));
-    double sc[4];
-    CQ_TRY(cq_fetch(ctx, 0, 4, sc));
-    const double mu = sc[0] / n_orb;
-    const double h_min = sc[1], h_max = sc[2];
-    const double lam = std::fmin(n_occ / (h_max - mu), (n_orb - n_occ) / (mu - h_min));
-    CQ_TRY(bsmm(ctx, -lam / n_orb, pX, TH, pT, T, 0.0, pL, L, CQ_FP64));
-    return cq_gather(ctx, pT, T, pL, L, 0, lam * mu / n_orb + n_occ / n_orb, 1.0);
+    if (nc == 1) {
+        const double n_orb = (double)pS->geo->n_orb, n_occ = n_occ_host[0];
+        CQ_TRY(cq_trace_dev(ctx, pT, T, pS, H, 0));
+        CQ_TRY(cq_row_bounds_dev(ctx, pX, TH, 1));
+        double sc[4];
+        CQ_TRY(cq_fetch(ctx, 0, 4, sc));
+        const double mu = sc[0] / n_orb;
+        const double h_min = sc[1], h_max = sc[2];
+        const double lam = std::fmin(n_occ / (h_max - mu), (n_orb - n_occ) / (mu - h_min));
+        CQ_TRY(bsmm(ctx, -lam / n_orb, pX, TH, pT, T, 0.0, pL, L, CQ_FP64));
+        return cq_gather(ctx, pT, T, pL, L, 0, lam * mu / n_orb + n_occ / n_orb, 1.0);
+    }
+    CQ_TRY(cq_trace_seg_dev(ctx, pT, T, pS, H, 0));
+    CQ_TRY(cq_row_bounds_seg_dev(ctx, pX, TH, nc));
+    std::vector<double> sc(4 * nc);
+    CQ_TRY(cq_fetch(ctx, 0, 4 * nc, sc.data()));
+    std::vector<double> a(nc), b(nc), one(nc, 1.0), zero(nc, 0.0);
+    for (int c = 0; c < nc; ++c) {
+        const double n_orb = (double)pS->geo->cell_orb[c], n_occ = n_occ_host[c];
+        const double mu = sc[c] / n_orb;
+        const double h_min = sc[nc + 3 * c], h_max = sc[nc + 3 * c + 1];
+        const double lam = std::fmin(n_occ / (h_max - mu), (n_orb - n_occ) / (mu - h_min));
+        a[c] = -lam / n_orb;
+        b[c] = lam * mu / n_orb + n_occ / n_orb;
+    }
+    // L = a_c THT + b_c T on P_L
+    CQ_TRY(bsmm(ctx, 1.0, pX, TH, pT, T, 0.0, pL, L, CQ_FP64));
+    CQ_TRY(axpby_c(ctx, pL, a, L, zero, L));
+    void *tl;
+    CQ_TRY(cq_scratch(ctx, "pm_TL", sizeof(double) * pL->n_values, &tl));
+    CQ_TRY(cq_gather(ctx, pT, T, pL, (double *)tl, 0, 1.0, 0.0));
+    return axpby_c(ctx, pL, b, (double *)tl, one, L);
+}
+
+extern "C" cq_status cq_pm_guess(cq_ctx *ctx, const cq_pattern *pS, const double *S,
+                                 const double *H, const cq_pattern *pT, const double *T,
+                                 const cq_pattern *pL, double *L, double n_occ)
+{
+    if (!ctx || !pS) return CQ_ERR_INVALID;
+    if (pS->n_cells() != 1)
+        return cq_fail(ctx, CQ_ERR_INVALID, "pm_guess: batch patterns need cq_pm_guess_cells");
+    return cq_pm_guess_cells(ctx, pS, S, H, pT, T, pL, L, &n_occ);
 }
 
 extern "C" cq_status cq_mcweeny_step(cq_ctx *ctx, const cq_pattern *pS, const double *S,
@@ -106,9 +201,9 @@ extern "C" cq_status cq_mcweeny_step(cq_ctx *ctx, const cq_pattern *pS, const do
     if (!ctx || !S || !L) return CQ_ERR_INVALID;
     CQ_TRY(same_ctx(ctx, pS, pL));
     cq_pattern *pX, *pU, *p2L;
-    CQ_TRY(cq_pattern_derived(ctx, pS, pL->range + pS->range, &pX));
-    CQ_TRY(cq_pattern_derived(ctx, pS, 2.0 * pS->range + pL->range, &pU));
-    CQ_TRY(cq_pattern_derived(ctx, pS, 2.0 * pL->range, &p2L));
+    CQ_TRY(cq_pattern_derived(ctx, pS, 1.0, pL, 1.0, pS, &pX));
+    CQ_TRY(cq_pattern_derived(ctx, pS, 2.0, pS, 1.0, pL, &pU));
+    CQ_TRY(cq_pattern_derived(ctx, pS, 2.0, pL, 0.0, pL, &p2L));
     void *x, *u, *m, *o;
     CQ_TRY(cq_scratch(ctx, "mw_X", sizeof(double) * pX->n_values, &x));
     CQ_TRY(cq_scratch(ctx, "mw_U", sizeof(double) * pU->n_values, &u));
@@ -120,9 +215,7 @@ extern "C" cq_status cq_mcweeny_step(cq_ctx *ctx, const cq_pattern *pS, const do
     CQ_TRY(bsmm(ctx, 1.0, pL, L, pU, U, 0.0, p2L, M, CQ_FP64));
     CQ_TRY(bsmm(ctx, 3.0, pX, X, pL, L, 0.0, pL, O, CQ_FP64));
     CQ_TRY(bsmm(ctx, -2.0, p2L, M, pL, L, 1.0, pL, O, CQ_FP64));
-    return cq_check_cuda(ctx, cudaMemcpyAsync(L, O, sizeof(double) * pL->n_values,
-                                              cudaMemcpyDeviceToDevice, ctx->stream),
-                         "mcweeny copy");
+    return copy_vals(ctx, L, O, pL->n_values);
 }
 
 // ---------------------------------------------------------------- LNV
@@ -133,24 +226,24 @@ struct cq_lnv {
     cq_pattern *pX = nullptr, *pU = nullptr;
     const double *S = nullptr, *H = nullptr;
     double *L = nullptr;
-    double ne = 0.0;
+    int nc = 1;
+    std::vector<double> ne, E, N, alpha_prev;
+    std::vector<int> n_corr_initial;
     cq_precision prec = CQ_FP64;
     DevBuf X, Y, U, Z, R1, R2, R3, GE, GN, G, Gp, D, Dp, Lt;
-    double E = 0.0, N = 0.0;
     bool have_prev = false, have_alpha = false;
-    double alpha_prev = 0.0;
     double n_tol = 1e-10;
     double n_tol_split = 1e-9;
     int max_corr = 5;
     double flops = 0.0;
     int products = 0;
-    int n_corr_initial = 0;
 };
 
 namespace {
 
-// E and N at Lsrc from the five products a trial point needs (X, Y, U, R1, R3).
-cq_status lnv_energy_number(cq_lnv *s, const double *Lsrc, double *E, double *N)
+// E and N (per cell) at Lsrc from the five products a trial point needs (X, Y, U, R1, R3).
+cq_status lnv_energy_number(cq_lnv *s, const double *Lsrc, std::vector<double> &E,
+                            std::vector<double> &N)
 {
     cq_ctx *ctx = s->ctx;
     double *X = s->X.as<double>(), *Y = s->Y.as<double>(), *U = s->U.as<double>();
@@ -161,14 +254,18 @@ cq_status lnv_energy_number(cq_lnv *s, const double *Lsrc, double *E, double *N)
     CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, Y, 0.0, s->pL, R1, s->prec, &s->flops));
     CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, X, 0.0, s->pL, R3, s->prec, &s->flops));
     s->products += 5;
-    CQ_TRY(cq_trace_dev(ctx, s->pX, X, s->pX, Y, 0));
-    CQ_TRY(cq_trace_dev(ctx, s->pL, Lsrc, s->pL, R1, 1));
-    CQ_TRY(cq_trace_dev(ctx, s->pX, X, s->pX, X, 2));
-    CQ_TRY(cq_trace_dev(ctx, s->pL, Lsrc, s->pL, R3, 3));
-    double t[4];
-    CQ_TRY(cq_fetch(ctx, 0, 4, t));
-    *E = 2.0 * (3.0 * t[0] - 2.0 * t[1]);
-    *N = 2.0 * (3.0 * t[2] - 2.0 * t[3]);
+    CQ_TRY(trace_q(ctx, s->pX, X, s->pX, Y, 0));
+    CQ_TRY(trace_q(ctx, s->pL, Lsrc, s->pL, R1, 1));
+    CQ_TRY(trace_q(ctx, s->pX, X, s->pX, X, 2));
+    CQ_TRY(trace_q(ctx, s->pL, Lsrc, s->pL, R3, 3));
+    std::vector<std::vector<double>> t;
+    CQ_TRY(fetch_q(ctx, s->nc, 4, t));
+    E.resize(s->nc);
+    N.resize(s->nc);
+    for (int c = 0; c < s->nc; ++c) {
+        E[c] = 2.0 * (3.0 * t[0][c] - 2.0 * t[1][c]);
+        N[c] = 2.0 * (3.0 * t[2][c] - 2.0 * t[3][c]);
+    }
     return CQ_OK;
 }
 
@@ -183,12 +280,13 @@ cq_status lnv_eval_n(cq_lnv *s)
     CQ_TRY(bsmm(ctx, 1.0, s->pS, s->S, s->pX, X, 0.0, s->pU, U, s->prec, &s->flops));
     CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, X, 0.0, s->pL, R3, s->prec, &s->flops));
     s->products += 3;
-    CQ_TRY(cq_trace_dev(ctx, s->pX, X, s->pX, X, 2));
-    CQ_TRY(cq_trace_dev(ctx, s->pL, s->L, s->pL, R3, 3));
+    CQ_TRY(trace_q(ctx, s->pX, X, s->pX, X, 0));
+    CQ_TRY(trace_q(ctx, s->pL, s->L, s->pL, R3, 1));
     CQ_TRY(cq_lnv_gradient_n(ctx, s->pL, s->pU, U, R3, s->GN.as<double>()));
-    double t[2];
-    CQ_TRY(cq_fetch(ctx, 2, 2, t));
-    s->N = 2.0 * (3.0 * t[0] - 2.0 * t[1]);
+    std::vector<std::vector<double>> t;
+    CQ_TRY(fetch_q(ctx, s->nc, 2, t));
+    s->N.resize(s->nc);
+    for (int c = 0; c < s->nc; ++c) s->N[c] = 2.0 * (3.0 * t[0][c] - 2.0 * t[1][c]);
     return CQ_OK;
 }
 
@@ -204,57 +302,77 @@ cq_status lnv_eval_rest(cq_lnv *s)
     CQ_TRY(bsmm(ctx, 1.0, s->pS, s->S, s->pX, Y, 0.0, s->pU, Z, s->prec, &s->flops));
     CQ_TRY(bsmm(ctx, 1.0, s->pU, Z, s->pX, X, 0.0, s->pL, R2, s->prec, &s->flops));
     s->products += 4;
-    CQ_TRY(cq_trace_dev(ctx, s->pX, X, s->pX, Y, 0));
-    CQ_TRY(cq_trace_dev(ctx, s->pL, s->L, s->pL, R1, 1));
+    CQ_TRY(trace_q(ctx, s->pX, X, s->pX, Y, 0));
+    CQ_TRY(trace_q(ctx, s->pL, s->L, s->pL, R1, 1));
     CQ_TRY(cq_lnv_gradient_e(ctx, s->pL, s->pU, Z, R1, R2, s->GE.as<double>()));
-    double t[2];
-    CQ_TRY(cq_fetch(ctx, 0, 2, t));
-    s->E = 2.0 * (3.0 * t[0] - 2.0 * t[1]);
+    std::vector<std::vector<double>> t;
+    CQ_TRY(fetch_q(ctx, s->nc, 2, t));
+    s->E.resize(s->nc);
+    for (int c = 0; c < s->nc; ++c) s->E[c] = 2.0 * (3.0 * t[0][c] - 2.0 * t[1][c]);
     return CQ_OK;
 }
 
-cq_status dot_l(cq_lnv *s, const double *a, const double *b, double *out)
+// <a, b> per cell
+cq_status dots(cq_lnv *s, const double *a, const double *b, std::vector<double> &out)
 {
-    CQ_TRY(cq_dot_dev(s->ctx, s->pL, a, b, 0));
-    return cq_fetch(s->ctx, 0, 1, out);
+    CQ_TRY(dot_q(s->ctx, s->pL, a, b, 0));
+    std::vector<std::vector<double>> t;
+    CQ_TRY(fetch_q(s->ctx, s->nc, 1, t));
+    out = t[0];
+    return CQ_OK;
 }
 
 // Evaluate at s->L with the electron-number corrections in between: N and G_N first, then
 // L += ((N_e - N)/<G_N,G_N>) G_N (at most max_corr times) while |N - N_e| > n_tol N_e, each
 // followed by N and G_N at the corrected L, and finally E and G_E at the last L.  The
 // iterates and decisions are those of "full evaluation, then correct and re-evaluate";
-// only the E half of the intermediate evaluations (never used) is skipped.
-cq_status lnv_evaluate_corrected(cq_lnv *s, int *count)
+// only the E half of the intermediate evaluations (never used) is skipped.  In a batch a
+// cell within tolerance receives a zero correction.
+cq_status lnv_evaluate_corrected(cq_lnv *s, std::vector<int> &count)
 {
     CQ_TRY(lnv_eval_n(s));
-    int k = 0;
+    count.assign(s->nc, 0);
     // split-BF16 products resolve N to ~1e-10 relative, so their corrections stop at 1e-9
     const double tol = s->prec == CQ_SPLIT_BF16X3 ? s->n_tol_split : s->n_tol;
-    while (std::fabs(s->N - s->ne) > tol * s->ne && k < s->max_corr) {
-        double gn2;
-        CQ_TRY(dot_l(s, s->GN.as<double>(), s->GN.as<double>(), &gn2));
-        CQ_TRY(cq_axpby(s->ctx, s->pL->n_values, (s->ne - s->N) / gn2, s->GN.as<double>(), 1.0,
-                        s->L));
+    for (int k = 0; k < s->max_corr; ++k) {
+        std::vector<bool> need(s->nc);
+        bool any = false;
+        for (int c = 0; c < s->nc; ++c) {
+            need[c] = std::fabs(s->N[c] - s->ne[c]) > tol * s->ne[c];
+            any = any || need[c];
+        }
+        if (!any) break;
+        std::vector<double> gn2;
+        CQ_TRY(dots(s, s->GN.as<double>(), s->GN.as<double>(), gn2));
+        std::vector<double> a(s->nc, 0.0), one(s->nc, 1.0);
+        for (int c = 0; c < s->nc; ++c)
+            if (need[c]) {
+                a[c] = (s->ne[c] - s->N[c]) / gn2[c];
+                count[c] += 1;
+            }
+        CQ_TRY(axpby_c(s->ctx, s->pL, a, s->GN.as<double>(), one, s->L));
         CQ_TRY(lnv_eval_n(s));
-        ++k;
     }
-    *count = k;
     return lnv_eval_rest(s);
 }
 
-// mu = <G_E,G_N>/<G_N,G_N> and G = G_E - mu G_N into s->G; returns <G_N,G_N>.
-cq_status lnv_mu_g(cq_lnv *s, double *mu, double *gn2)
+// mu_c = <G_E,G_N>/<G_N,G_N> and G = G_E - mu_c G_N into s->G; returns <G_N,G_N> per cell.
+cq_status lnv_mu_g(cq_lnv *s, std::vector<double> &mu, std::vector<double> &gn2)
 {
     cq_ctx *ctx = s->ctx;
-    CQ_TRY(cq_dot_dev(ctx, s->pL, s->GE.as<double>(), s->GN.as<double>(), 0));
-    CQ_TRY(cq_dot_dev(ctx, s->pL, s->GN.as<double>(), s->GN.as<double>(), 1));
-    double d[2];
-    CQ_TRY(cq_fetch(ctx, 0, 2, d));
-    *mu = d[0] / d[1];
-    *gn2 = d[1];
-    CQ_TRY(cq_check_cuda(ctx, cudaMemcpyAsync(s->G.ptr, s->GE.ptr, sizeof(double) * s->pL->n_values,
-                                              cudaMemcpyDeviceToDevice, ctx->stream), "copy"));
-    return cq_axpby(ctx, s->pL->n_values, -*mu, s->GN.as<double>(), 1.0, s->G.as<double>());
+    CQ_TRY(dot_q(ctx, s->pL, s->GE.as<double>(), s->GN.as<double>(), 0));
+    CQ_TRY(dot_q(ctx, s->pL, s->GN.as<double>(), s->GN.as<double>(), 1));
+    std::vector<std::vector<double>> d;
+    CQ_TRY(fetch_q(ctx, s->nc, 2, d));
+    mu.resize(s->nc);
+    gn2 = d[1];
+    std::vector<double> neg(s->nc), one(s->nc, 1.0);
+    for (int c = 0; c < s->nc; ++c) {
+        mu[c] = d[0][c] / d[1][c];
+        neg[c] = -mu[c];
+    }
+    CQ_TRY(copy_vals(ctx, s->G.as<double>(), s->GE.as<double>(), s->pL->n_values));
+    return axpby_c(ctx, s->pL, neg, s->GN.as<double>(), one, s->G.as<double>());
 }
 
 void cubic_coeffs(double f0, double g, double a1, double f1, double a2, double f2, double *c2,
@@ -279,27 +397,32 @@ bool cubic_min(double w1, double w2, double w3, double *a)
 
 cq_status lnv_report(cq_lnv *s, cq_lnv_report *rep)
 {
-    double mu, gn2, gg;
-    CQ_TRY(lnv_mu_g(s, &mu, &gn2));
-    CQ_TRY(dot_l(s, s->G.as<double>(), s->G.as<double>(), &gg));
-    rep->energy = s->E;
-    rep->n_elec = s->N;
-    rep->mu = mu;
-    rep->gnorm = std::sqrt(gg / (double)s->pL->n_scalars);
+    std::vector<double> mu, gn2, gg;
+    CQ_TRY(lnv_mu_g(s, mu, gn2));
+    CQ_TRY(dots(s, s->G.as<double>(), s->G.as<double>(), gg));
+    for (int c = 0; c < s->nc; ++c) {
+        rep[c].energy = s->E[c];
+        rep[c].n_elec = s->N[c];
+        rep[c].mu = mu[c];
+        rep[c].gnorm = std::sqrt(gg[c] / (double)s->pL->seg_scalars[c]);
+    }
     return CQ_OK;
 }
 
 }  // namespace
 
-extern "C" cq_status cq_lnv_create(cq_ctx *ctx, const cq_pattern *pS, const double *S,
-                                   const double *H, const cq_pattern *pL, double *L,
-                                   double n_electrons, cq_precision prec, cq_lnv **out)
+extern "C" cq_status cq_lnv_create_cells(cq_ctx *ctx, const cq_pattern *pS, const double *S,
+                                         const double *H, const cq_pattern *pL, double *L,
+                                         const double *n_electrons_host, cq_precision prec,
+                                         cq_lnv **out)
 {
-    if (!ctx || !out || !S || !H || !L) return CQ_ERR_INVALID;
+    if (!ctx || !out || !S || !H || !L || !n_electrons_host) return CQ_ERR_INVALID;
     *out = nullptr;
     CQ_TRY(same_ctx(ctx, pS, pL));
-    if (!(n_electrons > 0.0 && n_electrons < 2.0 * (double)pS->geo->n_orb))
-        return cq_fail(ctx, CQ_ERR_INVALID, "lnv_create: electron count outside (0, 2N)");
+    const int nc = pS->n_cells();
+    for (int c = 0; c < nc; ++c)
+        if (!(n_electrons_host[c] > 0.0 && n_electrons_host[c] < 2.0 * (double)pS->geo->cell_orb[c]))
+            return cq_fail(ctx, CQ_ERR_INVALID, "lnv_create: electron count outside (0, 2N)");
     if (prec != CQ_FP64 && prec != CQ_SPLIT_BF16X3)
         return cq_fail(ctx, CQ_ERR_INVALID, "lnv_create: unknown precision");
     std::unique_ptr<cq_lnv> s(new cq_lnv());
@@ -309,10 +432,12 @@ extern "C" cq_status cq_lnv_create(cq_ctx *ctx, const cq_pattern *pS, const doub
     s->S = S;
     s->H = H;
     s->L = L;
-    s->ne = n_electrons;
+    s->nc = nc;
+    s->ne.assign(n_electrons_host, n_electrons_host + nc);
+    s->alpha_prev.assign(nc, 0.0);
     s->prec = prec;
-    CQ_TRY(cq_pattern_derived(ctx, pS, pL->range + pS->range, &s->pX));
-    CQ_TRY(cq_pattern_derived(ctx, pS, 2.0 * pS->range + pL->range, &s->pU));
+    CQ_TRY(cq_pattern_derived(ctx, pS, 1.0, pL, 1.0, pS, &s->pX));
+    CQ_TRY(cq_pattern_derived(ctx, pS, 2.0, pS, 1.0, pL, &s->pU));
     const size_t bx = sizeof(double) * s->pX->n_values, bu = sizeof(double) * s->pU->n_values;
     const size_t bl = sizeof(double) * pL->n_values;
     CQ_TRY(cq_alloc(ctx, s->X, bx));
@@ -321,83 +446,106 @@ extern "C" cq_status cq_lnv_create(cq_ctx *ctx, const cq_pattern *pS, const doub
     CQ_TRY(cq_alloc(ctx, s->Z, bu));
     for (DevBuf *b : {&s->R1, &s->R2, &s->R3, &s->GE, &s->GN, &s->G, &s->Gp, &s->D, &s->Dp, &s->Lt})
         CQ_TRY(cq_alloc(ctx, *b, bl));
-    CQ_TRY(lnv_evaluate_corrected(s.get(), &s->n_corr_initial));
+    CQ_TRY(lnv_evaluate_corrected(s.get(), s->n_corr_initial));
     ctx->live_lnv.push_back(s.get());
     *out = s.release();
     return CQ_OK;
+}
+
+extern "C" cq_status cq_lnv_create(cq_ctx *ctx, const cq_pattern *pS, const double *S,
+                                   const double *H, const cq_pattern *pL, double *L,
+                                   double n_electrons, cq_precision prec, cq_lnv **out)
+{
+    if (!ctx || !pS) return CQ_ERR_INVALID;
+    if (pS->n_cells() != 1)
+        return cq_fail(ctx, CQ_ERR_INVALID, "lnv_create: batch patterns need cq_lnv_create_cells");
+    return cq_lnv_create_cells(ctx, pS, S, H, pL, L, &n_electrons, prec, out);
 }
 
 extern "C" cq_status cq_lnv_step(cq_lnv *s, cq_lnv_report *rep)
 {
     if (!s || !s->ctx) return CQ_ERR_INVALID;
     cq_ctx *ctx = s->ctx;
+    const int nc = s->nc;
     const int64_t n = s->pL->n_values;
+    const cq_pattern *pL = s->pL;
     double *G = s->G.as<double>(), *D = s->D.as<double>(), *GN = s->GN.as<double>();
     double *GE = s->GE.as<double>();
+    const std::vector<double> one(nc, 1.0), zero(nc, 0.0), neg1(nc, -1.0);
     s->flops = 0.0;
     s->products = 0;
-    double mu, gn2;
-    CQ_TRY(lnv_mu_g(s, &mu, &gn2));
-    bool restart = !s->have_prev;
-    if (restart) {
-        CQ_TRY(cq_axpby(ctx, n, -1.0, G, 0.0, D));
+    std::vector<double> mu, gn2;
+    CQ_TRY(lnv_mu_g(s, mu, gn2));
+    std::vector<bool> restart(nc, !s->have_prev);
+    if (!s->have_prev) {
+        CQ_TRY(axpby_c(ctx, pL, neg1, G, zero, D));
     } else {
         // beta = max(0, <G, G - G_prev> / <G_prev, G_prev>), D = -G + beta D_prev
-        CQ_TRY(cq_check_cuda(ctx, cudaMemcpyAsync(D, G, sizeof(double) * n,
-                                                  cudaMemcpyDeviceToDevice, ctx->stream), "copy"));
-        CQ_TRY(cq_axpby(ctx, n, -1.0, s->Gp.as<double>(), 1.0, D));
-        CQ_TRY(cq_dot_dev(ctx, s->pL, G, D, 0));
-        CQ_TRY(cq_dot_dev(ctx, s->pL, s->Gp.as<double>(), s->Gp.as<double>(), 1));
-        double d[2];
-        CQ_TRY(cq_fetch(ctx, 0, 2, d));
-        const double beta = std::fmax(0.0, d[0] / d[1]);
-        CQ_TRY(cq_check_cuda(ctx, cudaMemcpyAsync(D, s->Dp.ptr, sizeof(double) * n,
-                                                  cudaMemcpyDeviceToDevice, ctx->stream), "copy"));
-        CQ_TRY(cq_axpby(ctx, n, -1.0, G, beta, D));
+        CQ_TRY(copy_vals(ctx, D, G, n));
+        CQ_TRY(axpby_c(ctx, pL, neg1, s->Gp.as<double>(), one, D));
+        CQ_TRY(dot_q(ctx, pL, G, D, 0));
+        CQ_TRY(dot_q(ctx, pL, s->Gp.as<double>(), s->Gp.as<double>(), 1));
+        std::vector<std::vector<double>> d;
+        CQ_TRY(fetch_q(ctx, nc, 2, d));
+        std::vector<double> beta(nc);
+        for (int c = 0; c < nc; ++c) beta[c] = std::fmax(0.0, d[0][c] / d[1][c]);
+        CQ_TRY(copy_vals(ctx, D, s->Dp.as<double>(), n));
+        CQ_TRY(axpby_c(ctx, pL, neg1, G, beta, D));
     }
-    double dg;
-    CQ_TRY(dot_l(s, D, GN, &dg));
-    CQ_TRY(cq_axpby(ctx, n, -(dg / gn2), GN, 1.0, D));
-    double gd;
-    CQ_TRY(dot_l(s, G, D, &gd));
-    if (gd >= 0.0) {
-        CQ_TRY(cq_axpby(ctx, n, -1.0, G, 0.0, D));
-        restart = true;
-    }
-    double a1;
+    std::vector<double> dg;
+    CQ_TRY(dots(s, D, GN, dg));
+    std::vector<double> proj(nc);
+    for (int c = 0; c < nc; ++c) proj[c] = -(dg[c] / gn2[c]);
+    CQ_TRY(axpby_c(ctx, pL, proj, GN, one, D));
+    std::vector<double> gd;
+    CQ_TRY(dots(s, G, D, gd));
+    bool any_restart = false;
+    std::vector<double> ra(nc, 0.0), rb(nc, 1.0);
+    for (int c = 0; c < nc; ++c)
+        if (gd[c] >= 0.0) {
+            restart[c] = true;
+            any_restart = true;
+            ra[c] = -1.0;
+            rb[c] = 0.0;
+        }
+    if (any_restart) CQ_TRY(axpby_c(ctx, pL, ra, G, rb, D));
+    std::vector<double> a1(nc), a2(nc);
     if (!s->have_alpha) {
-        double gg;
-        CQ_TRY(dot_l(s, G, G, &gg));
-        a1 = 0.1 * std::sqrt((double)s->pL->n_scalars) / std::sqrt(gg);
+        std::vector<double> gg;
+        CQ_TRY(dots(s, G, G, gg));
+        for (int c = 0; c < nc; ++c)
+            a1[c] = 0.1 * std::sqrt((double)pL->seg_scalars[c]) / std::sqrt(gg[c]);
     } else {
         a1 = s->alpha_prev;
     }
-    const double a2 = 2.0 * a1;
-    const double E0 = s->E, N0 = s->N;
-    CQ_TRY(cq_dot_dev(ctx, s->pL, GE, D, 0));
-    CQ_TRY(cq_dot_dev(ctx, s->pL, GN, D, 1));
-    double g2[2];
-    CQ_TRY(cq_fetch(ctx, 0, 2, g2));
-    const double gE = g2[0], gNd = g2[1];
-    double E1, N1, E2, N2;
+    for (int c = 0; c < nc; ++c) a2[c] = 2.0 * a1[c];
+    const std::vector<double> E0 = s->E, N0 = s->N;
+    CQ_TRY(dot_q(ctx, pL, GE, D, 0));
+    CQ_TRY(dot_q(ctx, pL, GN, D, 1));
+    std::vector<std::vector<double>> g2;
+    CQ_TRY(fetch_q(ctx, nc, 2, g2));
+    const std::vector<double> &gE = g2[0], &gNd = g2[1];
+    std::vector<double> E1, N1, E2, N2;
     double *Lt = s->Lt.as<double>();
-    CQ_TRY(cq_check_cuda(ctx, cudaMemcpyAsync(Lt, s->L, sizeof(double) * n,
-                                              cudaMemcpyDeviceToDevice, ctx->stream), "copy"));
-    CQ_TRY(cq_axpby(ctx, n, a1, D, 1.0, Lt));
-    CQ_TRY(lnv_energy_number(s, Lt, &E1, &N1));
-    CQ_TRY(cq_check_cuda(ctx, cudaMemcpyAsync(Lt, s->L, sizeof(double) * n,
-                                              cudaMemcpyDeviceToDevice, ctx->stream), "copy"));
-    CQ_TRY(cq_axpby(ctx, n, a2, D, 1.0, Lt));
-    CQ_TRY(lnv_energy_number(s, Lt, &E2, &N2));
-    double e2, e3, n2, n3;
-    cubic_coeffs(E0, gE, a1, E1, a2, E2, &e2, &e3);
-    cubic_coeffs(N0, gNd, a1, N1, a2, N2, &n2, &n3);
-    double alpha = 0.0;
-    const bool ok = cubic_min(gE - mu * gNd, e2 - mu * n2, e3 - mu * n3, &alpha);
-    if (!ok) alpha = 2.0 * a2;
-    CQ_TRY(cq_axpby(ctx, n, alpha, D, 1.0, s->L));
-    int ncorr = 0;
-    CQ_TRY(lnv_evaluate_corrected(s, &ncorr));
+    CQ_TRY(copy_vals(ctx, Lt, s->L, n));
+    CQ_TRY(axpby_c(ctx, pL, a1, D, one, Lt));
+    CQ_TRY(lnv_energy_number(s, Lt, E1, N1));
+    CQ_TRY(copy_vals(ctx, Lt, s->L, n));
+    CQ_TRY(axpby_c(ctx, pL, a2, D, one, Lt));
+    CQ_TRY(lnv_energy_number(s, Lt, E2, N2));
+    std::vector<double> alpha(nc);
+    std::vector<bool> ok(nc);
+    for (int c = 0; c < nc; ++c) {
+        double e2, e3, n2, n3;
+        cubic_coeffs(E0[c], gE[c], a1[c], E1[c], a2[c], E2[c], &e2, &e3);
+        cubic_coeffs(N0[c], gNd[c], a1[c], N1[c], a2[c], N2[c], &n2, &n3);
+        double a = 0.0;
+        ok[c] = cubic_min(gE[c] - mu[c] * gNd[c], e2 - mu[c] * n2, e3 - mu[c] * n3, &a);
+        alpha[c] = ok[c] ? a : 2.0 * a2[c];
+    }
+    CQ_TRY(axpby_c(ctx, pL, alpha, D, one, s->L));
+    std::vector<int> ncorr;
+    CQ_TRY(lnv_evaluate_corrected(s, ncorr));
     std::swap(s->G.ptr, s->Gp.ptr);  // G_prev <- G
     std::swap(s->D.ptr, s->Dp.ptr);  // D_prev <- D
     s->have_prev = true;
@@ -405,12 +553,14 @@ extern "C" cq_status cq_lnv_step(cq_lnv *s, cq_lnv_report *rep)
     s->alpha_prev = alpha;
     if (rep) {
         CQ_TRY(lnv_report(s, rep));
-        rep->alpha = alpha;
-        rep->restart = restart ? 1 : 0;
-        rep->fallback = ok ? 0 : 1;
-        rep->n_corr = ncorr;
-        rep->n_products = s->products;
-        rep->flops = s->flops;
+        for (int c = 0; c < nc; ++c) {
+            rep[c].alpha = alpha[c];
+            rep[c].restart = restart[c] ? 1 : 0;
+            rep[c].fallback = ok[c] ? 0 : 1;
+            rep[c].n_corr = ncorr[c];
+            rep[c].n_products = s->products;
+            rep[c].flops = s->flops;
+        }
     }
     return CQ_OK;
 }
@@ -423,32 +573,35 @@ extern "C" cq_status cq_lnv_set_precision(cq_lnv *s, cq_precision prec)
     s->prec = prec;
     s->have_prev = false;
     s->have_alpha = false;
-    return lnv_evaluate_corrected(s, &s->n_corr_initial);
+    return lnv_evaluate_corrected(s, s->n_corr_initial);
 }
 
-extern "C" cq_status cq_lnv_state(const cq_lnv *s, cq_lnv_report *rep)
+extern "C" cq_status cq_lnv_state(const cq_lnv *cs, cq_lnv_report *rep)
 {
-    if (!s || !rep || !s->ctx) return CQ_ERR_INVALID;
+    if (!cs || !rep || !cs->ctx) return CQ_ERR_INVALID;
     // the report needs G scratch: use Lt (not part of the state between steps)
-    cq_lnv *m = const_cast<cq_lnv *>(s);
-    cq_ctx *ctx = m->ctx;
-    double d[2];
-    CQ_TRY(cq_dot_dev(ctx, m->pL, m->GE.as<double>(), m->GN.as<double>(), 0));
-    CQ_TRY(cq_dot_dev(ctx, m->pL, m->GN.as<double>(), m->GN.as<double>(), 1));
-    CQ_TRY(cq_fetch(ctx, 0, 2, d));
-    const double mu = d[0] / d[1];
-    double *T = m->Lt.as<double>();
-    CQ_TRY(cq_check_cuda(ctx, cudaMemcpyAsync(T, m->GE.ptr, sizeof(double) * m->pL->n_values,
-                                              cudaMemcpyDeviceToDevice, ctx->stream), "copy"));
-    CQ_TRY(cq_axpby(ctx, m->pL->n_values, -mu, m->GN.as<double>(), 1.0, T));
-    double gg;
-    CQ_TRY(dot_l(m, T, T, &gg));
-    *rep = cq_lnv_report();
-    rep->energy = m->E;
-    rep->n_elec = m->N;
-    rep->mu = mu;
-    rep->gnorm = std::sqrt(gg / (double)m->pL->n_scalars);
-    rep->n_corr = m->n_corr_initial;
+    cq_lnv *s = const_cast<cq_lnv *>(cs);
+    cq_ctx *ctx = s->ctx;
+    const int nc = s->nc;
+    CQ_TRY(dot_q(ctx, s->pL, s->GE.as<double>(), s->GN.as<double>(), 0));
+    CQ_TRY(dot_q(ctx, s->pL, s->GN.as<double>(), s->GN.as<double>(), 1));
+    std::vector<std::vector<double>> d;
+    CQ_TRY(fetch_q(ctx, nc, 2, d));
+    std::vector<double> neg(nc), one(nc, 1.0);
+    for (int c = 0; c < nc; ++c) neg[c] = -(d[0][c] / d[1][c]);
+    double *T = s->Lt.as<double>();
+    CQ_TRY(copy_vals(ctx, T, s->GE.as<double>(), s->pL->n_values));
+    CQ_TRY(axpby_c(ctx, s->pL, neg, s->GN.as<double>(), one, T));
+    std::vector<double> gg;
+    CQ_TRY(dots(s, T, T, gg));
+    for (int c = 0; c < nc; ++c) {
+        rep[c] = cq_lnv_report();
+        rep[c].energy = s->E[c];
+        rep[c].n_elec = s->N[c];
+        rep[c].mu = -neg[c];
+        rep[c].gnorm = std::sqrt(gg[c] / (double)s->pL->seg_scalars[c]);
+        rep[c].n_corr = s->n_corr_initial[c];
+    }
     return CQ_OK;
 }
 
@@ -459,11 +612,13 @@ extern "C" cq_status cq_lnv_step_flops(cq_lnv *s, double *flops_host)
     CQ_TRY(cq_get_tasks(s->ctx, s->pL, s->pS, s->pX, &a));
     CQ_TRY(cq_get_tasks(s->ctx, s->pS, s->pX, s->pU, &b));
     CQ_TRY(cq_get_tasks(s->ctx, s->pU, s->pX, s->pL, &c));
-    // full evaluation (X, Y, U, Z, R1, R2, R3) + two trial points (X, Y, U, R1, R3)
-    *flops_host = (2 * a->flops + 2 * b->flops + 3 * c->flops) +
-                  2.0 * (2 * a->flops + b->flops + 2 * c->flops);
+    // two trial points (X, Y, U, R1, R3) + one evaluation without corrections (7 products)
+    *flops_host = 2.0 * (2 * a->flops + b->flops + 2 * c->flops) +
+                  (2 * a->flops + 2 * b->flops + 3 * c->flops);
     return CQ_OK;
 }
+
+extern "C" int32_t cq_lnv_cells(const cq_lnv *s) { return s ? s->nc : 0; }
 
 void cq_lnv_detach(cq_lnv *s)
 {

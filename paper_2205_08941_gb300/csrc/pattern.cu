@@ -195,6 +195,39 @@ __global__ void k_scatter(int64_t n_pairs, const int32_t *pi, const int32_t *pj,
     for (int64_t e = lane; e < sz; e += 32) out[val_off[dst] + e] = pv[poff[b] + e];
 }
 
+// Batches: one CTA per atom row scans the atoms of the row's own cell in ascending order
+// with that cell's box and range; a ballot per warp and a CTA prefix keep the output in
+// ascending column order without sorting.
+template <bool FILL>
+__global__ void __launch_bounds__(ROW_THREADS)
+k_rows_cellwise(const double *pos, const int32_t *cell_of, const int32_t *cell_start,
+                const double *boxes, const double *r2s, int64_t *row_count,
+                const int64_t *row_ptr, int32_t *col)
+{
+    __shared__ int wcount[ROW_THREADS / 32];
+    const int i = blockIdx.x, c = cell_of[i];
+    const int j0 = cell_start[c], j1 = cell_start[c + 1];
+    const double r2 = r2s[c];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t run = FILL ? row_ptr[i] : 0;
+    for (int base = j0; base < j1; base += ROW_THREADS) {
+        const int j = base + threadIdx.x;
+        const bool hit = j < j1 && (j == i || min_image_d2(pos, boxes + 3 * c, i, j) < r2);
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) wcount[wid] = __popc(m);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < ROW_THREADS / 32; ++w) {
+            before += w < wid ? wcount[w] : 0;
+            total += wcount[w];
+        }
+        if (FILL && hit) col[run + before + __popc(m & ((1u << lane) - 1u))] = j;
+        run += total;
+        __syncthreads();
+    }
+    if (!FILL && threadIdx.x == 0) row_count[i] = run;
+}
+
 }  // namespace
 
 bool cq_same_atoms(const cq_pattern *a, const cq_pattern *b)
@@ -204,21 +237,52 @@ bool cq_same_atoms(const cq_pattern *a, const cq_pattern *b)
     if (ga.n_atoms != gb.n_atoms) return false;
     if (std::memcmp(ga.box, gb.box, sizeof(ga.box)) != 0) return false;
     if (ga.nb_host != gb.nb_host) return false;
+    if (ga.cell_start != gb.cell_start || ga.boxes != gb.boxes) return false;
     return std::memcmp(ga.pos_host.data(), gb.pos_host.data(),
                        sizeof(double) * ga.pos_host.size()) == 0;
 }
 
-cq_status cq_pattern_build_geo(cq_ctx *ctx, std::shared_ptr<Geometry> geo, double range,
-                               cq_pattern **out)
+// Row counts (COUNT) or sorted columns (FILL) of a batch pattern.
+static cq_status batch_rows(cq_ctx *ctx, const cq_pattern *p, bool fill, int64_t *row_count)
+{
+    const Geometry &g = *p->geo;
+    void *v_r2;
+    cq_status st = cq_scratch(ctx, "pb_r2", sizeof(double) * g.n_cells, &v_r2);
+    if (st != CQ_OK) return st;
+    std::vector<double> r2(g.n_cells);
+    for (int c = 0; c < g.n_cells; ++c) r2[c] = p->ranges[c] * p->ranges[c];
+    cudaMemcpyAsync(v_r2, r2.data(), sizeof(double) * g.n_cells, cudaMemcpyHostToDevice,
+                    ctx->stream);
+    const int n = g.n_atoms;
+    if (fill)
+        k_rows_cellwise<true><<<n, ROW_THREADS, 0, ctx->stream>>>(
+            g.pos.as<double>(), g.cell_of.as<int32_t>(), g.cell_start_dev.as<int32_t>(),
+            g.boxes_dev.as<double>(), (double *)v_r2, nullptr, p->row_ptr.as<int64_t>(),
+            p->col.as<int32_t>());
+    else
+        k_rows_cellwise<false><<<n, ROW_THREADS, 0, ctx->stream>>>(
+            g.pos.as<double>(), g.cell_of.as<int32_t>(), g.cell_start_dev.as<int32_t>(),
+            g.boxes_dev.as<double>(), (double *)v_r2, row_count, nullptr, nullptr);
+    cq_count_launch();
+    st = cq_check_cuda(ctx, cudaGetLastError(), "batch pattern rows");
+    if (st == CQ_OK)
+        st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "batch pattern rows");
+    return st;
+}
+
+cq_status cq_pattern_build_geo(cq_ctx *ctx, std::shared_ptr<Geometry> geo,
+                               const std::vector<double> &ranges, cq_pattern **out)
 {
     const int n = geo->n_atoms;
     cudaStream_t s = ctx->stream;
+    const bool batch = geo->n_cells > 1;
+    const double range = ranges[0];
     CellGrid g;
     int64_t ncell = 1;
     for (int c = 0; c < 3; ++c) {
         g.box[c] = geo->box[c];
         double q = range > 0.0 ? std::floor(geo->box[c] / range) : 64.0;
-        int nc = q >= 3.0 ? (int)std::min(q, 64.0) : 1;
+        int nc = (q >= 3.0 && !batch) ? (int)std::min(q, 64.0) : 1;
         g.nc[c] = nc;
         ncell *= nc;
     }
@@ -227,6 +291,7 @@ cq_status cq_pattern_build_geo(cq_ctx *ctx, std::shared_ptr<Geometry> geo, doubl
     p->id = ctx->next_id++;
     p->geo = geo;
     p->range = range;
+    p->ranges = ranges;
     cq_status st;
     void *v_cell_of, *v_cell_cnt, *v_cell_start, *v_cursor, *v_cell_atoms, *v_rowcnt;
     if ((st = cq_scratch(ctx, "pb_cell_of", sizeof(int32_t) * n, &v_cell_of)) != CQ_OK ||
@@ -249,11 +314,15 @@ cq_status cq_pattern_build_geo(cq_ctx *ctx, std::shared_ptr<Geometry> geo, doubl
                                                 (int32_t *)v_cell_atoms);
     cq_count_launch();
     const double r2 = range * range;
-    k_rows<false><<<n, ROW_THREADS, 0, s>>>(n, pos, g, (int32_t *)v_cell_of,
-                                            (int64_t *)v_cell_start, (int32_t *)v_cell_atoms,
-                                            r2, (int64_t *)v_rowcnt, nullptr, nullptr,
-                                            ctx->flag.as<int32_t>());
-    cq_count_launch();
+    if (batch) {
+        if ((st = batch_rows(ctx, p.get(), false, (int64_t *)v_rowcnt)) != CQ_OK) return st;
+    } else {
+        k_rows<false><<<n, ROW_THREADS, 0, s>>>(n, pos, g, (int32_t *)v_cell_of,
+                                                (int64_t *)v_cell_start, (int32_t *)v_cell_atoms,
+                                                r2, (int64_t *)v_rowcnt, nullptr, nullptr,
+                                                ctx->flag.as<int32_t>());
+        cq_count_launch();
+    }
     if ((st = cq_check_cuda(ctx, cudaGetLastError(), "pattern rows")) != CQ_OK) return st;
     if ((st = cq_alloc(ctx, p->row_ptr, sizeof(int64_t) * (n + 1))) != CQ_OK) return st;
     if ((st = cq_scan_i64(ctx, (int64_t *)v_rowcnt, p->row_ptr.as<int64_t>(), n)) != CQ_OK)
@@ -277,12 +346,17 @@ cq_status cq_pattern_build_geo(cq_ctx *ctx, std::shared_ptr<Geometry> geo, doubl
         (st = cq_alloc(ctx, p->val_off, sizeof(int64_t) * (nblk + 1))) != CQ_OK ||
         (st = cq_alloc(ctx, p->transpose, sizeof(int64_t) * nblk)) != CQ_OK)
         return st;
-    k_rows<true><<<n, ROW_THREADS, 0, s>>>(n, pos, g, (int32_t *)v_cell_of,
-                                           (int64_t *)v_cell_start, (int32_t *)v_cell_atoms,
-                                           r2, nullptr, p->row_ptr.as<int64_t>(),
-                                           p->col.as<int32_t>(), ctx->flag.as<int32_t>());
+    if (batch) {
+        if ((st = batch_rows(ctx, p.get(), true, nullptr)) != CQ_OK) return st;
+    } else {
+        k_rows<true><<<n, ROW_THREADS, 0, s>>>(n, pos, g, (int32_t *)v_cell_of,
+                                               (int64_t *)v_cell_start, (int32_t *)v_cell_atoms,
+                                               r2, nullptr, p->row_ptr.as<int64_t>(),
+                                               p->col.as<int32_t>(), ctx->flag.as<int32_t>());
+        cq_count_launch();
+    }
     k_block_rows<<<n, 128, 0, s>>>(n, p->row_ptr.as<int64_t>(), p->row.as<int32_t>());
-    cq_count_launch(2);
+    cq_count_launch();
     void *v_sizes;
     if ((st = cq_scratch(ctx, "pb_sizes", sizeof(int64_t) * nblk, &v_sizes)) != CQ_OK) return st;
     const unsigned gb = (unsigned)((nblk + 255) / 256);
@@ -312,21 +386,56 @@ cq_status cq_pattern_build_geo(cq_ctx *ctx, std::shared_ptr<Geometry> geo, doubl
     if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "sync")) != CQ_OK) return st;
     p->n_values = nv;
     p->uniform = geo->uniform_nb ? (int)cq_pad2((int64_t)geo->uniform_nb * geo->uniform_nb) : 0;
+    // per-cell segments: blocks of cell c are those of its atom rows
+    const int nc = geo->n_cells;
+    p->seg_blk.resize(nc + 1);
+    p->seg_val.resize(nc + 1);
+    p->seg_scalars.assign(nc, 0);
+    for (int c = 0; c <= nc; ++c) p->seg_blk[c] = p->row_ptr_host[geo->cell_start[c]];
+    for (int c = 0; c <= nc; ++c) {
+        if (p->seg_blk[c] == nblk) {
+            p->seg_val[c] = nv;
+        } else {
+            cudaMemcpyAsync(&p->seg_val[c], p->val_off.as<int64_t>() + p->seg_blk[c],
+                            sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        }
+    }
+    if (nc > 1) {
+        std::vector<int64_t> scal(nblk + 1);
+        cudaMemcpyAsync(scal.data(), v_scan, sizeof(int64_t) * (nblk + 1),
+                        cudaMemcpyDeviceToHost, s);
+        if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "sync")) != CQ_OK) return st;
+        for (int c = 0; c < nc; ++c) p->seg_scalars[c] = scal[p->seg_blk[c + 1]] - scal[p->seg_blk[c]];
+    } else {
+        if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "sync")) != CQ_OK) return st;
+        p->seg_scalars[0] = p->n_scalars;
+    }
+    if ((st = cq_alloc(ctx, p->seg_blk_dev, sizeof(int64_t) * (nc + 1))) != CQ_OK ||
+        (st = cq_alloc(ctx, p->seg_val_dev, sizeof(int64_t) * (nc + 1))) != CQ_OK)
+        return st;
+    cudaMemcpyAsync(p->seg_blk_dev.ptr, p->seg_blk.data(), sizeof(int64_t) * (nc + 1),
+                    cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->seg_val_dev.ptr, p->seg_val.data(), sizeof(int64_t) * (nc + 1),
+                    cudaMemcpyHostToDevice, s);
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "sync")) != CQ_OK) return st;
     *out = p.release();
     return CQ_OK;
 }
 
-cq_status cq_pattern_derived(cq_ctx *ctx, const cq_pattern *base, double range,
+cq_status cq_pattern_derived(cq_ctx *ctx, const cq_pattern *base, double ca,
+                             const cq_pattern *pa, double cb, const cq_pattern *pb,
                              cq_pattern **out)
 {
-    auto key = std::make_pair(base->geo->id, range);
+    std::vector<double> ranges(base->n_cells());
+    for (int c = 0; c < base->n_cells(); ++c) ranges[c] = ca * pa->ranges[c] + cb * pb->ranges[c];
+    auto key = std::make_pair(base->geo->id, ranges);
     auto it = ctx->derived.find(key);
     if (it != ctx->derived.end()) {
         *out = it->second;
         return CQ_OK;
     }
     cq_pattern *p = nullptr;
-    cq_status st = cq_pattern_build_geo(ctx, base->geo, range, &p);
+    cq_status st = cq_pattern_build_geo(ctx, base->geo, ranges, &p);
     if (st != CQ_OK) return st;
     p->owned_by_ctx = true;
     ctx->derived[key] = p;

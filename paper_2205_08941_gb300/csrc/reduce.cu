@@ -266,6 +266,130 @@ __global__ void k_lnv_grad_e(int64_t nblk, const int32_t *row, const int32_t *co
     }
 }
 
+// ---------------- per-cell (segmented) versions: blockIdx.y = cell, RED_S CTAs per cell
+constexpr int RED_S = 64;
+
+__global__ void __launch_bounds__(RED_T)
+k_trace_seg(const int64_t *seg, const int32_t *row, const int32_t *col, const int32_t *nb,
+            const int64_t *a_off, const int64_t *b_off, const int64_t *bmap, const double *A,
+            const double *B, double *part)
+{
+    const int lane = threadIdx.x & 31, c = blockIdx.y;
+    const int64_t b0 = seg[c], b1 = seg[c + 1];
+    double s = 0.0;
+    for (int64_t b = b0 + (int64_t)blockIdx.x * (RED_T / 32) + (threadIdx.x >> 5); b < b1;
+         b += (int64_t)RED_S * (RED_T / 32)) {
+        const int64_t t = bmap[b];
+        if (t < 0) continue;
+        const int ni = nb[row[b]], nj = nb[col[b]];
+        const double *a = A + a_off[b];
+        const double *bb = B + b_off[t];
+        for (int e = lane; e < ni * nj; e += 32) {
+            const int r = e / nj, q = e - r * nj;
+            s = fma(a[e], bb[q * ni + r], s);
+        }
+    }
+    s = cta_reduce<SUM>(s);
+    if (threadIdx.x == 0) part[(int64_t)c * RED_S + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(RED_T)
+k_dot_seg(const int64_t *seg, const int32_t *row, const int32_t *col, const int32_t *nb,
+          const int64_t *off, const double *A, const double *B, double *part)
+{
+    const int lane = threadIdx.x & 31, c = blockIdx.y;
+    const int64_t b0 = seg[c], b1 = seg[c + 1];
+    double s = 0.0;
+    for (int64_t b = b0 + (int64_t)blockIdx.x * (RED_T / 32) + (threadIdx.x >> 5); b < b1;
+         b += (int64_t)RED_S * (RED_T / 32)) {
+        const int sz = nb[row[b]] * nb[col[b]];
+        const int64_t o = off[b];
+        for (int e = lane; e < sz; e += 32) s = fma(A[o + e], B[o + e], s);
+    }
+    s = cta_reduce<SUM>(s);
+    if (threadIdx.x == 0) part[(int64_t)c * RED_S + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(RED_T)
+k_row_bounds_seg(const int32_t *cell_start, const int64_t *rp, const int32_t *col,
+                 const int32_t *nb, const int64_t *off, const double *M, double *part)
+{
+    const int lane = threadIdx.x & 31, c = blockIdx.y;
+    double lo = DBL_MAX, hi = -DBL_MAX, amax = 0.0;
+    for (int i = cell_start[c] + blockIdx.x * (RED_T / 32) + (threadIdx.x >> 5);
+         i < cell_start[c + 1]; i += RED_S * (RED_T / 32)) {
+        const int ni = nb[i];
+        if (lane >= ni) continue;
+        double centre = 0.0, rad = 0.0, tot = 0.0;
+        for (int64_t b = rp[i]; b < rp[i + 1]; ++b) {
+            const int j = col[b], nj = nb[j];
+            const double *m = M + off[b] + (int64_t)lane * nj;
+            for (int q = 0; q < nj; ++q) {
+                const double v = m[q];
+                tot += fabs(v);
+                if (j == i && q == lane)
+                    centre = v;
+                else
+                    rad += fabs(v);
+            }
+        }
+        lo = fmin(lo, centre - rad);
+        hi = fmax(hi, centre + rad);
+        amax = fmax(amax, tot);
+    }
+    lo = cta_reduce<MIN>(lo);
+    hi = cta_reduce<MAX>(hi);
+    amax = cta_reduce<MAX>(amax);
+    if (threadIdx.x == 0) {
+        const int64_t k = (int64_t)c * RED_S + blockIdx.x;
+        part[3 * k + 0] = lo;
+        part[3 * k + 1] = hi;
+        part[3 * k + 2] = amax;
+    }
+}
+
+// one CTA per cell folds that cell's RED_S partials (strided) into out[cell * ostride]
+template <int OP>
+__global__ void k_final_seg(const double *part, int stride, double *out, int ostride)
+{
+    const int c = blockIdx.x;
+    double v = identity_of<OP>();
+    for (int e = threadIdx.x; e < RED_S; e += RED_T)
+        v = combine<OP>(v, part[((int64_t)c * RED_S + e) * stride]);
+    v = cta_reduce<OP>(v);
+    if (threadIdx.x == 0) out[(int64_t)c * ostride] = v;
+}
+
+__global__ void k_axpby_seg(const int64_t *seg_val, const double *coef, int n_cells,
+                            const double *x, double *y)
+{
+    const int c = blockIdx.y;
+    const double a = coef[c], b = coef[n_cells + c];
+    const int64_t v1 = seg_val[c + 1];
+    for (int64_t e = seg_val[c] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < v1;
+         e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = (b == 0.0) ? a * x[e] : a * x[e] + b * y[e];
+}
+
+__global__ void k_identity_seg(int n_atoms, const int32_t *cell_of, const int64_t *rp,
+                               const int32_t *col, const int32_t *nb, const int64_t *off,
+                               const double *scale, double *M)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_atoms) return;
+    int64_t lo = rp[i], hi = rp[i + 1];
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < i)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    const int ni = nb[i];
+    const double s = scale[cell_of[i]];
+    for (int r = 0; r < ni; ++r) M[off[lo] + r * ni + r] = s;
+}
+
 cq_status red_part(cq_ctx *ctx, double **part)
 {
     void *p;
@@ -392,6 +516,99 @@ cq_status cq_lnv_gradients(cq_ctx *ctx, const cq_pattern *pL, const cq_pattern *
         Z, U, R1, R2, R3, GE, GN);
     cq_count_launch();
     return cq_check_cuda(ctx, cudaGetLastError(), "lnv gradients");
+}
+
+// ---------------------------------------------------------------- per-cell host wrappers
+
+static cq_status seg_part(cq_ctx *ctx, int n_cells, double **part)
+{
+    void *p;
+    cq_status st = cq_scratch(ctx, "red_part_seg", sizeof(double) * 3 * RED_S * n_cells, &p);
+    *part = (double *)p;
+    return st;
+}
+
+cq_status cq_trace_seg_dev(cq_ctx *ctx, const cq_pattern *pA, const double *A,
+                           const cq_pattern *pB, const double *B, int slot)
+{
+    const int64_t *bmap;
+    cq_status st = cq_get_map(ctx, pB, pA, 1, &bmap);
+    if (st != CQ_OK) return st;
+    const int nc = pA->n_cells();
+    double *part;
+    if ((st = seg_part(ctx, nc, &part)) != CQ_OK) return st;
+    k_trace_seg<<<dim3(RED_S, nc), RED_T, 0, ctx->stream>>>(
+        pA->seg_blk_dev.as<int64_t>(), pA->row.as<int32_t>(), pA->col.as<int32_t>(),
+        pA->geo->nb.as<int32_t>(), pA->val_off.as<int64_t>(), pB->val_off.as<int64_t>(), bmap, A,
+        B, part);
+    k_final_seg<SUM><<<nc, RED_T, 0, ctx->stream>>>(part, 1, ctx->red_out.as<double>() + slot, 1);
+    cq_count_launch(2);
+    return cq_check_cuda(ctx, cudaGetLastError(), "trace (cells)");
+}
+
+cq_status cq_dot_seg_dev(cq_ctx *ctx, const cq_pattern *p, const double *A, const double *B,
+                         int slot)
+{
+    const int nc = p->n_cells();
+    double *part;
+    cq_status st = seg_part(ctx, nc, &part);
+    if (st != CQ_OK) return st;
+    k_dot_seg<<<dim3(RED_S, nc), RED_T, 0, ctx->stream>>>(
+        p->seg_blk_dev.as<int64_t>(), p->row.as<int32_t>(), p->col.as<int32_t>(),
+        p->geo->nb.as<int32_t>(), p->val_off.as<int64_t>(), A, B, part);
+    k_final_seg<SUM><<<nc, RED_T, 0, ctx->stream>>>(part, 1, ctx->red_out.as<double>() + slot, 1);
+    cq_count_launch(2);
+    return cq_check_cuda(ctx, cudaGetLastError(), "dot (cells)");
+}
+
+cq_status cq_row_bounds_seg_dev(cq_ctx *ctx, const cq_pattern *p, const double *M, int slot)
+{
+    const int nc = p->n_cells();
+    double *part;
+    cq_status st = seg_part(ctx, nc, &part);
+    if (st != CQ_OK) return st;
+    k_row_bounds_seg<<<dim3(RED_S, nc), RED_T, 0, ctx->stream>>>(
+        p->geo->cell_start_dev.as<int32_t>(), p->row_ptr.as<int64_t>(), p->col.as<int32_t>(),
+        p->geo->nb.as<int32_t>(), p->val_off.as<int64_t>(), M, part);
+    double *o = ctx->red_out.as<double>() + slot;
+    k_final_seg<MIN><<<nc, RED_T, 0, ctx->stream>>>(part + 0, 3, o + 0, 3);
+    k_final_seg<MAX><<<nc, RED_T, 0, ctx->stream>>>(part + 1, 3, o + 1, 3);
+    k_final_seg<MAX><<<nc, RED_T, 0, ctx->stream>>>(part + 2, 3, o + 2, 3);
+    cq_count_launch(4);
+    return cq_check_cuda(ctx, cudaGetLastError(), "row bounds (cells)");
+}
+
+cq_status cq_axpby_seg(cq_ctx *ctx, const cq_pattern *p, const double *a, const double *x,
+                       const double *b, double *y)
+{
+    const int nc = p->n_cells();
+    void *v;
+    cq_status st = cq_scratch(ctx, "seg_coef", sizeof(double) * 2 * nc, &v);
+    if (st != CQ_OK) return st;
+    std::vector<double> coef(a, a + nc);
+    coef.insert(coef.end(), b, b + nc);
+    cudaMemcpyAsync(v, coef.data(), sizeof(double) * 2 * nc, cudaMemcpyHostToDevice, ctx->stream);
+    k_axpby_seg<<<dim3(64, nc), 256, 0, ctx->stream>>>(p->seg_val_dev.as<int64_t>(), (double *)v,
+                                                       nc, x, y);
+    cq_count_launch();
+    return cq_check_cuda(ctx, cudaGetLastError(), "axpby (cells)");
+}
+
+cq_status cq_set_identity_seg(cq_ctx *ctx, const cq_pattern *p, double *M, const double *s)
+{
+    const int nc = p->n_cells();
+    cq_status st = cq_check_cuda(ctx, cudaMemsetAsync(M, 0, sizeof(double) * p->n_values,
+                                                      ctx->stream), "identity");
+    if (st != CQ_OK) return st;
+    void *v;
+    if ((st = cq_scratch(ctx, "seg_scale", sizeof(double) * nc, &v)) != CQ_OK) return st;
+    cudaMemcpyAsync(v, s, sizeof(double) * nc, cudaMemcpyHostToDevice, ctx->stream);
+    const int n = p->geo->n_atoms;
+    k_identity_seg<<<(n + 127) / 128, 128, 0, ctx->stream>>>(
+        n, p->geo->cell_of.as<int32_t>(), p->row_ptr.as<int64_t>(), p->col.as<int32_t>(),
+        p->geo->nb.as<int32_t>(), p->val_off.as<int64_t>(), (const double *)v, M);
+    cq_count_launch();
+    return cq_check_cuda(ctx, cudaGetLastError(), "identity (cells)");
 }
 
 cq_status cq_lnv_gradient_n(cq_ctx *ctx, const cq_pattern *pL, const cq_pattern *pU,

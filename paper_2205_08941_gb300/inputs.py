@@ -313,3 +313,144 @@ def write_fixture(path: str, cell: Cell, **pair_lists: PairBlocks) -> None:
         arrays[f"{name}_off"] = pb.off
         arrays[f"{name}_values"] = pb.values
     np.savez(path, **arrays)
+
+
+# ---------------------------------------------------------------------------------------
+# Mixed species (batched heterogeneous cells): 5-orbital sp3s*, 9-orbital spd and
+# 13-orbital s p s* p* d atoms, all with four valence electrons.
+# ---------------------------------------------------------------------------------------
+
+# shells of each species: (label, l); orbitals follow shell order, m order as above
+SPECIES = {
+    5: [("s", 0), ("p", 1), ("s*", 0)],
+    9: [("s", 0), ("p", 1), ("d", 2)],
+    13: [("s", 0), ("p", 1), ("s*", 0), ("p*", 1), ("d", 2)],
+}
+SHELL_ONSITE_EV = {"s": -8.0, "p": -8.0, "d": 6.0, "s*": 4.0, "p*": 6.0}
+SHELL_SCALE = {"s": 1.0, "p": 1.0, "d": 1.0, "s*": 0.6, "p*": 0.5}
+_LKEY = {(0, 0): "ss", (0, 1): "sp", (1, 1): "pp", (0, 2): "sd", (1, 2): "pd", (2, 2): "dd"}
+_MSYM = {0: "s", 1: "p", 2: "d"}
+# local bond-frame orbitals of a shell: symmetry (|m|, partner tag) per component
+_LOCAL = {0: [(0, "z")], 1: [(1, "x"), (1, "y"), (0, "z")],
+          2: [(2, "xy"), (1, "y"), (1, "x"), (2, "x2"), (0, "z")]}
+
+
+def _shell_rotation(l, rot):
+    if l == 0:
+        return np.ones((rot.shape[0], 1, 1))
+    if l == 1:
+        return rot
+    qg = np.einsum("pji,ajk,pkl->pail", rot, _DQ, rot)
+    return np.einsum("pail,bil->pab", qg, _DQ)
+
+
+def species_blocks(model: SKModel, disp: np.ndarray, sa: int, sb: int, which: str):
+    """Two-centre blocks (P, nb_a, nb_b) between species sa (at the origin) and sb (at disp),
+    `which` = "v" (hamiltonian) or "s" (overlap).  Shell pairs couple through the bond
+    integral of their l pair scaled by both shells' factors; the (l_a > l_b) element carries
+    the parity sign (-1)^(l_a + l_b)."""
+    par = model.v if which == "v" else model.s
+    r = np.linalg.norm(disp, axis=1)
+    rot = _frames(disp / r[:, None])
+    radial = np.exp(-(r - model.r_nn) / model.decay) * _cutoff(r, model.r_cut, model.cut_width)
+    p = disp.shape[0]
+    out = np.zeros((p, sa, sb))
+    oa = 0
+    for la_name, la in SPECIES[sa]:
+        da = _shell_rotation(la, rot)
+        ob = 0
+        for lb_name, lb in SPECIES[sb]:
+            db = _shell_rotation(lb, rot)
+            lo, hi = min(la, lb), max(la, lb)
+            key = _LKEY[(lo, hi)]
+            sign = (-1.0) ** (la + lb) if la > lb else 1.0
+            scale = SHELL_SCALE[la_name] * SHELL_SCALE[lb_name] * sign
+            m0 = np.zeros((2 * la + 1, 2 * lb + 1))
+            for ia, (ma, ta) in enumerate(_LOCAL[la]):
+                for ib, (mb, tb) in enumerate(_LOCAL[lb]):
+                    # only components of equal |m| and equal orientation couple
+                    if ma != mb or ta != tb:
+                        continue
+                    m0[ia, ib] = par[key + "spd"[ma]] * scale
+            blk = np.einsum("pab,ac,pcd->pbd", da, m0, db) * radial[:, None, None]
+            out[:, oa:oa + 2 * la + 1, ob:ob + 2 * lb + 1] = blk
+            ob += 2 * lb + 1
+        oa += 2 * la + 1
+    return out
+
+
+def species_onsite(nb: int) -> np.ndarray:
+    e = []
+    for name, l in SPECIES[nb]:
+        e += [SHELL_ONSITE_EV[name] * EV] * (2 * l + 1)
+    return np.array(e)
+
+
+def overlap_hamiltonian_species(cell: Cell, model: SKModel):
+    """Gamma-folded S and H for cells whose atoms carry 5, 9 or 13 orbitals (PairBlocks).
+
+    Blocks (i, j) with i <= j are computed; (j, i) is their transpose."""
+    i, j, d0 = neighbour_pairs(cell, model.r_cut)
+    nb = cell.nb
+    sizes = nb[i].astype(np.int64) * nb[j].astype(np.int64)
+    off = np.zeros(i.shape[0] + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    s_val, h_val = np.zeros(int(off[-1])), np.zeros(int(off[-1]))
+    n_img = [int(math.ceil(model.r_cut / b)) for b in cell.box]
+    upper = np.nonzero(i <= j)[0]
+    blocks_s, blocks_h = {}, {}
+    for sa in SPECIES:
+        for sb in SPECIES:
+            sel = upper[(nb[i[upper]] == sa) & (nb[j[upper]] == sb)]
+            if sel.size == 0:
+                continue
+            bs = np.zeros((sel.size, sa, sb))
+            bh = np.zeros((sel.size, sa, sb))
+            for sx in range(-n_img[0], n_img[0] + 1):
+                for sy in range(-n_img[1], n_img[1] + 1):
+                    for sz in range(-n_img[2], n_img[2] + 1):
+                        disp = d0[sel] + np.array([sx, sy, sz], dtype=np.float64) * cell.box
+                        r = np.linalg.norm(disp, axis=1)
+                        m = np.nonzero((r < model.r_cut) & (r > 1e-12))[0]
+                        if m.size == 0:
+                            continue
+                        bs[m] += species_blocks(model, disp[m], sa, sb, "s")
+                        bh[m] += species_blocks(model, disp[m], sa, sb, "v")
+            diag = np.nonzero(i[sel] == j[sel])[0]
+            if diag.size:
+                bs[diag] += np.eye(sa)
+                bh[diag] += np.diag(species_onsite(sa))
+            for q, b in enumerate(sel):
+                blocks_s[b] = bs[q]
+                blocks_h[b] = bh[q]
+    key = i.astype(np.int64) * cell.n_atoms + j
+    tpos = np.searchsorted(key, j.astype(np.int64) * cell.n_atoms + i)
+    for b in range(i.shape[0]):
+        if i[b] <= j[b]:
+            s_blk, h_blk = blocks_s[b], blocks_h[b]
+        else:
+            s_blk, h_blk = blocks_s[tpos[b]].T, blocks_h[tpos[b]].T
+        s_val[off[b]:off[b + 1]] = s_blk.reshape(-1)
+        h_val[off[b]:off[b + 1]] = h_blk.reshape(-1)
+    return PairBlocks(i=i, j=j, off=off, values=s_val), PairBlocks(i=i, j=j, off=off, values=h_val)
+
+
+def mixed_cell(ncell, density_per_A3: float, sigma: float, seed: int,
+               species=(5, 9, 13)) -> Cell:
+    """Diamond lattice scaled to a density (atoms per cubic angstrom) with species drawn per
+    atom from `species` (seeded)."""
+    a = (8.0 / (density_per_A3 / 1.8897261254578281 ** 3)) ** (1.0 / 3.0)
+    cell = diamond_cell(ncell, a=a, sigma=sigma, seed=seed, norb=9)
+    rng = np.random.default_rng(seed + 7919)
+    cell.nb = rng.choice(np.array(species, dtype=np.int32), size=cell.n_atoms)
+    return cell
+
+
+def concat_cells(cells):
+    """Atoms of several cells back to back: positions, nb, atom prefix, boxes (per cell)."""
+    pos = np.concatenate([c.pos for c in cells])
+    nb = np.concatenate([c.nb for c in cells]).astype(np.int32)
+    start = np.zeros(len(cells) + 1, dtype=np.int32)
+    np.cumsum([c.n_atoms for c in cells], out=start[1:])
+    boxes = np.stack([c.box for c in cells])
+    return pos, nb, start, boxes
