@@ -87,6 +87,18 @@ cq_status cq_ctx_set_timing(cq_ctx *ctx, int on);
  * products issued (0 for FP64 products).  Synchronises. */
 cq_status cq_ctx_kernel_stats(cq_ctx *ctx, int64_t *launches_host, double *ms_host,
                               double *flops_host, double *mma_flops_host);
+/* Autotuner (off by default): on the first FP64 product of each (P_A, P_B, P_C) triple, time
+ * every lane split of the FP64 kernel (1..32 lanes per C row) on the real operands into
+ * scratch and keep the fastest for that triple.  Synchronises on that first use only. */
+cq_status cq_ctx_set_autotune(cq_ctx *ctx, int on);
+/* CUDA graphs (off by default): LNV evaluation phases (trial point, electron-number half,
+ * energy half: their products, traces and gradients) run eagerly once, are captured on
+ * their second use and replayed afterwards, with identical results.  Needs a context on a
+ * created stream (the legacy default stream cannot be captured): CQ_ERR_INVALID otherwise. */
+cq_status cq_ctx_set_graphs(cq_ctx *ctx, int on);
+/* Lanes per C row the FP64 product of this triple uses, and whether the autotuner chose it. */
+cq_status cq_bsmm_config(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
+                         const cq_pattern *pC, int32_t *lane_split_host, int32_t *tuned_host);
 /* Measure the device's FP64 FMA throughput (flop/s, an FMA counted as 2) with a register-
  * resident chain of independent FMAs filling every SM: the FP64 roofline denominator. */
 cq_status cq_peak_fp64(cq_ctx *ctx, double *flops_per_s_host);

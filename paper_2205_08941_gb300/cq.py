@@ -86,6 +86,9 @@ SIGNATURES = {
     "cq_lnv_create_cells": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
                                   ctypes.POINTER(_vp)]),
     "cq_lnv_cells": (_i32, [_vp]),
+    "cq_ctx_set_autotune": (_st, [_vp, ctypes.c_int]),
+    "cq_ctx_set_graphs": (_st, [_vp, ctypes.c_int]),
+    "cq_bsmm_config": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
 }
 
 
@@ -174,6 +177,18 @@ class Context:
 
     def set_timing(self, on: bool):
         self._check(lib().cq_ctx_set_timing(self.h, 1 if on else 0))
+
+    def set_autotune(self, on: bool):
+        self._check(lib().cq_ctx_set_autotune(self.h, 1 if on else 0))
+
+    def set_graphs(self, on: bool):
+        self._check(lib().cq_ctx_set_graphs(self.h, 1 if on else 0))
+
+    def bsmm_config(self, pA, pB, pC):
+        q, tuned = ctypes.c_int32(), ctypes.c_int32()
+        self._check(lib().cq_bsmm_config(self.h, pA.h, pB.h, pC.h, ctypes.byref(q),
+                                         ctypes.byref(tuned)))
+        return int(q.value), bool(tuned.value)
 
     def kernel_stats(self):
         n, ms, fl, mf = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -153,48 +153,24 @@ void launch_uniform(int q, unsigned grid, cudaStream_t s, int64_t n_items, const
 
 }  // namespace
 
-cq_status cq_bsmm_f64(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pattern *pA,
-                      const double *A, const cq_pattern *pB, const double *B, double beta,
-                      const cq_pattern *pC, double *C)
+// One launch of the FP64 product with lane split q.
+static void launch_f64(cq_ctx *ctx, int q, const TaskList *tl, double alpha,
+                       const cq_pattern *pA, const double *A, const cq_pattern *pB,
+                       const double *B, double beta, const cq_pattern *pC, double *C)
 {
-    if (tl->n_c == 0) return CQ_OK;
-    const int q = pick_q(tl);
     const int nbu = pC->geo->uniform_nb;
     cudaStream_t s = ctx->stream;
+    const int64_t n_items = tl->n_items;
+    const unsigned grid = (unsigned)((n_items * q + 255) / 256);
     if (nbu == 9 || nbu == 4) {
-        const int64_t n_items = tl->n_c * nbu;
-        const int64_t threads = n_items * q;
-        const unsigned grid = (unsigned)((threads + 255) / 256);
-        cq_timing_begin(ctx, tl->flops);
         if (nbu == 9)
             launch_uniform<9>(q, grid, s, n_items, tl, A, B, C, pC->uniform, alpha, beta);
         else
             launch_uniform<4>(q, grid, s, n_items, tl, A, B, C, pC->uniform, alpha, beta);
-        cq_timing_end(ctx);
-        cq_count_launch();
-        return cq_check_cuda(ctx, cudaGetLastError(), "bsmm_f64");
+        return;
     }
-    // general basis: rowitem prefix exists for non-uniform patterns; build one on the fly
-    // for uniform bases other than 4 and 9
-    const int64_t *rowitem = tl->c_rowitem.ptr ? tl->c_rowitem.as<int64_t>() : nullptr;
-    DevBuf tmp;
-    int64_t n_items = 0;
-    if (!rowitem) {
-        std::vector<int64_t> h(tl->n_c + 1);
-        for (int64_t c = 0; c <= tl->n_c; ++c) h[c] = c * nbu;
-        cq_status st = cq_alloc(ctx, tmp, sizeof(int64_t) * h.size());
-        if (st != CQ_OK) return st;
-        cudaMemcpyAsync(tmp.ptr, h.data(), sizeof(int64_t) * h.size(), cudaMemcpyHostToDevice, s);
-        cudaStreamSynchronize(s);
-        rowitem = tmp.as<int64_t>();
-        n_items = tl->n_c * nbu;
-    } else {
-        cudaMemcpyAsync(&n_items, rowitem + tl->n_c, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
-    }
-    const unsigned grid = (unsigned)((n_items * q + 255) / 256);
+    const int64_t *rowitem = tl->c_rowitem.as<int64_t>();
     const int32_t *nb = pC->geo->nb.as<int32_t>();
-    cq_timing_begin(ctx, tl->flops);
 #define CQ_GEN(QQ)                                                                            \
     k_bsmm_f64_generic<QQ><<<grid, 256, 0, s>>>(                                              \
         n_items, tl->n_c, rowitem, tl->seg.as<int64_t>(), tl->tasks.as<int2>(), nb,           \
@@ -210,9 +186,57 @@ cq_status cq_bsmm_f64(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pa
     default: CQ_GEN(32); break;
     }
 #undef CQ_GEN
+}
+
+// Autotuner: on the first product of a task list (with autotuning on and no capture open),
+// time every lane split on the real operands into scratch (beta = 0, so the caller's C is
+// untouched) and keep the fastest for this task list.
+static cq_status tune_q(cq_ctx *ctx, const TaskList *tl, const cq_pattern *pA, const double *A,
+                        const cq_pattern *pB, const double *B, const cq_pattern *pC)
+{
+    void *tmp;
+    cq_status st = cq_scratch(ctx, "tune_C", sizeof(double) * pC->n_values, &tmp);
+    if (st != CQ_OK) return st;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_q = pick_q(tl);
+    for (int q = 1; q <= 32; q <<= 1) {
+        launch_f64(ctx, q, tl, 1.0, pA, A, pB, B, 0.0, pC, (double *)tmp);  // warm
+        cudaEventRecord(e0, ctx->stream);
+        launch_f64(ctx, q, tl, 1.0, pA, A, pB, B, 0.0, pC, (double *)tmp);
+        cudaEventRecord(e1, ctx->stream);
+        cq_count_launch(2);
+        st = cq_check_cuda(ctx, cudaEventSynchronize(e1), "autotune");
+        if (st != CQ_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_q = q;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tl->q = best_q;
+    return st;
+}
+
+int cq_lane_split(const TaskList *tl) { return tl->q ? tl->q : pick_q(tl); }
+
+cq_status cq_bsmm_f64(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pattern *pA,
+                      const double *A, const cq_pattern *pB, const double *B, double beta,
+                      const cq_pattern *pC, double *C)
+{
+    if (tl->n_c == 0) return CQ_OK;
+    if (ctx->autotune && tl->q == 0 && !ctx->capturing) {
+        cq_status st = tune_q(ctx, tl, pA, A, pB, B, pC);
+        if (st != CQ_OK) return st;
+    }
+    cq_timing_begin(ctx, tl->flops);
+    launch_f64(ctx, cq_lane_split(tl), tl, alpha, pA, A, pB, B, beta, pC, C);
     cq_timing_end(ctx);
     cq_count_launch();
-    cq_status st = cq_check_cuda(ctx, cudaGetLastError(), "bsmm_f64_generic");
-    if (tmp.ptr) cudaStreamSynchronize(s);
-    return st;
+    return cq_check_cuda(ctx, cudaGetLastError(), "bsmm_f64");
 }

@@ -491,13 +491,16 @@ cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_
     a.flag = ctx->flag.as<int32_t>();
     const int grid = std::min(tiles->n_tiles, ctx->num_sms);
     cq_timing_begin(ctx, tl->flops, tiles->mma_flops);
-    if (nb == 9) {
+    static bool attr_set = false;  // once per process (outside any graph capture)
+    if (!attr_set) {
         cudaFuncSetAttribute(k_bsmm_split<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        k_bsmm_split<9><<<grid, ST, SMEM, s>>>(a);
-    } else {
         cudaFuncSetAttribute(k_bsmm_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        k_bsmm_split<4><<<grid, ST, SMEM, s>>>(a);
+        attr_set = true;
     }
+    if (nb == 9)
+        k_bsmm_split<9><<<grid, ST, SMEM, s>>>(a);
+    else
+        k_bsmm_split<4><<<grid, ST, SMEM, s>>>(a);
     cq_timing_end(ctx);
     cq_count_launch();
     return cq_check_cuda(ctx, cudaGetLastError(), "bsmm_split");

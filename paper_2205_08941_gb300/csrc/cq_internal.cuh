@@ -57,7 +57,9 @@ struct TaskList {
     double flops = 0.0;
     DevBuf seg;     // int64 [n_c + 1]
     DevBuf tasks;   // int2  [n_tasks]: (A block, B block)
-    DevBuf c_rowitem;  // int64 [n_c + 1] prefix of n_i over C blocks (mixed bases only)
+    DevBuf c_rowitem;  // int64 [n_c + 1] prefix of n_i over C blocks (bases other than 4, 9)
+    int64_t n_items = 0;  // scalar C rows (sum of n_i over C blocks)
+    mutable int q = 0;    // lanes per C row of the FP64 kernel chosen by the autotuner (0: none)
 };
 
 struct cq_pattern {
@@ -112,6 +114,10 @@ struct cq_ctx {
     size_t ev_used = 0;
     double timed_flops = 0.0;
     double timed_mma_flops = 0.0;
+    bool autotune = false;           // time the FP64 lane splits on a product's first use
+    bool graphs = false;             // replay LNV evaluation phases as CUDA graphs
+    bool capturing = false;          // a graph capture is open on the stream
+    uint64_t scratch_gen = 0;        // bumped whenever a scratch buffer is reallocated
 };
 
 // Record a timing event pair around a product launch when timing is on.
@@ -151,6 +157,9 @@ cq_status cq_get_map(cq_ctx *ctx, const cq_pattern *pSrc, const cq_pattern *pDst
 cq_status cq_bsmm_f64(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pattern *pA,
                       const double *A, const cq_pattern *pB, const double *B, double beta,
                       const cq_pattern *pC, double *C);
+// Lane split the FP64 kernel uses for a task list (tuned if the autotuner ran, else the
+// mean-segment heuristic).
+int cq_lane_split(const TaskList *tl);
 cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pattern *pA,
                         const double *A, const cq_pattern *pB, const double *B, double beta,
                         const cq_pattern *pC, double *C);
@@ -196,6 +205,10 @@ cq_status cq_set_identity_seg(cq_ctx *ctx, const cq_pattern *p, double *M, const
 
 // Launch-count bookkeeping (kernels this library launched; read by the bench).
 void cq_count_launch(int64_t n = 1);
+// While a graph is captured on this thread, launches are counted into the graph (and
+// added to the total each time it is replayed).
+void cq_capture_counting(bool on);
+int64_t cq_capture_launches(void);
 
 static inline int64_t cq_pad2(int64_t x) { return (x + 1) & ~int64_t(1); }
 

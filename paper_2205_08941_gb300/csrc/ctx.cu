@@ -8,7 +8,21 @@
 
 static std::atomic<int64_t> g_launches{0};
 extern "C" int64_t cq_kernel_launches(void) { return g_launches.load(); }
-void cq_count_launch(int64_t n) { g_launches.fetch_add(n); }
+static thread_local bool t_capturing = false;
+static thread_local int64_t t_captured = 0;
+void cq_count_launch(int64_t n)
+{
+    if (t_capturing)
+        t_captured += n;
+    else
+        g_launches.fetch_add(n);
+}
+void cq_capture_counting(bool on)
+{
+    t_capturing = on;
+    if (on) t_captured = 0;
+}
+int64_t cq_capture_launches(void) { return t_captured; }
 
 DevBuf::~DevBuf()
 {
@@ -60,11 +74,14 @@ cq_status cq_scratch(cq_ctx *ctx, const std::string &name, size_t bytes, void **
     auto &slot = ctx->scratch[name];
     if (!slot) slot.reset(new DevBuf());
     if (slot->bytes < bytes) {
+        if (ctx->capturing)
+            return cq_fail(ctx, CQ_ERR_INVALID, "scratch growth inside a graph capture");
         // make sure no queued kernel still uses the old buffer
         cq_status st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync");
         if (st != CQ_OK) return st;
         st = cq_alloc(ctx, *slot, bytes);
         if (st != CQ_OK) return st;
+        ctx->scratch_gen++;
     }
     *out = slot->ptr;
     return CQ_OK;
@@ -519,6 +536,20 @@ extern "C" cq_status cq_bsmm_work(cq_ctx *ctx, const cq_pattern *pA, const cq_pa
     return CQ_OK;
 }
 
+extern "C" cq_status cq_bsmm_config(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
+                                    const cq_pattern *pC, int32_t *lane_split_host,
+                                    int32_t *tuned_host)
+{
+    if (!ctx) return CQ_ERR_INVALID;
+    cq_status st = check_triple(ctx, pA, pB, pC);
+    if (st != CQ_OK) return st;
+    TaskList *tl = nullptr;
+    if ((st = cq_get_tasks(ctx, pA, pB, pC, &tl)) != CQ_OK) return st;
+    if (lane_split_host) *lane_split_host = cq_lane_split(tl);
+    if (tuned_host) *tuned_host = tl->q != 0;
+    return CQ_OK;
+}
+
 extern "C" cq_status cq_trace_prod(cq_ctx *ctx, const cq_pattern *pA, const double *A,
                                    const cq_pattern *pB, const double *B, double *out_host)
 {
@@ -543,7 +574,7 @@ extern "C" cq_status cq_dot(cq_ctx *ctx, const cq_pattern *p, const double *A, c
 
 void cq_timing_begin(cq_ctx *ctx, double flops, double mma_flops)
 {
-    if (!ctx->timing) return;
+    if (!ctx->timing || ctx->capturing) return;
     ctx->timed_mma_flops += mma_flops;
     if (ctx->ev_used == ctx->ev_pool.size()) {
         cudaEvent_t a, b;
@@ -557,7 +588,7 @@ void cq_timing_begin(cq_ctx *ctx, double flops, double mma_flops)
 
 void cq_timing_end(cq_ctx *ctx)
 {
-    if (!ctx->timing) return;
+    if (!ctx->timing || ctx->capturing) return;
     cudaEventRecord(ctx->ev_pool[ctx->ev_used].second, ctx->stream);
     ctx->ev_used++;
 }
@@ -566,6 +597,23 @@ extern "C" cq_status cq_ctx_set_timing(cq_ctx *ctx, int on)
 {
     if (!ctx) return CQ_ERR_INVALID;
     ctx->timing = on != 0;
+    return CQ_OK;
+}
+
+extern "C" cq_status cq_ctx_set_autotune(cq_ctx *ctx, int on)
+{
+    if (!ctx) return CQ_ERR_INVALID;
+    ctx->autotune = on != 0;
+    return CQ_OK;
+}
+
+extern "C" cq_status cq_ctx_set_graphs(cq_ctx *ctx, int on)
+{
+    if (!ctx) return CQ_ERR_INVALID;
+    if (on && ctx->stream == nullptr)
+        return cq_fail(ctx, CQ_ERR_INVALID,
+                       "graphs need a context on a created stream (the default stream cannot be captured)");
+    ctx->graphs = on != 0;
     return CQ_OK;
 }
 

@@ -237,9 +237,76 @@ struct cq_lnv {
     int max_corr = 5;
     double flops = 0.0;
     int products = 0;
+    // CUDA graphs of the evaluation phases, keyed (phase, source L, precision)
+    struct Graph {
+        bool warm = false;
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0;
+        double flops = 0.0;
+        int products = 0;
+        uint64_t gen = 0;  // context scratch generation at capture
+    };
+    std::map<std::tuple<int, const void *, int>, Graph> graphs;
+    ~cq_lnv()
+    {
+        for (auto &kv : graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    }
 };
 
 namespace {
+
+// Device-only phase `body` (products, traces, gradients; no host synchronisation).  With
+// graphs off it runs directly.  With graphs on it runs eagerly the first time (building task
+// lists and sizing scratch), is captured into a CUDA graph the second time and replayed
+// from then on; the graph's launches, flops and products are credited at every replay.
+template <class F>
+cq_status run_phase(cq_lnv *s, int phase, const void *key, F body)
+{
+    cq_ctx *ctx = s->ctx;
+    if (!ctx->graphs) return body();
+    cq_lnv::Graph &g = s->graphs[std::make_tuple(phase, key, (int)s->prec)];
+    if (g.exec && g.gen != ctx->scratch_gen) {
+        // a scratch buffer the graph reads was reallocated since the capture: capture again
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    if (!g.exec) {
+        if (!g.warm) {
+            g.warm = true;
+            return body();
+        }
+        const double f0 = s->flops;
+        const int p0 = s->products;
+        CQ_TRY(cq_check_cuda(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed),
+                             "begin capture"));
+        ctx->capturing = true;
+        cq_capture_counting(true);
+        cq_status st = body();
+        cq_capture_counting(false);
+        ctx->capturing = false;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+        g.launches = cq_capture_launches();
+        g.flops = s->flops - f0;
+        g.products = s->products - p0;
+        s->flops = f0;
+        s->products = p0;
+        if (st != CQ_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return st != CQ_OK ? st : cq_check_cuda(ctx, e, "end capture");
+        }
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CQ_TRY(cq_check_cuda(ctx, e, "graph instantiate"));
+        g.gen = ctx->scratch_gen;
+    }
+    CQ_TRY(cq_check_cuda(ctx, cudaGraphLaunch(g.exec, ctx->stream), "graph launch"));
+    cq_count_launch(g.launches);
+    s->flops += g.flops;
+    s->products += g.products;
+    return CQ_OK;
+}
 
 // E and N (per cell) at Lsrc from the five products a trial point needs (X, Y, U, R1, R3).
 cq_status lnv_energy_number(cq_lnv *s, const double *Lsrc, std::vector<double> &E,
@@ -248,16 +315,18 @@ cq_status lnv_energy_number(cq_lnv *s, const double *Lsrc, std::vector<double> &
     cq_ctx *ctx = s->ctx;
     double *X = s->X.as<double>(), *Y = s->Y.as<double>(), *U = s->U.as<double>();
     double *R1 = s->R1.as<double>(), *R3 = s->R3.as<double>();
-    CQ_TRY(bsmm(ctx, 1.0, s->pL, Lsrc, s->pS, s->S, 0.0, s->pX, X, s->prec, &s->flops));
-    CQ_TRY(bsmm(ctx, 1.0, s->pL, Lsrc, s->pS, s->H, 0.0, s->pX, Y, s->prec, &s->flops));
-    CQ_TRY(bsmm(ctx, 1.0, s->pS, s->S, s->pX, X, 0.0, s->pU, U, s->prec, &s->flops));
-    CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, Y, 0.0, s->pL, R1, s->prec, &s->flops));
-    CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, X, 0.0, s->pL, R3, s->prec, &s->flops));
-    s->products += 5;
-    CQ_TRY(trace_q(ctx, s->pX, X, s->pX, Y, 0));
-    CQ_TRY(trace_q(ctx, s->pL, Lsrc, s->pL, R1, 1));
-    CQ_TRY(trace_q(ctx, s->pX, X, s->pX, X, 2));
-    CQ_TRY(trace_q(ctx, s->pL, Lsrc, s->pL, R3, 3));
+    CQ_TRY(run_phase(s, 1, Lsrc, [&]() -> cq_status {
+        CQ_TRY(bsmm(ctx, 1.0, s->pL, Lsrc, s->pS, s->S, 0.0, s->pX, X, s->prec, &s->flops));
+        CQ_TRY(bsmm(ctx, 1.0, s->pL, Lsrc, s->pS, s->H, 0.0, s->pX, Y, s->prec, &s->flops));
+        CQ_TRY(bsmm(ctx, 1.0, s->pS, s->S, s->pX, X, 0.0, s->pU, U, s->prec, &s->flops));
+        CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, Y, 0.0, s->pL, R1, s->prec, &s->flops));
+        CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, X, 0.0, s->pL, R3, s->prec, &s->flops));
+        s->products += 5;
+        CQ_TRY(trace_q(ctx, s->pX, X, s->pX, Y, 0));
+        CQ_TRY(trace_q(ctx, s->pL, Lsrc, s->pL, R1, 1));
+        CQ_TRY(trace_q(ctx, s->pX, X, s->pX, X, 2));
+        return trace_q(ctx, s->pL, Lsrc, s->pL, R3, 3);
+    }));
     std::vector<std::vector<double>> t;
     CQ_TRY(fetch_q(ctx, s->nc, 4, t));
     E.resize(s->nc);
@@ -276,13 +345,15 @@ cq_status lnv_eval_n(cq_lnv *s)
 {
     cq_ctx *ctx = s->ctx;
     double *X = s->X.as<double>(), *U = s->U.as<double>(), *R3 = s->R3.as<double>();
-    CQ_TRY(bsmm(ctx, 1.0, s->pL, s->L, s->pS, s->S, 0.0, s->pX, X, s->prec, &s->flops));
-    CQ_TRY(bsmm(ctx, 1.0, s->pS, s->S, s->pX, X, 0.0, s->pU, U, s->prec, &s->flops));
-    CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, X, 0.0, s->pL, R3, s->prec, &s->flops));
-    s->products += 3;
-    CQ_TRY(trace_q(ctx, s->pX, X, s->pX, X, 0));
-    CQ_TRY(trace_q(ctx, s->pL, s->L, s->pL, R3, 1));
-    CQ_TRY(cq_lnv_gradient_n(ctx, s->pL, s->pU, U, R3, s->GN.as<double>()));
+    CQ_TRY(run_phase(s, 2, s->L, [&]() -> cq_status {
+        CQ_TRY(bsmm(ctx, 1.0, s->pL, s->L, s->pS, s->S, 0.0, s->pX, X, s->prec, &s->flops));
+        CQ_TRY(bsmm(ctx, 1.0, s->pS, s->S, s->pX, X, 0.0, s->pU, U, s->prec, &s->flops));
+        CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, X, 0.0, s->pL, R3, s->prec, &s->flops));
+        s->products += 3;
+        CQ_TRY(trace_q(ctx, s->pX, X, s->pX, X, 0));
+        CQ_TRY(trace_q(ctx, s->pL, s->L, s->pL, R3, 1));
+        return cq_lnv_gradient_n(ctx, s->pL, s->pU, U, R3, s->GN.as<double>());
+    }));
     std::vector<std::vector<double>> t;
     CQ_TRY(fetch_q(ctx, s->nc, 2, t));
     s->N.resize(s->nc);
@@ -297,14 +368,16 @@ cq_status lnv_eval_rest(cq_lnv *s)
     cq_ctx *ctx = s->ctx;
     double *X = s->X.as<double>(), *Y = s->Y.as<double>(), *U = s->U.as<double>();
     double *Z = s->Z.as<double>(), *R1 = s->R1.as<double>(), *R2 = s->R2.as<double>();
-    CQ_TRY(bsmm(ctx, 1.0, s->pL, s->L, s->pS, s->H, 0.0, s->pX, Y, s->prec, &s->flops));
-    CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, Y, 0.0, s->pL, R1, s->prec, &s->flops));
-    CQ_TRY(bsmm(ctx, 1.0, s->pS, s->S, s->pX, Y, 0.0, s->pU, Z, s->prec, &s->flops));
-    CQ_TRY(bsmm(ctx, 1.0, s->pU, Z, s->pX, X, 0.0, s->pL, R2, s->prec, &s->flops));
-    s->products += 4;
-    CQ_TRY(trace_q(ctx, s->pX, X, s->pX, Y, 0));
-    CQ_TRY(trace_q(ctx, s->pL, s->L, s->pL, R1, 1));
-    CQ_TRY(cq_lnv_gradient_e(ctx, s->pL, s->pU, Z, R1, R2, s->GE.as<double>()));
+    CQ_TRY(run_phase(s, 3, s->L, [&]() -> cq_status {
+        CQ_TRY(bsmm(ctx, 1.0, s->pL, s->L, s->pS, s->H, 0.0, s->pX, Y, s->prec, &s->flops));
+        CQ_TRY(bsmm(ctx, 1.0, s->pU, U, s->pX, Y, 0.0, s->pL, R1, s->prec, &s->flops));
+        CQ_TRY(bsmm(ctx, 1.0, s->pS, s->S, s->pX, Y, 0.0, s->pU, Z, s->prec, &s->flops));
+        CQ_TRY(bsmm(ctx, 1.0, s->pU, Z, s->pX, X, 0.0, s->pL, R2, s->prec, &s->flops));
+        s->products += 4;
+        CQ_TRY(trace_q(ctx, s->pX, X, s->pX, Y, 0));
+        CQ_TRY(trace_q(ctx, s->pL, s->L, s->pL, R1, 1));
+        return cq_lnv_gradient_e(ctx, s->pL, s->pU, Z, R1, R2, s->GE.as<double>());
+    }));
     std::vector<std::vector<double>> t;
     CQ_TRY(fetch_q(ctx, s->nc, 2, t));
     s->E.resize(s->nc);

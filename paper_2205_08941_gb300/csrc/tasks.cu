@@ -163,7 +163,11 @@ cq_status cq_get_tasks(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
                                          tl->tasks.as<int2>());
         cq_count_launch();
     }
-    if (!pC->uniform && n_c > 0) {
+    const int nbu = pC->geo->uniform_nb;
+    if (nbu == 9 || nbu == 4) {
+        tl->n_items = n_c * nbu;
+    } else if (n_c > 0) {
+        // prefix of block rows for the general kernel (any basis other than 4 or 9)
         void *v_items;
         if ((st = cq_scratch(ctx, "tk_items", sizeof(int64_t) * n_c, &v_items)) != CQ_OK) return st;
         if ((st = cq_alloc(ctx, tl->c_rowitem, sizeof(int64_t) * (n_c + 1))) != CQ_OK) return st;
@@ -172,6 +176,9 @@ cq_status cq_get_tasks(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
         cq_count_launch();
         if ((st = cq_scan_i64(ctx, (int64_t *)v_items, tl->c_rowitem.as<int64_t>(), n_c)) != CQ_OK)
             return st;
+        cudaMemcpyAsync(&tl->n_items, tl->c_rowitem.as<int64_t>() + n_c, sizeof(int64_t),
+                        cudaMemcpyDeviceToHost, s);
+        if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "task rows")) != CQ_OK) return st;
     }
     if ((st = cq_check_cuda(ctx, cudaGetLastError(), "task build")) != CQ_OK) return st;
     *out = tl.get();
