@@ -266,6 +266,58 @@ cq_status cq_lnv_state(const cq_lnv *lnv, cq_lnv_report *report_host);
 cq_status cq_lnv_step_flops(cq_lnv *lnv, double *flops_host);
 void cq_lnv_destroy(cq_lnv *lnv);
 
+/* ---------------------------------------------------------------- learned initial guess */
+
+/*
+ * A small network that predicts the density-matrix blocks of L from each atom pair's local
+ * environment, as a start for the LNV minimisation (which refines it and falls back to
+ * cq_pm_guess when its start is poor).  The paper's density-matrix optimisation needs a
+ * start; a learned one is this library's addition.  Pairs are the blocks (i, j), i <= j, of
+ * a one-cell P_L with a uniform basis of 4 or 9 orbitals; (j, i) is the transpose.
+ *
+ * Pair frame: e3 along r_j - r_i (on-site: toward i's nearest neighbour); e1 toward the atom
+ * nearest the midpoint (other than i, j; ties to the lowest index; atoms on the axis
+ * skipped), orthogonalised; e2 = e3 x e1.  Descriptor (64 floats): 10 Gaussians of r_ij
+ * (centres 1.6p, width 1.6) and, over atoms k of row i within 8 bohr of the midpoint,
+ * sum_k h_n(|r_k - m|) Y_a(frame direction) for 6 radial Gaussians (centres 1.6n, width
+ * 1.2, cosine cut at 8) and 9 real harmonics (1, z, x, y, (3z^2-1)/2, xz, yz, (x^2-y^2)/2,
+ * xy).  Targets: the block in the pair frame, D L_ij D^T (D the s/p/d orbital rotation),
+ * 81 floats (zero-padded for 4 orbitals).  Network: 64 -> 256 -> 256 -> 256 -> 81, SiLU
+ * hidden activations, BF16 weights (FP32 master copy) and FP32 accumulation, inputs and
+ * outputs normalised per column.  Training: MSE on normalised targets, Adam (0.9, 0.999,
+ * 1e-8).  fp32_weights != 0 makes the forward pass read the FP32 weights (test mode).
+ */
+typedef struct cq_guess cq_guess;
+cq_status cq_guess_create(cq_ctx *ctx, uint64_t seed, int32_t fp32_weights, cq_guess **out);
+void cq_guess_destroy(cq_guess *g);
+/* Number of pair blocks (i <= j) of pL. */
+cq_status cq_guess_pairs(cq_ctx *ctx, const cq_pattern *pL, int64_t *n_pairs_host);
+/* Descriptors (n_pairs x 64), frames (n_pairs x 9: rows e1, e2, e3) and, if pairs_dev is
+ * not NULL, the block index of each pair (n_pairs int32). */
+cq_status cq_guess_descriptors(cq_ctx *ctx, const cq_pattern *pL, float *desc_dev,
+                               float *frames_dev, int32_t *pairs_dev);
+/* Pair-frame targets (n_pairs x 81) of a converged L on pL. */
+cq_status cq_guess_targets(cq_ctx *ctx, const cq_pattern *pL, const double *L,
+                           const float *frames_dev, float *targets_dev);
+/* Per-column normalisation of inputs and targets from training data (rows samples). */
+cq_status cq_guess_fit_scale(cq_guess *g, const float *desc_dev, const float *targets_dev,
+                             int64_t rows);
+cq_status cq_guess_set_scale(cq_guess *g, const float *in_mean_host, const float *in_scale_host,
+                             const float *out_mean_host, const float *out_scale_host);
+/* Copy the FP32 weights and biases (layer by layer, row-major in x out) to (set = 0) or from
+ * (set != 0) host arrays of n_w and n_b floats; either pointer may be NULL. */
+cq_status cq_guess_params(cq_guess *g, float *w_host, float *b_host, int64_t *n_w,
+                          int64_t *n_b, int32_t set);
+/* One Adam step on a minibatch of rows samples (raw targets; lr = 0: loss and gradients
+ * only).  Optional host outputs: mean-square loss of the normalised targets, gradients. */
+cq_status cq_guess_train_step(cq_guess *g, const float *desc_dev, const float *targets_dev,
+                              int64_t rows, float lr, float *loss_host, float *grad_w_host,
+                              float *grad_b_host);
+/* Normalised network outputs (rows x 81). */
+cq_status cq_guess_forward(cq_guess *g, const float *desc_dev, int64_t rows, float *out_dev);
+/* L on pL from the network: every block predicted, rotated back, (j, i) = (i, j)^T. */
+cq_status cq_guess_apply(cq_guess *g, const cq_pattern *pL, double *L);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,18 @@ SIGNATURES = {
     "cq_ctx_set_autotune": (_st, [_vp, ctypes.c_int]),
     "cq_ctx_set_graphs": (_st, [_vp, ctypes.c_int]),
     "cq_bsmm_config": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "cq_guess_create": (_st, [_vp, ctypes.c_uint64, _i32, ctypes.POINTER(_vp)]),
+    "cq_guess_destroy": (None, [_vp]),
+    "cq_guess_pairs": (_st, [_vp, _vp, ctypes.POINTER(_i64)]),
+    "cq_guess_descriptors": (_st, [_vp, _vp, _vp, _vp, _vp]),
+    "cq_guess_targets": (_st, [_vp, _vp, _vp, _vp, _vp]),
+    "cq_guess_fit_scale": (_st, [_vp, _vp, _vp, _i64]),
+    "cq_guess_set_scale": (_st, [_vp, _vp, _vp, _vp, _vp]),
+    "cq_guess_params": (_st, [_vp, _vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i32]),
+    "cq_guess_train_step": (_st, [_vp, _vp, _vp, _i64, ctypes.c_float,
+                                  ctypes.POINTER(ctypes.c_float), _vp, _vp]),
+    "cq_guess_forward": (_st, [_vp, _vp, _i64, _vp]),
+    "cq_guess_apply": (_st, [_vp, _vp, _vp]),
 }
 
 
@@ -376,6 +388,102 @@ class Lnv:
     def close(self):
         if getattr(self, "h", None):
             lib().cq_lnv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Guess:
+    """Learned initial guess (cq_guess_*): descriptors, targets, training, apply."""
+
+    N_IN, N_OUT = 64, 81
+
+    def __init__(self, ctx: Context, seed: int = 0, fp32_weights: bool = False):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx._check(lib().cq_guess_create(ctx.h, int(seed), 1 if fp32_weights else 0,
+                                         ctypes.byref(h)))
+        self.h = h
+        ctx._children.add(self)
+
+    def pairs(self, pL) -> int:
+        n = ctypes.c_int64()
+        self.ctx._check(lib().cq_guess_pairs(self.ctx.h, pL.h, ctypes.byref(n)))
+        return int(n.value)
+
+    def descriptors(self, pL):
+        n = self.pairs(pL)
+        dev = f"cuda:{self.ctx.device}"
+        desc = torch.empty((max(n, 1), self.N_IN), dtype=torch.float32, device=dev)
+        frames = torch.empty((max(n, 1), 9), dtype=torch.float32, device=dev)
+        pairs = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        self.ctx._check(lib().cq_guess_descriptors(self.ctx.h, pL.h, _ptr(desc), _ptr(frames),
+                                                   _ptr(pairs)))
+        self.ctx.sync()
+        return desc[:n], frames[:n], pairs[:n]
+
+    def targets(self, pL, L, frames):
+        t = torch.empty((max(frames.shape[0], 1), self.N_OUT), dtype=torch.float32,
+                        device=frames.device)
+        self.ctx._check(lib().cq_guess_targets(self.ctx.h, pL.h, _ptr(L), _ptr(frames), _ptr(t)))
+        self.ctx.sync()
+        return t[:frames.shape[0]]
+
+    def fit_scale(self, desc, targets):
+        self.ctx._check(lib().cq_guess_fit_scale(self.h, _ptr(desc), _ptr(targets),
+                                                 int(desc.shape[0])))
+
+    def set_scale(self, in_mean, in_scale, out_mean, out_scale):
+        f = lambda a: (ctypes.c_float * len(a))(*[float(x) for x in a])
+        self.ctx._check(lib().cq_guess_set_scale(self.h, f(in_mean), f(in_scale), f(out_mean),
+                                                 f(out_scale)))
+
+    def params(self):
+        nw, nb = ctypes.c_int64(), ctypes.c_int64()
+        self.ctx._check(lib().cq_guess_params(self.h, None, None, ctypes.byref(nw),
+                                              ctypes.byref(nb), 0))
+        import numpy as np
+        w = np.zeros(nw.value, dtype=np.float32)
+        b = np.zeros(nb.value, dtype=np.float32)
+        self.ctx._check(lib().cq_guess_params(self.h, w.ctypes.data, b.ctypes.data, None, None, 0))
+        return w, b
+
+    def set_params(self, w, b):
+        import numpy as np
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        self.ctx._check(lib().cq_guess_params(self.h, w.ctypes.data, b.ctypes.data, None, None, 1))
+
+    def train_step(self, desc, targets, lr, grads=False):
+        import numpy as np
+        loss = ctypes.c_float()
+        gw = gb = None
+        if grads:
+            w, b = self.params()
+            gw, gb = np.zeros_like(w), np.zeros_like(b)
+        self.ctx._check(lib().cq_guess_train_step(
+            self.h, _ptr(desc), _ptr(targets), int(desc.shape[0]), float(lr), ctypes.byref(loss),
+            None if gw is None else gw.ctypes.data, None if gb is None else gb.ctypes.data))
+        return (float(loss.value), gw, gb) if grads else float(loss.value)
+
+    def forward(self, desc):
+        out = torch.empty((max(desc.shape[0], 1), self.N_OUT), dtype=torch.float32,
+                          device=desc.device)
+        self.ctx._check(lib().cq_guess_forward(self.h, _ptr(desc), int(desc.shape[0]), _ptr(out)))
+        self.ctx.sync()
+        return out[:desc.shape[0]]
+
+    def apply(self, pL, L):
+        self.ctx._check(lib().cq_guess_apply(self.h, pL.h, _ptr(L)))
+        return L
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cq_guess_destroy(self.h)
             self.h = None
 
     def __del__(self):
