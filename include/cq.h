@@ -175,6 +175,32 @@ cq_status cq_bsmm_work(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
 cq_status cq_trace_prod(cq_ctx *ctx, const cq_pattern *pA, const double *A,
                         const cq_pattern *pB, const double *B, double *out_host);
 
+/*
+ * Tr(A.B) as cq_trace_prod computes it, for callers that cannot allocate device memory when
+ * they need it: code running while a stream capture is open (cudaMalloc is not allowed in a
+ * global-mode capture), code whose device memory is owned by a framework with a fixed
+ * budget, or callers that hold no context.  (The paper has no counterpart: this is an
+ * interface variant, not part of the method.)
+ *
+ * It allocates nothing: its scratch, one FP64 partial per atom row, is a file-scope
+ * __device__ array of 65536 doubles (512 KiB) that every GPU loading the library keeps until
+ * the process exits; no cudaMalloc, cudaFree or allocating library routine is called.
+ * pA, A, pB, B are as for cq_trace_prod (existing patterns and values); out_dev is a device
+ * pointer that receives the trace; cuda_stream is the stream to enqueue on (NULL: legacy
+ * default stream).  The call is asynchronous: read out_dev after synchronising the stream.
+ * Patterns of more than 65536 atoms are rejected with CQ_ERR_INVALID.  On error,
+ * *message_host (if message_host is not NULL) points to a static description.
+ *
+ * The first call on a device looks up the array's device address with that device current
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  Every call
+ * shares the one array and leaves its contents behind; each call overwrites the rows it
+ * reads, but calls that overlap on the GPU (different streams or host threads) race on the
+ * array and must be serialised by the caller.
+ */
+cq_status cq_trace_prod_static(const cq_pattern *pA, const double *A, const cq_pattern *pB,
+                               const double *B, double *out_dev, void *cuda_stream,
+                               const char **message_host);
+
 /* Frobenius inner product <A, B> over the blocks of p.  Synchronises. */
 cq_status cq_dot(cq_ctx *ctx, const cq_pattern *p, const double *A, const double *B,
                  double *out_host);

@@ -101,7 +101,21 @@ SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_float), _vp, _vp]),
     "cq_guess_forward": (_st, [_vp, _vp, _i64, _vp]),
     "cq_guess_apply": (_st, [_vp, _vp, _vp]),
+    "cq_trace_prod_static": (_st, [_vp, _vp, _vp, _vp, _vp, _vp,
+                                   ctypes.POINTER(ctypes.c_char_p)]),
 }
+
+
+def trace_prod_static(pA, A, pB, B, out, stream=None):
+    """cq_trace_prod_static: Tr(A.B) into the device tensor `out` (one float64) without any
+    device allocation; asynchronous on `stream` (a torch.cuda.Stream, default: current)."""
+    st = stream or torch.cuda.current_stream()
+    msg = ctypes.c_char_p()
+    status = lib().cq_trace_prod_static(pA.h, _ptr(A), pB.h, _ptr(B), _ptr(out),
+                                        ctypes.c_void_p(st.cuda_stream), ctypes.byref(msg))
+    if status != CQ_OK:
+        raise CQError(status, msg.value.decode() if msg.value else "")
+    return out
 
 
 def _host_f64(values):
