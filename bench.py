@@ -50,7 +50,88 @@ def parse():
     ap.add_argument("--only-split", action="store_true",
                     help="skip the FP64 leg (profiling the tensor-core path)")
     ap.add_argument("--hotelling-steps", type=int, default=12)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--converge", action="store_true",
+                    help="time full minimisations (plain FP64 vs learned guess + split-BF16 + "
+                         "FP64 refinement) instead of the step benchmark")
     return ap.parse_args()
+
+
+BATCH_CELLS = [((3, 3, 3), 0.05, 14.0), ((4, 3, 3), 0.03, 16.0), ((4, 4, 3), 0.06, 12.0),
+               ((4, 4, 4), 0.045, 15.0)]
+
+
+def run_batch(args, dev):
+    """Batched heterogeneous cells (reduced form of the 32-cell workload): four cells of
+    216-512 atoms, densities 0.03-0.06 atoms/A^3, species mixed from 5/9/13 orbitals,
+    r_L 12-16 bohr (r_S = r_L - 2), solved as one batch: one launch per product for all
+    cells, per-cell scalars, LNV phases replayed as CUDA graphs, FP64 lane splits autotuned."""
+    import torch
+
+    from paper_2205_08941_gb300 import cq
+    from paper_2205_08941_gb300 import inputs as I
+    cells, Ss, Hs = [], [], []
+    for k, (shape, dens, rl) in enumerate(BATCH_CELLS):
+        cell = I.mixed_cell(shape, dens, 0.1, 3 + k)
+        S, H = I.overlap_hamiltonian_species(cell, I.silicon_model(rl - 2.0))
+        cells.append(cell)
+        Ss.append(S)
+        Hs.append(H)
+    pos, nb, start, boxes = I.concat_cells(cells)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    ctx = cq.Context(dev, stream=stream)
+    ctx.set_autotune(True)
+    t = lambda a, dt: torch.tensor(a, dtype=dt, device=f"cuda:{dev}")
+    rS = [c[2] - 2.0 for c in BATCH_CELLS]
+    rL = [c[2] for c in BATCH_CELLS]
+    pS = ctx.pattern_batch(t(pos, torch.float64), start, boxes, t(nb, torch.int32), rS)
+    pL = ctx.pattern_batch(t(pos, torch.float64), start, boxes, t(nb, torch.int32), rL)
+
+    def up(pairs_list):
+        i = np.concatenate([pb.i + start[k] for k, pb in enumerate(pairs_list)]).astype(np.int32)
+        j = np.concatenate([pb.j + start[k] for k, pb in enumerate(pairs_list)]).astype(np.int32)
+        sizes = np.concatenate([np.diff(pb.off) for pb in pairs_list])
+        off = np.zeros(sizes.shape[0] + 1, dtype=np.int64)
+        np.cumsum(sizes, out=off[1:])
+        v = np.concatenate([pb.values for pb in pairs_list])
+        return ctx.scatter(pS, t(i, torch.int32), t(j, torch.int32), t(off, torch.int64),
+                           t(v, torch.float64))
+
+    S, H = up(Ss), up(Hs)
+    T = ctx.zeros(pL)
+    torch.cuda.synchronize()
+    ctx.hotelling_init(pS, S, pL, T)
+    for _ in range(10):
+        ctx.hotelling_step(pS, S, pL, T)
+    n_occ = [2.0 * c.n_atoms for c in cells]
+    L = ctx.zeros(pL)
+    torch.cuda.synchronize()
+    ctx.pm_guess_cells(pS, S, H, pL, T, pL, L, n_occ)
+    ctx.set_graphs(True)
+    lnv = ctx.lnv_cells(pS, S, H, pL, L, [2 * x for x in n_occ])
+    for _ in range(2):  # eager once, captured on the second use
+        lnv.step()
+    n0 = cq.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 2
+    stream.synchronize()
+    e0.record(stream)
+    reps = [lnv.step() for _ in range(steps)]
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    flops = sum(r[0]["flops"] for r in reps)
+    out = {"workload": "4 cells, " + ", ".join(f"{c.n_atoms} atoms" for c in cells)
+                       + "; species 5/9/13 orbitals mixed per atom; reduced from 32 cells",
+           "value": flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "dtype": "f64",
+           "ms_per_step": ms / steps, "graphs": True, "autotune": True,
+           "gpu_launches": int(cq.kernel_launches() - n0),
+           "energy_per_atom": [r["energy"] / c.n_atoms for r, c in zip(reps[-1], cells)],
+           "gnorm": [r["gnorm"] for r in reps[-1]]}
+    lnv.close()
+    ctx.close()
+    return out
 
 
 def make_inputs(ncell):
@@ -326,6 +407,10 @@ def run_cq(args, rank, world, local_rank):
                                                 torch.linalg.vector_norm(L_fp64))
             split["speedup_vs_fp64_step"] = (res["fp64"]["ms"] / r["ms"])
 
+    batched = None
+    if not args.no_batch:
+        batched = run_batch(args, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g, times, f, cores, desc = oracle_sample(cell, Spb, Hpb)
@@ -357,6 +442,7 @@ def run_cq(args, rank, world, local_rank):
                          "launches": n_launch, "kernel_ms": kern_ms,
                          "kernel_share": kern_ms / ms if ms > 0 else None},
             "split": split,
+            "batched": batched,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": main["clk"],
@@ -371,8 +457,114 @@ def run_cq(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_converge(args, dev):
+    """Full minimisations on the 4096-atom cell, both to RMS gradient 1e-8:
+    (a) plain: PM start, FP64 LNV;
+    (b) learned: network trained on converged 216-atom cells (thermal jitter 0.1-0.3 bohr),
+        guarded learned start, split-BF16 LNV to RMS gradient 1e-6, FP64 refinement.
+    Times exclude pattern/task-list construction (shared, cached) and the one-off training."""
+    import torch
+
+    from paper_2205_08941_gb300 import build as B
+    B.build()
+    from paper_2205_08941_gb300 import cq, learned
+    from paper_2205_08941_gb300 import inputs as I
+    torch.cuda.set_device(dev)
+    ctx = cq.Context(dev)
+    t = lambda a, dt: torch.tensor(a, dtype=dt, device=f"cuda:{dev}")
+    rS, rL = WORKLOAD["r_S"], WORKLOAD["r_L"]
+
+    def setup(cell, Spb, Hpb, hsteps=12):
+        pos, nb = t(cell.pos, torch.float64), t(cell.nb, torch.int32)
+        pS, pL = ctx.pattern(pos, cell.box, nb, rS), ctx.pattern(pos, cell.box, nb, rL)
+        up = lambda p, pb: ctx.scatter(p, t(pb.i, torch.int32), t(pb.j, torch.int32),
+                                       t(pb.off, torch.int64), t(pb.values, torch.float64))
+        S, H = up(pS, Spb), up(pS, Hpb)
+        T = ctx.zeros(pL)
+        ctx.hotelling_init(pS, S, pL, T)
+        for _ in range(hsteps):
+            ctx.hotelling_step(pS, S, pL, T)
+        return pS, pL, S, H, T
+
+    def run(lnv, gtol, cap):
+        it, st = 0, lnv.state()
+        while st["gnorm"] > gtol and it < cap:
+            st = lnv.step()
+            it += 1
+        return it, st
+
+    # training set: converged L of small thermally displaced cells
+    t0 = time.perf_counter()
+    rng = np.random.default_rng(1000)
+    samples, keep = [], []
+    for k in range(6):
+        c = I.diamond_cell(3, a=WORKLOAD["a_bohr"], sigma=float(rng.uniform(0.1, 0.3)),
+                           seed=1000 + k, norb=9)
+        s_, h_ = I.overlap_hamiltonian(c, I.silicon_model(rS))
+        pS, pL, S, H, T = setup(c, s_, h_)
+        L = ctx.zeros(pL)
+        ctx.pm_guess(pS, S, H, pL, T, pL, L, 2.0 * c.n_atoms)
+        lnv = ctx.lnv(pS, S, H, pL, L, 4.0 * c.n_atoms)
+        run(lnv, 1e-7, 80)
+        lnv.close()
+        samples.append((pL, L))
+        keep.append((pS, S, H, T))
+    guess = cq.Guess(ctx, seed=11)
+    desc, targ = learned.training_set(guess, samples)
+    hist = learned.train(guess, desc, targ, epochs=60, batch=4096, lr=2e-3, lr_decay=0.96)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    n_samples = int(desc.shape[0])
+    del samples, keep, desc, targ
+
+    cell, Spb, Hpb = make_inputs(args.ncell)
+    n_e = 4.0 * cell.n_atoms
+    pS, pL, S, H, T = setup(cell, Spb, Hpb, args.hotelling_steps)
+    # (a) plain FP64 from the PM start
+    L = ctx.zeros(pL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.pm_guess(pS, S, H, pL, T, pL, L, n_e / 2.0)
+    lnv = ctx.lnv(pS, S, H, pL, L, n_e)
+    it_a, st_a = run(lnv, 1e-8, 120)
+    torch.cuda.synchronize()
+    t_a = time.perf_counter() - t0
+    lnv.close()
+    # (b) learned start, split-BF16 steps, FP64 refinement
+    L2 = ctx.zeros(pL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lnv, used, info = learned.guarded_start(ctx, guess, pS, S, H, pL, T, pL, L2, n_e,
+                                            prec=cq.CQ_SPLIT_BF16X3)
+    it_b1, st_b1 = run(lnv, 1e-6, 120)
+    t_b1 = time.perf_counter() - t0
+    lnv.set_precision(cq.CQ_FP64)
+    it_b2, st_b2 = run(lnv, 1e-8, 60)
+    torch.cuda.synchronize()
+    t_b = time.perf_counter() - t0
+    lnv.close()
+    line = {"mode": "converge", "workload": WORKLOAD["workload"], "n_atoms": cell.n_atoms,
+            "gradient_target_rms": 1e-8,
+            "plain_fp64": {"seconds": t_a, "steps": it_a, "energy": st_a["energy"],
+                           "gnorm": st_a["gnorm"]},
+            "learned_split_then_fp64": {
+                "seconds": t_b, "split_steps": it_b1, "split_seconds": t_b1,
+                "fp64_steps": it_b2, "energy": st_b2["energy"], "gnorm": st_b2["gnorm"],
+                "learned_start_used": used, "start": info},
+            "energy_diff_per_atom": abs(st_b2["energy"] - st_a["energy"]) / cell.n_atoms,
+            "speedup": t_a / t_b,
+            "training": {"cells": 6, "atoms_per_cell": 216, "samples": n_samples,
+                         "loss_first_last": [hist[0], hist[-1]], "seconds": t_train}}
+    print(json.dumps(line), flush=True)
+    guess.close()
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.converge:
+        run_converge(args, int(os.environ.get("LOCAL_RANK", 0)))
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -11,22 +11,28 @@
 // after the barrier of the MMAs that last read it has completed.
 constexpr int NS = 3;
 
+// block indices of this thread's row for the four atoms of chunk c (-1: absent)
 template <int NB>
-__device__ __forceinline__ void gather_chunk(const SplitArgs &p, uint8_t *stg, uint32_t sbase,
-                                             int64_t kb, int64_t kn, int c, bool a_role,
-                                             bool b_role, int grow, int slot, int o)
+__device__ __forceinline__ void load_index(const SplitArgs &p, int64_t kb, int64_t kn, int c,
+                                           int slot, int32_t blk[4])
 {
     constexpr int GI = MT / NB, GJ = NT / NB, W = GI + GJ;
-    if (!(a_role || b_role)) return;
-    const uint32_t dbase = a_role ? sbase : sbase + 3 * A_PLANE;
-    uint8_t *gbase = a_role ? stg : stg + 3 * A_PLANE;
-    const int plane = a_role ? A_PLANE : B_PLANE;
-    int32_t blk[4];
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
         const int64_t kidx = (int64_t)c * 4 + kk;
         blk[kk] = (slot >= 0 && kidx < kn) ? p.table[(kb + kidx) * W + slot] : -1;
     }
+}
+
+template <int NB>
+__device__ __forceinline__ void gather_chunk(const SplitArgs &p, uint8_t *stg, uint32_t sbase,
+                                             const int32_t blk[4], bool a_role, bool b_role,
+                                             int grow, int o)
+{
+    if (!(a_role || b_role)) return;
+    const uint32_t dbase = a_role ? sbase : sbase + 3 * A_PLANE;
+    uint8_t *gbase = a_role ? stg : stg + 3 * A_PLANE;
+    const int plane = a_role ? A_PLANE : B_PLANE;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
 #pragma unroll
@@ -111,16 +117,20 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
 #pragma unroll
         for (int x = 0; x < 32; ++x) hi[x] = lo[x] = 0.f;
         const int nch = (int)((kn + 3) / 4);
-        // prologue: the first NS-1 chunks
+        // prologue: the first NS-1 chunks; nxt holds the indices of the next chunk to gather,
+        // loaded one iteration ahead so the gather waits for one memory round trip only
+        int32_t nxt[4];
         for (int c = 0; c < NS - 1 && c < nch; ++c) {
             if (!free_stage(c % NS)) {
                 failed = true;
                 break;
             }
-            gather_chunk<NB>(p, smem + (c % NS) * STAGE, sm0 + (c % NS) * STAGE, kb, kn, c,
-                             a_role, b_role, grow, slot, o);
+            load_index<NB>(p, kb, kn, c, slot, nxt);
+            gather_chunk<NB>(p, smem + (c % NS) * STAGE, sm0 + (c % NS) * STAGE, nxt, a_role,
+                             b_role, grow, o);
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
+        load_index<NB>(p, kb, kn, NS - 1, slot, nxt);
         for (int c = 0; c < nch && !failed; ++c) {
             const int s = c % NS;
             if (c + 1 < nch)
@@ -159,9 +169,10 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
                     failed = true;
                     break;
                 }
-                gather_chunk<NB>(p, smem + (cn % NS) * STAGE, sm0 + (cn % NS) * STAGE, kb, kn, cn,
-                                 a_role, b_role, grow, slot, o);
+                gather_chunk<NB>(p, smem + (cn % NS) * STAGE, sm0 + (cn % NS) * STAGE, nxt,
+                                 a_role, b_role, grow, o);
                 asm volatile("cp.async.commit_group;" ::: "memory");
+                load_index<NB>(p, kb, kn, cn + 1, slot, nxt);
             }
             if (c % DRAIN == DRAIN - 1 || c == nch - 1) {
                 if (!free_stage(s)) {
