@@ -37,6 +37,10 @@ WORKLOAD = {"workload": "Si diamond 4096 atoms SZP (9 orb/atom, 36864 orbitals)"
 BF16_FALLBACK_TFLOPS = 1900.0
 
 
+def workload_name(n_atoms):
+    return f"Si diamond {n_atoms} atoms SZP (9 orb/atom, {9 * n_atoms} orbitals)"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -431,7 +435,8 @@ def run_cq(args, rank, world, local_rank):
             "s_per_lnv_step": ms / args.steps / 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if "fp64" in res else "bf16x3", "data": "synthetic",
-            "config": dict(WORKLOAD, n_atoms=cell.n_atoms, parallelism=f"replicas x{world}",
+            "config": dict(WORKLOAD, workload=workload_name(cell.n_atoms), ncell=args.ncell,
+                           n_atoms=cell.n_atoms, parallelism=f"replicas x{world}",
                            l2="inputs larger than L2 (U, Z 6.9 GB each)",
                            hotelling_resid=resid[-1] if resid else None),
             "roofline": {"bound": "alu", "kernel": "k_bsmm_f64_uniform",
@@ -450,6 +455,8 @@ def run_cq(args, rank, world, local_rank):
             "lnv": [{k: x[k] for k in ("energy", "n_elec", "gnorm", "alpha", "n_corr",
                                        "n_products")} for x in main["reps"]],
         }
+        if "fp64" not in res:
+            line["roofline"] = split["roofline"]
         print(json.dumps(line), flush=True)
     lnv.close()
     ctx.close()
