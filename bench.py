@@ -37,6 +37,45 @@ WORKLOAD = {"workload": "Si diamond 4096 atoms SZP (9 orb/atom, 36864 orbitals)"
 BF16_FALLBACK_TFLOPS = 1900.0
 
 
+METRIC = ("block-sparse GEMM GFLOP/s (useful FP64 flops) & s per LNV step, Si SZP; "
+          "FP64 (value) and split-BF16 (split)")
+
+
+class Replicas:
+    """N independent replicas, one per rank (the path has no exchange step): a barrier that
+    also drains the device, the maximum of a per-rank time, and the sum of per-rank work.
+    `dist` is torch.distributed with an initialised group, or None for one process."""
+
+    def __init__(self, dist, device):
+        self.dist, self.device = dist, device
+
+    def barrier(self):
+        import torch
+        if self.device.type == "cuda":
+            torch.cuda.synchronize(self.device)
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+        tt = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(tt, op=op)
+        return float(tt.item())
+
+    def max(self, x):
+        return self._reduce(x, self.dist.ReduceOp.MAX if self.dist else None)
+
+    def sum(self, x):
+        return self._reduce(x, self.dist.ReduceOp.SUM if self.dist else None)
+
+    def rate(self, units, ms):
+        """Whole-job throughput: the units all ranks processed over the slowest rank's time
+        (ms), in units per second."""
+        return self.sum(units) / (self.max(ms) * 1e-3)
+
+
 def workload_name(n_atoms):
     return f"Si diamond {n_atoms} atoms SZP (9 orb/atom, {9 * n_atoms} orbitals)"
 
@@ -65,7 +104,7 @@ BATCH_CELLS = [((3, 3, 3), 0.05, 14.0), ((4, 3, 3), 0.03, 16.0), ((4, 4, 3), 0.0
                ((4, 4, 4), 0.045, 15.0)]
 
 
-def run_batch(args, dev):
+def run_batch(args, dev, rep):
     """Batched heterogeneous cells (reduced form of the 32-cell workload): four cells of
     216-512 atoms, densities 0.03-0.06 atoms/A^3, species mixed from 5/9/13 orbitals,
     r_L 12-16 bohr (r_S = r_L - 2), solved as one batch: one launch per product for all
@@ -124,8 +163,8 @@ def run_batch(args, dev):
     reps = [lnv.step() for _ in range(steps)]
     e1.record(stream)
     stream.synchronize()
-    ms = e0.elapsed_time(e1)
-    flops = sum(r[0]["flops"] for r in reps)
+    ms = rep.max(e0.elapsed_time(e1))
+    flops = rep.sum(sum(r[0]["flops"] for r in reps))  # r[0]: the batch total, on every cell
     out = {"workload": "4 cells, " + ", ".join(f"{c.n_atoms} atoms" for c in cells)
                        + "; species 5/9/13 orbitals mixed per atom; reduced from 32 cells",
            "value": flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "dtype": "f64",
@@ -253,11 +292,13 @@ def run_reference(args, rank, world):
             secs.append(t[0])
         sample = (cores, desc)
     v = sum(vals) / len(vals)
-    line = {"impl": "reference", "metric": "block-sparse GEMM GFLOP/s (useful FP64 flops)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": v, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(WORKLOAD, parallelism="cpu oracle"),
+            "data": "synthetic",
+            "config": dict(WORKLOAD, workload=workload_name(cell.n_atoms), ncell=args.ncell,
+                           n_atoms=cell.n_atoms, parallelism="cpu oracle"),
             "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": sample[0],
                              "kind": "oracle", "sample": sample[1]},
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
@@ -280,18 +321,8 @@ def run_cq(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-
-    def barrier():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        tt = torch.tensor([x], device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
+    rep = Replicas(dist, torch.device("cuda", dev))
+    barrier = rep.barrier
 
     cell, Spb, Hpb = make_inputs(args.ncell)
     ctx = cq.Context(dev)
@@ -332,10 +363,11 @@ def run_cq(args, rank, world, local_rank):
         e1.record(stream)
         barrier()
         clk = clocks.stop()
-        ms = max_over_ranks(e0.elapsed_time(e1))
+        ms = rep.max(e0.elapsed_time(e1))
+        flops_all = rep.sum(sum(x["flops"] for x in reps))
         stats = ctx.kernel_stats()
         ctx.set_timing(False)
-        return {"reps": reps, "ms": ms, "clk": clk, "stats": stats,
+        return {"reps": reps, "ms": ms, "clk": clk, "stats": stats, "flops_all": flops_all,
                 "launches": cq.kernel_launches() - launches0}
 
     for _ in range(args.warmup):
@@ -367,8 +399,8 @@ def run_cq(args, rank, world, local_rank):
             fl2 += r["flops"]
         e3.record(stream)
         barrier()
-        ms2 = max_over_ranks(e2.elapsed_time(e3))
-        e2e = {"value": world * fl2 / (ms2 * 1e-3) / 1e9, "unit": "GFLOP/s",
+        ms2 = rep.max(e2.elapsed_time(e3))
+        e2e = {"value": rep.sum(fl2) / (ms2 * 1e-3) / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": int(L.numel() * 8),
                "d2h_bytes_per_step": int(L.numel() * 8 + 96),
                "ms_per_step": ms2 / k2}
@@ -384,10 +416,9 @@ def run_cq(args, rank, world, local_rank):
         res["split"] = timed(args.steps, "split")
         r = res["split"]
         n_launch, kern_ms, kern_flops, mma_flops = r["stats"]
-        flops = sum(x["flops"] for x in r["reps"])
         peaks = measured_peaks()
         bf16 = (peaks or {}).get("bf16_tflops")
-        split = {"value": world * flops / (r["ms"] * 1e-3) / 1e9, "unit": "GFLOP/s",
+        split = {"value": r["flops_all"] / (r["ms"] * 1e-3) / 1e9, "unit": "GFLOP/s",
                  "dtype": "bf16x3 split, fp32 accumulate, fp64 traces",
                  "ms_per_step": r["ms"] / args.steps, "s_per_lnv_step": r["ms"] / args.steps / 1e3,
                  "roofline": {"bound": "tensor", "kernel": "k_bsmm_split",
@@ -413,7 +444,7 @@ def run_cq(args, rank, world, local_rank):
 
     batched = None
     if not args.no_batch:
-        batched = run_batch(args, dev)
+        batched = run_batch(args, dev, rep)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -424,13 +455,11 @@ def run_cq(args, rank, world, local_rank):
     if rank == 0:
         main = res.get("fp64") or res.get("split")
         n_launch, kern_ms, kern_flops, mma_flops = main["stats"]
-        flops = sum(x["flops"] for x in main["reps"])
         ms = main["ms"]
         achieved = kern_flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
         line = {
-            "metric": "block-sparse GEMM GFLOP/s (useful FP64 flops) & s per LNV step, "
-                      "4096-atom Si SZP; FP64 (value) and split-BF16 (split)",
-            "value": world * flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": world,
+            "metric": METRIC,
+            "value": main["flops_all"] / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "s_per_lnv_step": ms / args.steps / 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
