@@ -522,6 +522,9 @@ def run_converge(args, dev):
             ctx.hotelling_step(pS, S, pL, T)
         return pS, pL, S, H, T
 
+    def rel(x, ref):
+        return float(torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref))
+
     def run(lnv, gtol, cap):
         it, st = 0, lnv.state()
         while st["gnorm"] > gtol and it < cap:
@@ -574,12 +577,13 @@ def run_converge(args, dev):
                                             prec=cq.CQ_SPLIT_BF16X3)
     it_b1, st_b1 = run(lnv, 1e-6, 120)
     t_b1 = time.perf_counter() - t0
+    L2_split = L2.clone()  # the split-only solution, compared after the timings
     lnv.set_precision(cq.CQ_FP64)
     it_b2, st_b2 = run(lnv, 1e-8, 60)
     torch.cuda.synchronize()
     t_b = time.perf_counter() - t0
     lnv.close()
-    line = {"mode": "converge", "workload": WORKLOAD["workload"], "n_atoms": cell.n_atoms,
+    line = {"mode": "converge", "workload": workload_name(cell.n_atoms), "n_atoms": cell.n_atoms,
             "gradient_target_rms": 1e-8,
             "plain_fp64": {"seconds": t_a, "steps": it_a, "energy": st_a["energy"],
                            "gnorm": st_a["gnorm"]},
@@ -588,6 +592,10 @@ def run_converge(args, dev):
                 "fp64_steps": it_b2, "energy": st_b2["energy"], "gnorm": st_b2["gnorm"],
                 "learned_start_used": used, "start": info},
             "energy_diff_per_atom": abs(st_b2["energy"] - st_a["energy"]) / cell.n_atoms,
+            "L_rel_diff": rel(L2, L),
+            "split_only_vs_fp64": {  # split-BF16 solution at RMS gradient 1e-6, before refinement
+                "energy_err_per_atom": abs(st_b1["energy"] - st_a["energy"]) / cell.n_atoms,
+                "L_rel_diff": rel(L2_split, L)},
             "speedup": t_a / t_b,
             "training": {"cells": 6, "atoms_per_cell": 216, "samples": n_samples,
                          "loss_first_last": [hist[0], hist[-1]], "seconds": t_train}}

@@ -159,7 +159,11 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  * P_B (the sparse matrix multiplication of the paper's Background and Exascale sections).
  * With beta == 0 the old C is not read.  The (i, k, j) task list of each (P_A, P_B, P_C)
  * triple is built on the device on first use and cached in the context.  C must not alias
- * A or B.  prec selects FP64 FMAs or the split-BF16 tensor-core product.
+ * A or B.  prec selects FP64 FMAs or the split-BF16 tensor-core product.  The call is
+ * asynchronous on the context stream; if a bounded wait inside the split kernel ran out (a
+ * tensor-core completion not seen within about two seconds), the next synchronising call on
+ * the context (cq_ctx_sync, a trace, a dot, an LNV or Hotelling step) returns
+ * CQ_ERR_TIMEOUT and C is incomplete.
  */
 cq_status cq_bsmm(cq_ctx *ctx, double alpha, const cq_pattern *pA, const double *A,
                   const cq_pattern *pB, const double *B, double beta,

@@ -186,6 +186,10 @@ cq_status cq_scan_i64(cq_ctx *ctx, const int64_t *in, int64_t *out, int64_t n)
     return scan_level(ctx, in, out, n, 0);
 }
 
+// Device error bits that asynchronous kernels leave for the next synchronising call (the
+// pattern and scatter bits are read by their own calls before they return).
+constexpr int32_t CQ_FLAG_WAIT_TIMEOUT = 16;
+
 cq_status cq_read_flag(cq_ctx *ctx, int32_t *flag)
 {
     cq_status st = cq_check_cuda(
@@ -195,9 +199,31 @@ cq_status cq_read_flag(cq_ctx *ctx, int32_t *flag)
     st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync");
     if (st != CQ_OK) return st;
     std::memcpy(flag, ctx->host_out, sizeof(int32_t));
-    if (*flag)
-        return cq_check_cuda(ctx, cudaMemsetAsync(ctx->flag.ptr, 0, 4, ctx->stream), "flag");
-    return CQ_OK;
+    if (!*flag) return CQ_OK;
+    st = cq_check_cuda(ctx, cudaMemsetAsync(ctx->flag.ptr, 0, 4, ctx->stream), "flag");
+    if (st == CQ_OK && (*flag & CQ_FLAG_WAIT_TIMEOUT))
+        return cq_fail(ctx, CQ_ERR_TIMEOUT,
+                       "split product: a tensor-core wait ran out; the result is incomplete");
+    return st;
+}
+
+// Copies the flag word into the last pinned slot with the stream's other work; after the
+// stream is synchronised, reports (and clears) a wait that ran out on the device.
+static cq_status queue_flag_read(cq_ctx *ctx)
+{
+    return cq_check_cuda(ctx, cudaMemcpyAsync(ctx->host_out + CQ_RED_SLOTS - 1, ctx->flag.ptr,
+                                              sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                              ctx->stream), "flag read");
+}
+
+static cq_status check_async_flag(cq_ctx *ctx)
+{
+    int32_t f;
+    std::memcpy(&f, ctx->host_out + CQ_RED_SLOTS - 1, sizeof(int32_t));
+    if (!(f & CQ_FLAG_WAIT_TIMEOUT)) return CQ_OK;
+    cudaMemsetAsync(ctx->flag.ptr, 0, 4, ctx->stream);
+    return cq_fail(ctx, CQ_ERR_TIMEOUT,
+                   "split product: a tensor-core wait ran out; the result is incomplete");
 }
 
 cq_status cq_fetch(cq_ctx *ctx, int first, int count, double *host)
@@ -207,8 +233,10 @@ cq_status cq_fetch(cq_ctx *ctx, int first, int count, double *host)
                              sizeof(double) * count, cudaMemcpyDeviceToHost, ctx->stream),
         "scalar read");
     if (st != CQ_OK) return st;
+    if ((st = queue_flag_read(ctx)) != CQ_OK) return st;
     st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync");
     if (st != CQ_OK) return st;
+    if ((st = check_async_flag(ctx)) != CQ_OK) return st;
     for (int e = 0; e < count; ++e) {
         host[e] = ctx->host_out[e];
         if (!std::isfinite(host[e]))
@@ -277,7 +305,11 @@ extern "C" const char *cq_last_error(const cq_ctx *ctx) { return ctx ? ctx->err.
 extern "C" cq_status cq_ctx_sync(cq_ctx *ctx)
 {
     if (!ctx) return CQ_ERR_INVALID;
-    return cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "stream");
+    cq_status st = queue_flag_read(ctx);
+    if (st != CQ_OK) return st;
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "stream")) != CQ_OK)
+        return st;
+    return check_async_flag(ctx);
 }
 
 extern "C" cq_status cq_ctx_set_mem_limit(cq_ctx *ctx, int64_t bytes)
