@@ -12,23 +12,24 @@
 // tile a group of floor(64/nb) atoms.  A work tile is a pair (M group g, N group h) that
 // holds at least one block of P_C; its K list is every atom k with (i, k) in P_A for some
 // i in g and (k, j) in P_B for some j in h (built on the device with shared-memory
-// bitmaps).  Along K each atom's orbitals are padded to 16 so that an atom is exactly two
-// 8x8 core matrices; a K chunk is four atoms (64).  Absent blocks are zero in shared
-// memory.  Every C block belongs to exactly one tile, so there are no atomics.
+// bitmaps).  Absent blocks are zero in shared memory.  Every C block belongs to exactly one
+// tile, so there are no atomics.
 //
-// Operands are pre-split once per product into padded BF16 planes ("A form": rows = left
-// orbital, 16 K values = right orbital; "B form": rows = right orbital, K = left orbital),
-// so the tile kernel only moves 16-byte pieces with cp.async into the canonical no-swizzle
-// K-major layout (core matrix = 8 rows x 16 bytes; LBO = 128 B between K-adjacent core
-// matrices, SBO = 1024 B between 8-row groups) and one thread issues the MMAs.
+// K layout.  Along K an atom's orbitals are split into a "main" piece of 8 values (one
+// 16-byte core-matrix row) and a "tail" of 4 values (half a core-matrix row; for nb = 9:
+// orbital 8 and three zeros, for nb = 4: all four orbitals).  A K chunk of 48 values (six
+// core-matrix columns, three MMA K steps) holds 4 atoms of 9 orbitals (mains in columns
+// 0-3, tails paired in columns 4-5) or 12 atoms of 4 orbitals (tails only), so 9-orbital
+// atoms cost 12 K values instead of 16.
 //
-// Pipeline per CTA (256 threads; warps w and w+4 share TMEM lane quarter w and split the
-// 64 accumulator columns; one CTA per SM): three shared stages; while the tensor core runs
-// chunk c, the gathers of chunks c+1 and c+2 are in flight; an mbarrier per stage
-// (tcgen05.commit) tells when a stage is free.  Gathers read per-tile block-index tables,
-// so no load in the hot loop depends on another.
-// Every wait is bounded (about a second); on timeout the kernel records an error flag,
-// stops issuing work, waits (bounded) for its own MMAs, frees its TMEM and returns.
+// Operands are pre-split once per product into BF16 planes ("A form": rows = left orbital,
+// K = right orbital; "B form": rows = right orbital, K = left orbital), each as a main
+// array (8 values per block row) and a tail array (4 values per block row), so the tile
+// kernel only moves aligned 16- and 8-byte pieces with cp.async into the canonical
+// no-swizzle K-major layout (core matrix = 8 rows x 16 bytes; LBO = 128 B between
+// K-adjacent core matrices, SBO = 768 B between 8-row groups) and one thread issues the
+// MMAs.  Producer warps, the MMA thread and the drain warps hand stages and the two TMEM
+// accumulators to one another through mbarriers (bsmm_split_kernel.cuh).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -39,33 +40,48 @@
 
 namespace {
 
-constexpr int ST = 256;                      // threads per CTA (two warpgroups)
-constexpr int MT = 128, NT = 64, KCH = 64;   // tile M, N and K chunk
-constexpr int KP = 16;                       // padded orbitals per atom along K
-constexpr int A_PLANE = MT * KCH * 2;        // 16 KB
-constexpr int B_PLANE = NT * KCH * 2;        // 8 KB
+constexpr int ST = 384;                      // threads per CTA (12 warps)
+constexpr int MT = 128, NT = 64, KCH = 48;   // tile M, N and K chunk
+constexpr int KSTEPS = KCH / 16;             // MMA K steps per chunk
+constexpr int TAILW = 4;                     // values in an atom's tail piece
+constexpr int SBO = (KCH / 8) * 128;         // bytes between 8-row groups
+constexpr int A_PLANE = MT * KCH * 2;        // 12 KB
+constexpr int B_PLANE = NT * KCH * 2;        // 6 KB
 constexpr int STAGE = 3 * A_PLANE + 3 * B_PLANE;
-constexpr int SMEM = 3 * STAGE + 64;  // three pipeline stages + barriers
+constexpr int BAR_BYTES = 256;
 constexpr int DRAIN = 4;                     // chunks per FP32 accumulation period
-constexpr int TMEM_COLS = 64;
+constexpr int TMEM_COLS = 2 * NT;            // two FP32 accumulators
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+// Atoms per chunk and core-matrix columns of an atom's pieces.
+template <int NB> struct KLayout;
+template <> struct KLayout<9> {
+    static constexpr int CA = 4, MAINW = 8;
+    __device__ static constexpr int main_col(int a) { return a; }
+    __device__ static constexpr int tail_col(int a) { return 4 + (a >> 1); }
+};
+template <> struct KLayout<4> {
+    static constexpr int CA = 12, MAINW = 0;
+    __device__ static constexpr int main_col(int) { return 0; }
+    __device__ static constexpr int tail_col(int a) { return a >> 1; }
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// byte offset of (row, 16-byte K column) in the canonical no-swizzle K-major layout
-__device__ __forceinline__ uint32_t cm_off(int row, int kc)
+// byte offset of (row, core-matrix column, byte) in the canonical no-swizzle K-major layout
+__device__ __forceinline__ uint32_t tile_off(int row, int col, int byte)
 {
-    return (uint32_t)((row >> 3) * 1024 + kc * 128 + (row & 7) * 16);
+    return (uint32_t)((row >> 3) * SBO + col * 128 + (row & 7) * 16 + byte);
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
 {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
     d |= (uint64_t)(128 >> 4) << 16;    // leading (K) byte offset
-    d |= (uint64_t)(1024 >> 4) << 32;   // stride (M/N) byte offset
+    d |= (uint64_t)(SBO >> 4) << 32;    // stride (M/N) byte offset
     d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
     return d;                           // base offset 0, no swizzle
 }
@@ -84,30 +100,55 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16 &b0, __nv_bfloat1
     b2 = __double2bfloat16(r);
 }
 
-// A form: block b = (i, k) -> rows r < NB (orbital of i), 16 K values (orbital of k).
-__global__ void k_split_a(int64_t n, int nb, int stride, const double *__restrict__ A,
-                          __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2)
+struct SplitPlanes {
+    __nv_bfloat16 *main[3], *tail[3];
+};
+
+// Position of K value m of a block row in the main/tail arrays of a plane.
+__device__ __forceinline__ int64_t piece_index(int64_t row, int m, int mainw, int64_t n_rows,
+                                               bool &in_tail)
 {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const int per = nb * KP;
-    const int64_t b = e / per;
-    const int rem = (int)(e - b * per), r = rem / KP, m = rem % KP;
-    const double x = m < nb ? A[b * stride + r * nb + m] : 0.0;
-    split3(x, p0[e], p1[e], p2[e]);
+    in_tail = m >= mainw;
+    return in_tail ? row * TAILW + (m - mainw) : row * mainw + m;
 }
 
-// B form: block b = (k, j) -> rows n < NB (orbital of j), 16 K values (orbital of k).
-__global__ void k_split_b(int64_t n, int nb, int stride, const double *__restrict__ B,
-                          __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2)
+// A form: block b = (i, k) -> row r < nb (orbital of i), K value m (orbital of k).
+// One thread per (block, row, m < mainw + 4); writes three planes of main and tail arrays.
+__global__ void k_split_a(int64_t n, int nb, int mainw, int stride, const double *__restrict__ A,
+                          SplitPlanes out)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
-    const int per = nb * KP;
-    const int64_t b = e / per;
-    const int rem = (int)(e - b * per), r = rem / KP, m = rem % KP;
+    const int ka = mainw + TAILW;
+    const int64_t row = e / ka;
+    const int m = (int)(e - row * ka);
+    const int64_t b = row / nb;
+    const int r = (int)(row - b * nb);
+    const double x = m < nb ? A[b * stride + r * nb + m] : 0.0;
+    bool in_tail;
+    const int64_t q = piece_index(row, m, mainw, 0, in_tail);
+    __nv_bfloat16 v[3];
+    split3(x, v[0], v[1], v[2]);
+    for (int pl = 0; pl < 3; ++pl) (in_tail ? out.tail[pl] : out.main[pl])[q] = v[pl];
+}
+
+// B form: block b = (k, j) -> row n < nb (orbital of j), K value m (orbital of k).
+__global__ void k_split_b(int64_t n, int nb, int mainw, int stride, const double *__restrict__ B,
+                          SplitPlanes out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int ka = mainw + TAILW;
+    const int64_t row = e / ka;
+    const int m = (int)(e - row * ka);
+    const int64_t b = row / nb;
+    const int r = (int)(row - b * nb);
     const double x = m < nb ? B[b * stride + m * nb + r] : 0.0;
-    split3(x, p0[e], p1[e], p2[e]);
+    bool in_tail;
+    const int64_t q = piece_index(row, m, mainw, 0, in_tail);
+    __nv_bfloat16 v[3];
+    split3(x, v[0], v[1], v[2]);
+    for (int pl = 0; pl < 3; ++pl) (in_tail ? out.tail[pl] : out.main[pl])[q] = v[pl];
 }
 
 // Tile existence: bit (g, h) for every C block (i, j).
@@ -218,26 +259,19 @@ k_tile_index(const int2 *tiles, int gi, int gj, const int32_t *g_atoms, const in
     }
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
+// cp.async of 16 or 8 bytes; src_bytes = 0 writes zeros and reads nothing
+__device__ __forceinline__ void cp16z(uint32_t dst, const void *src, uint32_t src_bytes)
 {
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > WAIT_CYCLES) return false;
-    }
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
 }
 
-__device__ __forceinline__ void cp16(uint32_t dst, const void *src)
+__device__ __forceinline__ void cp8z(uint32_t dst, const void *src, uint32_t src_bytes)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
 }
 
 __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x)
@@ -259,7 +293,7 @@ struct SplitArgs {
     const int64_t *a_rp, *b_rp, *c_rp;
     const int32_t *a_col, *b_col, *c_col;
     const int64_t *b_tr;
-    const __nv_bfloat16 *sa[3], *sb[3];
+    const __nv_bfloat16 *sa_main[3], *sa_tail[3], *sb_main[3], *sb_tail[3];
     double *C;
     int c_stride;
     double alpha, beta;
@@ -268,10 +302,12 @@ struct SplitArgs {
 
 #include "bsmm_split_kernel.cuh"
 
+constexpr int SMEM = NS * STAGE + BAR_BYTES;  // pipeline stages + barriers
+
 // ---------------------------------------------------------------- host side
 
 struct Groups {
-    int gi = 0, gj = 0, n_g = 0, n_h = 0;
+    int gi = 0, gj = 0, n_g = 0, n_h = 0, ca = 0;  // atoms per M, N group; atoms per K chunk
     DevBuf g_atoms, h_atoms, g_of, h_of;
 };
 
@@ -323,6 +359,7 @@ cq_status get_groups(cq_ctx *ctx, const cq_pattern *p, Groups **out)
     const int nb = g.uniform_nb;
     gr->gi = MT / nb;
     gr->gj = NT / nb;
+    gr->ca = nb == 9 ? KLayout<9>::CA : KLayout<4>::CA;
     gr->n_g = (g.n_atoms + gr->gi - 1) / gr->gi;
     gr->n_h = (g.n_atoms + gr->gj - 1) / gr->gj;
     std::vector<int32_t> order = spatial_order(g);
@@ -409,8 +446,9 @@ cq_status get_tiles(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
         cudaMemcpyAsync(ks.data(), st_->kstart.ptr, 8 * ks.size(), cudaMemcpyDeviceToHost, s);
         if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "k lists")) != CQ_OK) return st;
         double chunks = 0.0;
-        for (int q = 0; q < st_->n_tiles; ++q) chunks += (double)((ks[q + 1] - ks[q] + 3) / 4);
-        st_->mma_flops = chunks * 6.0 * (KCH / 16) * 2.0 * MT * NT * 16;
+        for (int q = 0; q < st_->n_tiles; ++q)
+            chunks += (double)((ks[q + 1] - ks[q] + gr->ca - 1) / gr->ca);
+        st_->mma_flops = chunks * 6.0 * KSTEPS * 2.0 * MT * NT * 16;
     }
     if (!tiles.empty()) {
         k_tile_klist<true><<<st_->n_tiles, 256, shm, s>>>(
@@ -454,17 +492,33 @@ cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_
     cq_status st = get_groups(ctx, pC, &gr);
     if (st != CQ_OK) return st;
     if ((st = get_tiles(ctx, pA, pB, pC, gr, &tiles)) != CQ_OK) return st;
-    // operands in padded split form
-    const int64_t na = pA->n_blocks * nb * KP, nbv = pB->n_blocks * nb * KP;
+    // operands in split form: per plane a main array (8 values per block row, nb = 9) and a
+    // tail array (4 values per block row)
+    const int mainw = nb == 9 ? KLayout<9>::MAINW : KLayout<4>::MAINW;
+    const int ka = mainw + TAILW;
+    const int64_t ra = pA->n_blocks * nb, rb = pB->n_blocks * nb;  // block rows
     void *va, *vb;
-    if ((st = cq_scratch(ctx, "split_A", 3 * 2 * (size_t)na, &va)) != CQ_OK) return st;
-    if ((st = cq_scratch(ctx, "split_B", 3 * 2 * (size_t)nbv, &vb)) != CQ_OK) return st;
-    __nv_bfloat16 *sa = (__nv_bfloat16 *)va, *sb = (__nv_bfloat16 *)vb;
-    k_split_a<<<(unsigned)((na + 255) / 256), 256, 0, s>>>(na, nb, pA->uniform, A, sa, sa + na,
-                                                           sa + 2 * na);
-    k_split_b<<<(unsigned)((nbv + 255) / 256), 256, 0, s>>>(nbv, nb, pB->uniform, B, sb,
-                                                            sb + nbv, sb + 2 * nbv);
-    cq_count_launch(2);
+    if ((st = cq_scratch(ctx, "split_A", 3 * 2 * (size_t)(ra * ka), &va)) != CQ_OK) return st;
+    if ((st = cq_scratch(ctx, "split_B", 3 * 2 * (size_t)(rb * ka), &vb)) != CQ_OK) return st;
+    SplitPlanes pa, pb;
+    {
+        __nv_bfloat16 *x = (__nv_bfloat16 *)va, *y = (__nv_bfloat16 *)vb;
+        for (int q = 0; q < 3; ++q) {
+            pa.main[q] = x + q * ra * mainw;
+            pb.main[q] = y + q * rb * mainw;
+        }
+        for (int q = 0; q < 3; ++q) {
+            pa.tail[q] = x + 3 * ra * mainw + q * ra * TAILW;
+            pb.tail[q] = y + 3 * rb * mainw + q * rb * TAILW;
+        }
+    }
+    if (ra > 0)
+        k_split_a<<<(unsigned)((ra * ka + 255) / 256), 256, 0, s>>>(ra * ka, nb, mainw,
+                                                                   pA->uniform, A, pa);
+    if (rb > 0)
+        k_split_b<<<(unsigned)((rb * ka + 255) / 256), 256, 0, s>>>(rb * ka, nb, mainw,
+                                                                   pB->uniform, B, pb);
+    cq_count_launch((ra > 0) + (rb > 0));
     SplitArgs a;
     a.n_tiles = tiles->n_tiles;
     a.tiles = tiles->tiles.as<int2>();
@@ -481,8 +535,10 @@ cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_
     a.c_col = pC->col.as<int32_t>();
     a.b_tr = pB->transpose.as<int64_t>();
     for (int q = 0; q < 3; ++q) {
-        a.sa[q] = sa + q * na;
-        a.sb[q] = sb + q * nbv;
+        a.sa_main[q] = pa.main[q];
+        a.sa_tail[q] = pa.tail[q];
+        a.sb_main[q] = pb.main[q];
+        a.sb_tail[q] = pb.tail[q];
     }
     a.C = C;
     a.c_stride = pC->uniform;

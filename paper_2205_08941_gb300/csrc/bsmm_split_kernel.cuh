@@ -1,54 +1,161 @@
 // The tile kernel of the split-BF16 product (included by bsmm_split.cu).
 //
-// Roles: threads 0..127 gather the 128 A rows of a chunk, threads 128..191 the 64 B rows
-// (16-byte cp.async pieces, block indices from the tile's index table, zeros for absent
-// blocks); thread 0 issues the 24 MMAs of a chunk (4 K steps x 6 split products) and
-// commits them to the chunk's stage barrier; all 8 warps drain the accumulator (warps w and
-// w+4 read TMEM lane quarter w, columns 0..31 and 32..63).
+// Warp roles (12 warps, one CTA per SM):
+//   warps 0-7   drain: every DRAIN chunks they read the FP32 accumulator (warp w: TMEM lane
+//               quarter w % 4, columns 32 * (w / 4) ..) into double-float (hi, lo) sums in
+//               registers, release the accumulator, and write C after a tile's last period;
+//   warps 8-10  producers: thread q < 64 copies A rows q and q + 64, thread q >= 64 copies
+//               B rows q - 64 and q - 32: per chunk the rows' pieces of the chunk's atoms,
+//               three BF16 planes each, with cp.async (zero fill for absent blocks), then
+//               marks the stage full;
+//   warp 11     lane 0 issues the 18 MMAs of a chunk (3 K steps x 6 split products) into
+//               one of two TMEM accumulators and commits them to the stage's "empty"
+//               barrier, and at the end of a drain period to the accumulator's "full" barrier.
+// Stages rotate over one running chunk counter across all tiles of the CTA; accumulators
+// over one running period counter; every wait computes its parity from those counters.
+// Producers signal a chunk LAG chunks after issuing it: they wait for their own copies
+// (cp.async.wait_group), make them visible to the tensor core (fence.proxy.async) and
+// arrive, so LAG + 1 chunks of copies per thread are in flight.
 //
-// Pipeline: NS shared stages.  Chunk c lives in stage c % NS.  Gathers run NS-1 chunks
-// ahead of the tensor core (cp.async groups, one per chunk); a stage is refilled only
-// after the barrier of the MMAs that last read it has completed.
-constexpr int NS = 3;
+// Every wait is bounded (about two seconds) and also ends when another role has given up:
+// the CTA then stops issuing work, retires its own copies and MMAs (bounded), frees its
+// tensor memory and returns with bit 16 of the context flag set.
+constexpr int NS = 4;    // shared-memory stages
+constexpr int LAG = 2;   // chunks a producer keeps in flight before signalling
+constexpr int N_PROD = (MT + NT) / 2;  // producer threads (two tile rows each)
+constexpr int N_DRAIN = 256;           // drain threads
+constexpr int W_PROD = 8, W_MMA = 11;  // first producer warp, MMA warp
 
-// block indices of this thread's row for the four atoms of chunk c (-1: absent)
+struct Bars {
+    uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], done;
+    uint32_t tmem_slot;
+    int abort_flag;
+};
+static_assert(sizeof(Bars) <= BAR_BYTES, "barrier block");
+static_assert(NS * STAGE + BAR_BYTES <= 227 * 1024, "shared memory per CTA");
+
+__device__ __forceinline__ bool bar_try(uint32_t addr, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait on an mbarrier phase; gives up when another role has set the abort flag.
+__device__ __forceinline__ bool bar_wait(uint32_t addr, uint32_t parity, volatile int *abort_flag)
+{
+    const long long t0 = clock64();
+    while (!bar_try(addr, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Bounded wait that ignores the abort flag (retiring work already issued).
+__device__ __forceinline__ bool bar_wait_plain(uint32_t addr, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!bar_try(addr, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t addr)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+__device__ __forceinline__ void bar_commit(uint32_t addr)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(addr)
+        : "memory");
+}
+
+// block indices of this thread's row for the atoms of chunk c (-1: absent)
 template <int NB>
 __device__ __forceinline__ void load_index(const SplitArgs &p, int64_t kb, int64_t kn, int c,
-                                           int slot, int32_t blk[4])
+                                           int slot, int32_t (&blk)[KLayout<NB>::CA])
 {
-    constexpr int GI = MT / NB, GJ = NT / NB, W = GI + GJ;
+    constexpr int CA = KLayout<NB>::CA, W = MT / NB + NT / NB;
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        const int64_t kidx = (int64_t)c * 4 + kk;
-        blk[kk] = (slot >= 0 && kidx < kn) ? p.table[(kb + kidx) * W + slot] : -1;
+    for (int a = 0; a < CA; ++a) {
+        const int64_t kidx = (int64_t)c * CA + a;
+        blk[a] = (slot >= 0 && kidx < kn) ? __ldg(&p.table[(kb + kidx) * W + slot]) : -1;
     }
 }
 
+// copy this thread's row of one chunk (all atoms, three planes) into a stage
 template <int NB>
-__device__ __forceinline__ void gather_chunk(const SplitArgs &p, uint8_t *stg, uint32_t sbase,
-                                             const int32_t blk[4], bool a_role, bool b_role,
-                                             int grow, int o)
+__device__ __forceinline__ void gather_chunk(const SplitArgs &p, uint32_t stage, bool a_side,
+                                             int row, int o,
+                                             const int32_t (&blk)[KLayout<NB>::CA])
 {
-    if (!(a_role || b_role)) return;
-    const uint32_t dbase = a_role ? sbase : sbase + 3 * A_PLANE;
-    uint8_t *gbase = a_role ? stg : stg + 3 * A_PLANE;
-    const int plane = a_role ? A_PLANE : B_PLANE;
+    constexpr int CA = KLayout<NB>::CA, MW = KLayout<NB>::MAINW;
+    const uint32_t base = a_side ? stage : stage + 3 * A_PLANE;
+    const int plane = a_side ? A_PLANE : B_PLANE;
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
+    for (int a = 0; a < CA; ++a) {
+        const bool have = blk[a] >= 0;
+        const int64_t r = have ? (int64_t)blk[a] * NB + o : 0;
 #pragma unroll
         for (int pl = 0; pl < 3; ++pl) {
-            const uint32_t d = dbase + pl * plane;
-            if (blk[kk] >= 0) {
-                const __nv_bfloat16 *src =
-                    (a_role ? p.sa[pl] : p.sb[pl]) + ((int64_t)blk[kk] * NB + o) * KP;
-                cp16(d + cm_off(grow, 2 * kk), src);
-                cp16(d + cm_off(grow, 2 * kk + 1), src + 8);
-            } else {
-                uint8_t *g = gbase + pl * plane;
-                *reinterpret_cast<uint4 *>(g + cm_off(grow, 2 * kk)) = make_uint4(0u, 0u, 0u, 0u);
-                *reinterpret_cast<uint4 *>(g + cm_off(grow, 2 * kk + 1)) =
-                    make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t d = base + pl * plane;
+            if (MW) {
+                const __nv_bfloat16 *m = (a_side ? p.sa_main[pl] : p.sb_main[pl]) + r * MW;
+                cp16z(d + tile_off(row, KLayout<NB>::main_col(a), 0), m, have ? 16u : 0u);
             }
+            const __nv_bfloat16 *tl = (a_side ? p.sa_tail[pl] : p.sb_tail[pl]) + r * TAILW;
+            cp8z(d + tile_off(row, KLayout<NB>::tail_col(a), (a & 1) * 8), tl, have ? 8u : 0u);
+        }
+    }
+}
+
+// Epilogue of one drain thread: accumulator row arow = (atom ia of group g, orbital a),
+// columns 32*HALF .. +31 = (atom of group h, orbital); each block (ia, j) that P_C holds is
+// found by one binary search over row ia of P_C and written as beta*C + alpha*(hi + lo).
+template <int NB, int HALF>
+__device__ __forceinline__ void write_rows(const SplitArgs &p, int2 tg, int arow,
+                                           const float (&hi)[32], const float (&lo)[32])
+{
+    constexpr int GI = MT / NB, GJ = NT / NB;
+    constexpr int J0 = (HALF * 32) / NB, J1 = (HALF * 32 + 31) / NB;
+    if (arow >= GI * NB) return;
+    const int ia = p.g_atoms[(int64_t)tg.x * GI + arow / NB];
+    if (ia < 0) return;
+    const int a = arow % NB;
+    const int64_t r0 = p.c_rp[ia], r1 = p.c_rp[ia + 1];
+#pragma unroll
+    for (int jl = J0; jl <= J1; ++jl) {
+        if (jl >= GJ) continue;
+        const int j = p.h_atoms[(int64_t)tg.y * GJ + jl];
+        if (j < 0) continue;
+        int64_t lo_i = r0, hi_i = r1;
+        while (lo_i < hi_i) {
+            const int64_t mid = (lo_i + hi_i) >> 1;
+            if (p.c_col[mid] < j)
+                lo_i = mid + 1;
+            else
+                hi_i = mid;
+        }
+        if (lo_i >= r1 || p.c_col[lo_i] != j) continue;
+        double *dst = p.C + lo_i * p.c_stride + a * NB;
+#pragma unroll
+        for (int bo = 0; bo < NB; ++bo) {
+            const int x = jl * NB + bo - HALF * 32;
+            if (x < 0 || x >= 32) continue;
+            const double v = (double)hi[x] + (double)lo[x];
+            dst[bo] = p.beta == 0.0 ? p.alpha * v : p.beta * dst[bo] + p.alpha * v;
         }
     }
 }
@@ -56,26 +163,37 @@ __device__ __forceinline__ void gather_chunk(const SplitArgs &p, uint8_t *stg, u
 template <int NB>
 __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
 {
-    constexpr int GI = MT / NB, GJ = NT / NB;
+    constexpr int GI = MT / NB, GJ = NT / NB, CA = KLayout<NB>::CA;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + NS * STAGE);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + NS * STAGE + 8 * NS);
+    Bars *bars = reinterpret_cast<Bars *>(smem + NS * STAGE);
+    volatile int *abort_flag = &bars->abort_flag;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const bool a_role = t < MT, b_role = t >= MT && t < MT + NT;
-    const int grow = a_role ? t : t - MT;
-    const int arow = (warp & 3) * 32 + lane, half = warp >> 2;
+    const uint32_t sm0 = smem_u32(smem);
 
     for (int e = t; e < NS * STAGE / 16; e += ST)
         reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
     if (t == 0) {
-        for (int s = 0; s < NS; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[s])),
+        for (int s = 0; s < NS; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->full[s])),
+                         "r"(N_PROD));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->empty[s])),
                          "r"(1));
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
+                             smem_u32(&bars->acc_full[b])),
+                         "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
+                             smem_u32(&bars->acc_empty[b])),
+                         "r"(N_DRAIN));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->done)), "r"(1));
+        bars->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == W_MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
+                         smem_u32(&bars->tmem_slot)),
                      "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
@@ -83,100 +201,133 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * 32);
-    const uint32_t sm0 = smem_u32(smem);
+    const uint32_t tmem = bars->tmem_slot;
 
-    uint32_t phase[NS];
-    bool pending[NS];
+    if (warp >= W_PROD && warp < W_MMA) {
+        // ------------------------------------------------------------ producers
+        const int q = t - W_PROD * 32;
+        const bool a_side = q < MT / 2;
+        int row[2], slot[2], o[2];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        phase[s] = 0u;
-        pending[s] = false;
-    }
-    bool failed = false;
-
-    // wait (CTA-uniformly, bounded) until the MMAs that last read stage s are complete
-    auto free_stage = [&](int s) -> bool {
-        if (!pending[s]) return true;
-        const bool ok = mbar_wait(smem_u32(&mbar[s]), phase[s]);
-        if (__syncthreads_or(!ok)) return false;
-        phase[s] ^= 1u;
-        pending[s] = false;
-        return true;
-    };
-
-    for (int tile = blockIdx.x; tile < p.n_tiles && !failed; tile += gridDim.x) {
-        const int2 tg = p.tiles[tile];
-        const int64_t kb = p.kstart[tile], kn = p.kstart[tile + 1] - kb;
-        int slot = -1;
-        if (a_role && grow < GI * NB) slot = grow / NB;
-        if (b_role && grow < GJ * NB) slot = GI + grow / NB;
-        const int o = grow % NB;
-        float hi[32], lo[32];
-#pragma unroll
-        for (int x = 0; x < 32; ++x) hi[x] = lo[x] = 0.f;
-        const int nch = (int)((kn + 3) / 4);
-        // prologue: the first NS-1 chunks; nxt holds the indices of the next chunk to gather,
-        // loaded one iteration ahead so the gather waits for one memory round trip only
-        int32_t nxt[4];
-        for (int c = 0; c < NS - 1 && c < nch; ++c) {
-            if (!free_stage(c % NS)) {
-                failed = true;
-                break;
-            }
-            load_index<NB>(p, kb, kn, c, slot, nxt);
-            gather_chunk<NB>(p, smem + (c % NS) * STAGE, sm0 + (c % NS) * STAGE, nxt, a_role,
-                             b_role, grow, o);
-            asm volatile("cp.async.commit_group;" ::: "memory");
+        for (int rr = 0; rr < 2; ++rr) {
+            row[rr] = a_side ? q + rr * (MT / 2) : q - MT / 2 + rr * (NT / 2);
+            slot[rr] = -1;
+            if (a_side && row[rr] < GI * NB) slot[rr] = row[rr] / NB;
+            if (!a_side && row[rr] < GJ * NB) slot[rr] = GI + row[rr] / NB;
+            o[rr] = row[rr] % NB;
         }
-        load_index<NB>(p, kb, kn, NS - 1, slot, nxt);
-        for (int c = 0; c < nch && !failed; ++c) {
-            const int s = c % NS;
-            if (c + 1 < nch)
-                asm volatile("cp.async.wait_group 1;" ::: "memory");
-            else
-                asm volatile("cp.async.wait_group 0;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (t == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ab = sm0 + s * STAGE, bbase = ab + 3 * A_PLANE;
-                const int pq[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
+        uint32_t cg = 0;  // running chunk counter
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+            const int64_t kb = p.kstart[tile], kn = p.kstart[tile + 1] - kb;
+            const int nch = (int)((kn + CA - 1) / CA);
+            int32_t nxt[2][CA];
+            if (nch > 0)
 #pragma unroll
-                for (int ks = 0; ks < KCH / 16; ++ks)
-#pragma unroll
-                    for (int x = 0; x < 6; ++x) {
-                        const uint64_t ad = smem_desc(ab + pq[x][0] * A_PLANE + ks * 256);
-                        const uint64_t bd = smem_desc(bbase + pq[x][1] * B_PLANE + ks * 256);
-                        const uint32_t acc = (c % DRAIN == 0 && ks == 0 && x == 0) ? 0u : 1u;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
-                                tmem),
-                            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
-                    }
-                asm volatile(
-                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        smem_u32(&mbar[s]))
-                    : "memory");
-            }
-            pending[s] = true;
-            // refill: chunk c + NS - 1 goes to the stage chunk c - 1 used
-            const int cn = c + NS - 1;
-            if (cn < nch) {
-                if (!free_stage(cn % NS)) {
-                    failed = true;
+                for (int rr = 0; rr < 2; ++rr) load_index<NB>(p, kb, kn, 0, slot[rr], nxt[rr]);
+            for (int c = 0; c < nch; ++c, ++cg) {
+                const int s = (int)(cg % NS);
+                if (cg >= (uint32_t)NS &&
+                    !bar_wait(smem_u32(&bars->empty[s]), ((cg / NS) + 1) & 1u, abort_flag)) {
+                    ok = false;
                     break;
                 }
-                gather_chunk<NB>(p, smem + (cn % NS) * STAGE, sm0 + (cn % NS) * STAGE, nxt,
-                                 a_role, b_role, grow, o);
+                int32_t cur[2][CA];
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                    for (int a = 0; a < CA; ++a) cur[rr][a] = nxt[rr][a];
+                if (c + 1 < nch)
+#pragma unroll
+                    for (int rr = 0; rr < 2; ++rr)
+                        load_index<NB>(p, kb, kn, c + 1, slot[rr], nxt[rr]);
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr)
+                    gather_chunk<NB>(p, sm0 + s * STAGE, a_side, row[rr], o[rr], cur[rr]);
                 asm volatile("cp.async.commit_group;" ::: "memory");
-                load_index<NB>(p, kb, kn, cn + 1, slot, nxt);
+                if (cg >= (uint32_t)LAG) {
+                    asm volatile("cp.async.wait_group %0;" ::"n"(LAG) : "memory");
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bar_arrive(smem_u32(&bars->full[(cg - LAG) % NS]));
+                }
             }
-            if (c % DRAIN == DRAIN - 1 || c == nch - 1) {
-                if (!free_stage(s)) {
-                    failed = true;
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (ok) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (uint32_t q = cg > (uint32_t)LAG ? cg - LAG : 0u; q < cg; ++q)
+                bar_arrive(smem_u32(&bars->full[q % NS]));
+        }
+    } else if (warp == W_MMA) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            uint32_t cg = 0, pg = 0;
+            bool ok = true, issued = false;
+            const int pq[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
+            for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+                const int64_t kn = p.kstart[tile + 1] - p.kstart[tile];
+                const int nch = (int)((kn + CA - 1) / CA);
+                for (int c = 0; c < nch; ++c, ++cg) {
+                    const uint32_t b = pg & 1u;
+                    if (c % DRAIN == 0 && pg >= 2 &&
+                        !bar_wait(smem_u32(&bars->acc_empty[b]), ((pg / 2) + 1) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const int s = (int)(cg % NS);
+                    if (!bar_wait(smem_u32(&bars->full[s]), (cg / NS) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t ab = sm0 + s * STAGE, bb = ab + 3 * A_PLANE;
+                    const uint32_t acc_addr = tmem + b * NT;
+#pragma unroll
+                    for (int ks = 0; ks < KSTEPS; ++ks)
+#pragma unroll
+                        for (int x = 0; x < 6; ++x) {
+                            const uint64_t ad = smem_desc(ab + pq[x][0] * A_PLANE + ks * 256);
+                            const uint64_t bd = smem_desc(bb + pq[x][1] * B_PLANE + ks * 256);
+                            const uint32_t acc = (c % DRAIN == 0 && ks == 0 && x == 0) ? 0u : 1u;
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+                                    acc_addr),
+                                "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+                        }
+                    bar_commit(smem_u32(&bars->empty[s]));
+                    issued = true;
+                    if (c % DRAIN == DRAIN - 1 || c == nch - 1) {
+                        bar_commit(smem_u32(&bars->acc_full[b]));
+                        ++pg;
+                    }
+                }
+            }
+            if (issued) {  // retire every MMA before the tensor memory is released
+                bar_commit(smem_u32(&bars->done));
+                if (!bar_wait_plain(smem_u32(&bars->done), 0u)) *abort_flag = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ drain and epilogue
+        const int quarter = warp & 3, half = warp >> 2;
+        const int arow = quarter * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+        uint32_t pg = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+            const int2 tg = p.tiles[tile];
+            const int64_t kn = p.kstart[tile + 1] - p.kstart[tile];
+            const int nch = (int)((kn + CA - 1) / CA);
+            const int np = (nch + DRAIN - 1) / DRAIN;
+            float hi[32], lo[32];
+#pragma unroll
+            for (int x = 0; x < 32; ++x) hi[x] = lo[x] = 0.f;
+            for (int d = 0; d < np; ++d, ++pg) {
+                const uint32_t b = pg & 1u;
+                if (!bar_wait(smem_u32(&bars->acc_full[b]), (pg / 2) & 1u, abort_flag)) {
+                    ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -189,60 +340,28 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
                           "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]),
                           "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                        : "r"(taddr + q * 16));
+                        : "r"(lane_addr + b * NT + q * 16));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int x = 0; x < 16; ++x)
                         two_sum_add(hi[q * 16 + x], lo[q * 16 + x], __uint_as_float(v[x]));
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncthreads();
+                bar_arrive(smem_u32(&bars->acc_empty[b]));
             }
-        }
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        if (failed) break;
-        // epilogue: accumulator row arow = (atom ia, orbital a), columns 32*half .. +31 =
-        // (atom of group h, orbital) of every block P_C holds
-        const int ia = arow < GI * NB ? p.g_atoms[(int64_t)tg.x * GI + arow / NB] : -1;
-        if (ia >= 0) {
-            const int a = arow % NB;
-            int cached_jl = -1;
-            double *dst = nullptr;
-#pragma unroll
-            for (int x = 0; x < 32; ++x) {
-                const int col = half * 32 + x;
-                const int jl = col / NB, bo = col % NB;
-                if (jl >= GJ) continue;
-                if (jl != cached_jl) {
-                    cached_jl = jl;
-                    dst = nullptr;
-                    const int j = p.h_atoms[(int64_t)tg.y * GJ + jl];
-                    if (j >= 0) {
-                        int64_t lo_i = p.c_rp[ia], hi_i = p.c_rp[ia + 1];
-                        while (lo_i < hi_i) {
-                            const int64_t mid = (lo_i + hi_i) >> 1;
-                            if (p.c_col[mid] < j)
-                                lo_i = mid + 1;
-                            else
-                                hi_i = mid;
-                        }
-                        if (lo_i < p.c_rp[ia + 1] && p.c_col[lo_i] == j)
-                            dst = p.C + lo_i * p.c_stride + a * NB;
-                    }
-                }
-                if (!dst) continue;
-                const double v = (double)hi[x] + (double)lo[x];
-                dst[bo] = p.beta == 0.0 ? p.alpha * v : p.beta * dst[bo] + p.alpha * v;
-            }
+            if (!ok) break;
+            if (half == 0)
+                write_rows<NB, 0>(p, tg, arow, hi, lo);
+            else
+                write_rows<NB, 1>(p, tg, arow, hi, lo);
         }
     }
-    if (failed && t == 0) atomicOr(p.flag, 16);
-    // retire outstanding commits before releasing tensor memory
-    for (int s = 0; s < NS; ++s)
-        if (pending[s]) mbar_wait(smem_u32(&mbar[s]), phase[s]);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (t == 0 && *abort_flag) atomicOr(p.flag, 16);
+    if (warp == W_MMA) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TMEM_COLS));
+    }
 }
