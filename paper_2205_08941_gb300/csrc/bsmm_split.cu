@@ -8,28 +8,29 @@
 // rounding only acts within a drain period; the result is written back in FP64.
 //
 // Local densification.  9x9 blocks do not fit MMA shapes, so atoms are grouped in space
-// (Morton order): an M tile is a group of floor(128/nb) atoms (126 rows for nb = 9), an N
-// tile a group of floor(64/nb) atoms.  A work tile is a pair (M group g, N group h) that
-// holds at least one block of P_C; its K list is every atom k with (i, k) in P_A for some
-// i in g and (k, j) in P_B for some j in h (built on the device with shared-memory
-// bitmaps).  Absent blocks are zero in shared memory.  Every C block belongs to exactly one
-// tile, so there are no atomics.
+// (Morton order): an M group holds floor(128/nb) atoms (126 rows for nb = 9), an N group
+// floor(64/nb) atoms, a K group CA atoms (4 for nb = 9, 12 for nb = 4).  A work tile is a
+// pair (M group g, N group h) that holds at least one block of P_C; its chunks are the K
+// groups that contain an atom k with (i, k) in P_A for some i in g and (k, j) in P_B for
+// some j in h.  Absent blocks are zero.  Every C block belongs to exactly one tile, so
+// there are no atomics.
 //
 // K layout.  Along K an atom's orbitals are split into a "main" piece of 8 values (one
 // 16-byte core-matrix row) and a "tail" of 4 values (half a core-matrix row; for nb = 9:
-// orbital 8 and three zeros, for nb = 4: all four orbitals).  A K chunk of 48 values (six
+// orbital 8 and three zeros, for nb = 4: all four orbitals).  A chunk of 48 K values (six
 // core-matrix columns, three MMA K steps) holds 4 atoms of 9 orbitals (mains in columns
 // 0-3, tails paired in columns 4-5) or 12 atoms of 4 orbitals (tails only), so 9-orbital
 // atoms cost 12 K values instead of 16.
 //
-// Operands are pre-split once per product into BF16 planes ("A form": rows = left orbital,
-// K = right orbital; "B form": rows = right orbital, K = left orbital), each as a main
-// array (8 values per block row) and a tail array (4 values per block row), so the tile
-// kernel only moves aligned 16- and 8-byte pieces with cp.async into the canonical
-// no-swizzle K-major layout (core matrix = 8 rows x 16 bytes; LBO = 128 B between
-// K-adjacent core matrices, SBO = 768 B between 8-row groups) and one thread issues the
-// MMAs.  Producer warps, the MMA thread and the drain warps hand stages and the two TMEM
-// accumulators to one another through mbarriers (bsmm_split_kernel.cuh).
+// Panels.  Before each product the operands are split and packed into panels that are
+// byte-for-byte the shared-memory image of one chunk in the canonical no-swizzle K-major
+// layout (core matrix = 8 rows x 16 bytes; LBO = 128 B between K-adjacent core matrices,
+// SBO = 768 B between 8-row groups): an A panel per (M group, K group) pair that has a
+// block of P_A (3 planes x 128 rows x 48 K, 36 KB), a B panel per (N group, K group) pair
+// that has a block of P_B (3 planes x 64 rows, 18 KB).  The tile kernel then moves each
+// chunk with two TMA bulk copies; one thread issues the MMAs, eight warps drain the
+// accumulators (bsmm_split_kernel.cuh).  A panels are packed in batches of M groups so
+// that their scratch stays below A_PANEL_CAP bytes.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -40,30 +41,33 @@
 
 namespace {
 
-constexpr int ST = 384;                      // threads per CTA (12 warps)
+constexpr int ST = 320;                      // threads per CTA (10 warps)
 constexpr int MT = 128, NT = 64, KCH = 48;   // tile M, N and K chunk
 constexpr int KSTEPS = KCH / 16;             // MMA K steps per chunk
 constexpr int TAILW = 4;                     // values in an atom's tail piece
 constexpr int SBO = (KCH / 8) * 128;         // bytes between 8-row groups
 constexpr int A_PLANE = MT * KCH * 2;        // 12 KB
 constexpr int B_PLANE = NT * KCH * 2;        // 6 KB
-constexpr int STAGE = 3 * A_PLANE + 3 * B_PLANE;
+constexpr int A_CHUNK = 3 * A_PLANE;         // one packed A panel
+constexpr int B_CHUNK = 3 * B_PLANE;         // one packed B panel
+constexpr int STAGE = A_CHUNK + B_CHUNK;
 constexpr int BAR_BYTES = 256;
 constexpr int DRAIN = 4;                     // chunks per FP32 accumulation period
 constexpr int TMEM_COLS = 2 * NT;            // two FP32 accumulators
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr size_t A_PANEL_CAP = (size_t)12 << 30;  // scratch bound for one batch of A panels
 
 // Atoms per chunk and core-matrix columns of an atom's pieces.
 template <int NB> struct KLayout;
 template <> struct KLayout<9> {
     static constexpr int CA = 4, MAINW = 8;
-    __device__ static constexpr int main_col(int a) { return a; }
-    __device__ static constexpr int tail_col(int a) { return 4 + (a >> 1); }
+    __host__ __device__ static constexpr int main_col(int a) { return a; }
+    __host__ __device__ static constexpr int tail_col(int a) { return 4 + (a >> 1); }
 };
 template <> struct KLayout<4> {
     static constexpr int CA = 12, MAINW = 0;
-    __device__ static constexpr int main_col(int) { return 0; }
-    __device__ static constexpr int tail_col(int a) { return a >> 1; }
+    __host__ __device__ static constexpr int main_col(int) { return 0; }
+    __host__ __device__ static constexpr int tail_col(int a) { return a >> 1; }
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -72,7 +76,7 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
 }
 
 // byte offset of (row, core-matrix column, byte) in the canonical no-swizzle K-major layout
-__device__ __forceinline__ uint32_t tile_off(int row, int col, int byte)
+__host__ __device__ __forceinline__ uint32_t tile_off(int row, int col, int byte)
 {
     return (uint32_t)((row >> 3) * SBO + col * 128 + (row & 7) * 16 + byte);
 }
@@ -100,56 +104,21 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16 &b0, __nv_bfloat1
     b2 = __double2bfloat16(r);
 }
 
-struct SplitPlanes {
-    __nv_bfloat16 *main[3], *tail[3];
-};
-
-// Position of K value m of a block row in the main/tail arrays of a plane.
-__device__ __forceinline__ int64_t piece_index(int64_t row, int m, int mainw, int64_t n_rows,
-                                               bool &in_tail)
+// index of block (row, col) in a pattern, or -1
+__device__ __forceinline__ int64_t find_block(const int64_t *rp, const int32_t *cl, int row, int col)
 {
-    in_tail = m >= mainw;
-    return in_tail ? row * TAILW + (m - mainw) : row * mainw + m;
+    int64_t lo = rp[row], hi = rp[row + 1];
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cl[mid] < col)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (lo < rp[row + 1] && cl[lo] == col) ? lo : -1;
 }
 
-// A form: block b = (i, k) -> row r < nb (orbital of i), K value m (orbital of k).
-// One thread per (block, row, m < mainw + 4); writes three planes of main and tail arrays.
-__global__ void k_split_a(int64_t n, int nb, int mainw, int stride, const double *__restrict__ A,
-                          SplitPlanes out)
-{
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const int ka = mainw + TAILW;
-    const int64_t row = e / ka;
-    const int m = (int)(e - row * ka);
-    const int64_t b = row / nb;
-    const int r = (int)(row - b * nb);
-    const double x = m < nb ? A[b * stride + r * nb + m] : 0.0;
-    bool in_tail;
-    const int64_t q = piece_index(row, m, mainw, 0, in_tail);
-    __nv_bfloat16 v[3];
-    split3(x, v[0], v[1], v[2]);
-    for (int pl = 0; pl < 3; ++pl) (in_tail ? out.tail[pl] : out.main[pl])[q] = v[pl];
-}
-
-// B form: block b = (k, j) -> row n < nb (orbital of j), K value m (orbital of k).
-__global__ void k_split_b(int64_t n, int nb, int mainw, int stride, const double *__restrict__ B,
-                          SplitPlanes out)
-{
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const int ka = mainw + TAILW;
-    const int64_t row = e / ka;
-    const int m = (int)(e - row * ka);
-    const int64_t b = row / nb;
-    const int r = (int)(row - b * nb);
-    const double x = m < nb ? B[b * stride + m * nb + r] : 0.0;
-    bool in_tail;
-    const int64_t q = piece_index(row, m, mainw, 0, in_tail);
-    __nv_bfloat16 v[3];
-    split3(x, v[0], v[1], v[2]);
-    for (int pl = 0; pl < 3; ++pl) (in_tail ? out.tail[pl] : out.main[pl])[q] = v[pl];
-}
+// ---------------------------------------------------------------- plan kernels
 
 // Tile existence: bit (g, h) for every C block (i, j).
 __global__ void k_tile_mark(int64_t n_c, const int32_t *c_row, const int32_t *c_col,
@@ -161,45 +130,17 @@ __global__ void k_tile_mark(int64_t n_c, const int32_t *c_row, const int32_t *c_
     atomicOr(&bits[key >> 5], 1u << (key & 31));
 }
 
-// K list of each tile: atoms k reachable from the M group through P_A and from the N group
-// through P_B (P_B symmetric: (k, j) in P_B <=> k in row j).  COUNT pass writes sizes,
-// the FILL pass writes ascending atom indices.
+// Scan of a shared-memory bitmap by a 256-thread CTA: COUNT writes the number of set bits,
+// FILL writes their indices in ascending order from out + out0.
 template <bool FILL>
-__global__ void __launch_bounds__(256)
-k_tile_klist(int n_atoms, const int2 *tiles, int gi, int gj, const int32_t *g_atoms,
-             const int32_t *h_atoms, const int64_t *a_rp, const int32_t *a_col,
-             const int64_t *b_rp, const int32_t *b_col, int64_t *count, const int64_t *start,
-             int32_t *klist)
+__device__ void bitmap_emit(const uint32_t *bits, int words, int64_t *count, int64_t out0,
+                            int32_t *out)
 {
-    extern __shared__ uint32_t bm[];  // 2 * words
-    const int words = (n_atoms + 31) >> 5;
-    uint32_t *ba = bm, *bb = bm + words;
-    for (int w = threadIdx.x; w < 2 * words; w += blockDim.x) bm[w] = 0u;
-    __syncthreads();
-    const int2 t = tiles[blockIdx.x];
-    for (int s = 0; s < gi; ++s) {
-        const int i = g_atoms[(int64_t)t.x * gi + s];
-        if (i < 0) continue;
-        for (int64_t e = a_rp[i] + threadIdx.x; e < a_rp[i + 1]; e += blockDim.x) {
-            const int k = a_col[e];
-            atomicOr(&ba[k >> 5], 1u << (k & 31));
-        }
-    }
-    for (int s = 0; s < gj; ++s) {
-        const int j = h_atoms[(int64_t)t.y * gj + s];
-        if (j < 0) continue;
-        for (int64_t e = b_rp[j] + threadIdx.x; e < b_rp[j + 1]; e += blockDim.x) {
-            const int k = b_col[e];
-            atomicOr(&bb[k >> 5], 1u << (k & 31));
-        }
-    }
-    __syncthreads();
-    // each thread owns a contiguous run of words
+    __shared__ int scan[256];
     const int per = (words + blockDim.x - 1) / blockDim.x;
     const int w0 = threadIdx.x * per, w1 = min(words, w0 + per);
     int mine = 0;
-    for (int w = w0; w < w1; ++w) mine += __popc(ba[w] & bb[w]);
-    __shared__ int scan[256];
+    for (int w = w0; w < w1; ++w) mine += __popc(bits[w]);
     scan[threadIdx.x] = mine;
     __syncthreads();
     for (int o = 1; o < 256; o <<= 1) {
@@ -209,69 +150,212 @@ k_tile_klist(int n_atoms, const int2 *tiles, int gi, int gj, const int32_t *g_at
         __syncthreads();
     }
     if (!FILL) {
-        if (threadIdx.x == blockDim.x - 1) count[blockIdx.x] = scan[threadIdx.x];
+        if (threadIdx.x == blockDim.x - 1) *count = scan[threadIdx.x];
         return;
     }
-    int64_t out = start[blockIdx.x] + scan[threadIdx.x] - mine;
+    int64_t o = out0 + scan[threadIdx.x] - mine;
     for (int w = w0; w < w1; ++w) {
+        uint32_t v = bits[w];
+        while (v) {
+            const int bit = __ffs(v) - 1;
+            v &= v - 1;
+            out[o++] = w * 32 + bit;
+        }
+    }
+}
+
+// K groups of each atom group (one CTA per group): every K group holding a column of a row
+// of the group's atoms in pattern (rp, col).
+template <bool FILL>
+__global__ void __launch_bounds__(256)
+k_group_kappa(int gsize, const int32_t *atoms, const int64_t *rp, const int32_t *col,
+              const int32_t *kg_of, int n_kappa, int64_t *count, const int64_t *start,
+              int32_t *out)
+{
+    extern __shared__ uint32_t bits[];
+    const int words = (n_kappa + 31) >> 5;
+    for (int w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
+    __syncthreads();
+    for (int s = 0; s < gsize; ++s) {
+        const int i = atoms[(int64_t)blockIdx.x * gsize + s];
+        if (i < 0) continue;
+        for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) {
+            const int kk = kg_of[col[e]];
+            atomicOr(&bits[kk >> 5], 1u << (kk & 31));
+        }
+    }
+    __syncthreads();
+    bitmap_emit<FILL>(bits, words, count + blockIdx.x, FILL ? start[blockIdx.x] : 0, out);
+}
+
+// K groups of each tile (one CTA per tile): the groups of the atoms k reachable from the M
+// group through P_A and from the N group through P_B (P_B symmetric: (k, j) in P_B <=> k in
+// row j).
+template <bool FILL>
+__global__ void __launch_bounds__(256)
+k_tile_kappa(int n_atoms, const int2 *tiles, int gi, int gj, const int32_t *g_atoms,
+             const int32_t *h_atoms, const int64_t *a_rp, const int32_t *a_col,
+             const int64_t *b_rp, const int32_t *b_col, const int32_t *kg_of, int n_kappa,
+             int64_t *count, const int64_t *start, int32_t *out)
+{
+    extern __shared__ uint32_t bm[];
+    const int words = (n_atoms + 31) >> 5, kwords = (n_kappa + 31) >> 5;
+    uint32_t *ba = bm, *bb = bm + words, *bk = bm + 2 * words;
+    for (int w = threadIdx.x; w < 2 * words + kwords; w += blockDim.x) bm[w] = 0u;
+    __syncthreads();
+    const int2 t = tiles[blockIdx.x];
+    for (int s = 0; s < gi; ++s) {
+        const int i = g_atoms[(int64_t)t.x * gi + s];
+        if (i < 0) continue;
+        for (int64_t e = a_rp[i] + threadIdx.x; e < a_rp[i + 1]; e += blockDim.x)
+            atomicOr(&ba[a_col[e] >> 5], 1u << (a_col[e] & 31));
+    }
+    for (int s = 0; s < gj; ++s) {
+        const int j = h_atoms[(int64_t)t.y * gj + s];
+        if (j < 0) continue;
+        for (int64_t e = b_rp[j] + threadIdx.x; e < b_rp[j + 1]; e += blockDim.x)
+            atomicOr(&bb[b_col[e] >> 5], 1u << (b_col[e] & 31));
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < words; w += blockDim.x) {
         uint32_t v = ba[w] & bb[w];
         while (v) {
             const int bit = __ffs(v) - 1;
             v &= v - 1;
-            klist[out++] = w * 32 + bit;
+            const int kk = kg_of[w * 32 + bit];
+            atomicOr(&bk[kk >> 5], 1u << (kk & 31));
         }
     }
+    __syncthreads();
+    bitmap_emit<FILL>(bk, kwords, count + blockIdx.x, FILL ? start[blockIdx.x] : 0, out);
 }
 
-// Block-index table of each tile: for every K-list entry k and every slot s of the tile's
-// groups, the index of block (i_s, k) in P_A (s < gi) or of block (k, j_s) in P_B, else -1.
-// Built once per pattern triple so the product kernel's gather has no dependent searches.
+// Chunk table: for every K group of every tile, the A panel (entry of the M group's list)
+// and the B panel (entry of the N group's list).
 __global__ void __launch_bounds__(256)
-k_tile_index(const int2 *tiles, int gi, int gj, const int32_t *g_atoms, const int32_t *h_atoms,
-             const int64_t *a_rp, const int32_t *a_col, const int64_t *b_rp,
-             const int32_t *b_col, const int64_t *b_tr, const int64_t *kstart,
-             const int32_t *klist, int32_t *table)
+k_tile_chunks(const int2 *tiles, const int64_t *kstart, const int32_t *tile_kappa,
+              const int64_t *ga_ptr, const int32_t *ga_kappa, const int64_t *hb_ptr,
+              const int32_t *hb_kappa, int2 *chunks)
 {
     const int2 t = tiles[blockIdx.x];
-    const int64_t kb = kstart[blockIdx.x], kn = kstart[blockIdx.x + 1] - kb;
-    const int w = gi + gj;
-    for (int s = 0; s < w; ++s) {
-        const bool left = s < gi;
-        const int atom = left ? g_atoms[(int64_t)t.x * gi + s] : h_atoms[(int64_t)t.y * gj + s - gi];
-        const int64_t *rp = left ? a_rp : b_rp;
-        const int32_t *cl = left ? a_col : b_col;
-        for (int64_t q = threadIdx.x; q < kn; q += blockDim.x) {
-            int32_t idx = -1;
-            if (atom >= 0) {
-                const int k = klist[kb + q];
-                int64_t lo = rp[atom], hi = rp[atom + 1];
-                while (lo < hi) {
-                    const int64_t mid = (lo + hi) >> 1;
-                    if (cl[mid] < k)
-                        lo = mid + 1;
-                    else
-                        hi = mid;
-                }
-                if (lo < rp[atom + 1] && cl[lo] == k) idx = (int32_t)(left ? lo : b_tr[lo]);
-            }
-            table[(kb + q) * w + s] = idx;
+    auto pos = [](const int32_t *lst, int64_t lo, int64_t hi, int key) {
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (lst[mid] < key)
+                lo = mid + 1;
+            else
+                hi = mid;
         }
+        return lo;
+    };
+    for (int64_t c = kstart[blockIdx.x] + threadIdx.x; c < kstart[blockIdx.x + 1]; c += blockDim.x) {
+        const int kk = tile_kappa[c];
+        chunks[c] = make_int2((int)pos(ga_kappa, ga_ptr[t.x], ga_ptr[t.x + 1], kk),
+                              (int)pos(hb_kappa, hb_ptr[t.y], hb_ptr[t.y + 1], kk));
     }
 }
 
-// cp.async of 16 or 8 bytes; src_bytes = 0 writes zeros and reads nothing
-__device__ __forceinline__ void cp16z(uint32_t dst, const void *src, uint32_t src_bytes)
+// C block of every (M slot, N slot) pair of each tile: index into P_C or -1, so that the
+// epilogue needs one independent load per block instead of a binary search.
+__global__ void __launch_bounds__(256)
+k_tile_cidx(const int2 *tiles, int gi, int gj, const int32_t *g_atoms, const int32_t *h_atoms,
+            const int64_t *c_rp, const int32_t *c_col, int32_t *cidx)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
-                 "r"(src_bytes)
-                 : "memory");
+    const int2 t = tiles[blockIdx.x];
+    for (int e = threadIdx.x; e < gi * gj; e += blockDim.x) {
+        const int si = e / gj, sj = e % gj;
+        const int i = g_atoms[(int64_t)t.x * gi + si], j = h_atoms[(int64_t)t.y * gj + sj];
+        cidx[(int64_t)blockIdx.x * gi * gj + e] =
+            (i >= 0 && j >= 0) ? (int32_t)find_block(c_rp, c_col, i, j) : -1;
+    }
 }
 
-__device__ __forceinline__ void cp8z(uint32_t dst, const void *src, uint32_t src_bytes)
+// ---------------------------------------------------------------- panel packing
+
+// Writes one row of one atom's K pieces (three planes) of a panel: x[m], m < MAINW + 4,
+// split into BF16 terms; the main piece is one 16-byte store, the tail one 8-byte store.
+template <int NB>
+__device__ __forceinline__ void put_piece(uint8_t *panel, int plane_bytes, int r, int a,
+                                          const double (&x)[KLayout<NB>::MAINW + TAILW])
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src),
-                 "r"(src_bytes)
-                 : "memory");
+    constexpr int MW = KLayout<NB>::MAINW;
+    __align__(16) __nv_bfloat16 v[3][MW + TAILW];
+#pragma unroll
+    for (int m = 0; m < MW + TAILW; ++m) split3(x[m], v[0][m], v[1][m], v[2][m]);
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) {
+        uint8_t *base = panel + pl * plane_bytes;
+        if (MW) {
+            uint4 w;
+            memcpy(&w, &v[pl][0], 16);
+            *reinterpret_cast<uint4 *>(base + tile_off(r, KLayout<NB>::main_col(a), 0)) = w;
+        }
+        uint2 w2;
+        memcpy(&w2, &v[pl][MW], 8);
+        *reinterpret_cast<uint2 *>(base + tile_off(r, KLayout<NB>::tail_col(a), (a & 1) * 8)) = w2;
+    }
+}
+
+// A panels of entries [e0, e0 + gridDim.x) (one CTA per entry = (M group g, K group kk)):
+// row r = (slot r / NB of g, orbital o = r % NB), K = (atom a of kk, orbital m): A_ik[o][m].
+template <int NB>
+__global__ void __launch_bounds__(256)
+k_pack_a(int64_t e0, const int32_t *ent_group, const int32_t *ent_kappa, const int32_t *g_atoms,
+         const int32_t *kg_atoms, const int64_t *rp, const int32_t *col,
+         const double *__restrict__ A, int stride, uint8_t *panels)
+{
+    constexpr int GI = MT / NB, CA = KLayout<NB>::CA, KA = KLayout<NB>::MAINW + TAILW;
+    __shared__ int64_t blk[GI * CA];
+    const int64_t e = e0 + blockIdx.x;
+    const int g = ent_group[e], kk = ent_kappa[e];
+    for (int q = threadIdx.x; q < GI * CA; q += blockDim.x) {
+        const int i = g_atoms[(int64_t)g * GI + q / CA], k = kg_atoms[(int64_t)kk * CA + q % CA];
+        blk[q] = (i >= 0 && k >= 0) ? find_block(rp, col, i, k) : -1;
+    }
+    __syncthreads();
+    uint8_t *panel = panels + (int64_t)blockIdx.x * A_CHUNK;
+    for (int q = threadIdx.x; q < MT * CA; q += blockDim.x) {
+        const int a = q / MT, r = q % MT;
+        const int64_t b = r < GI * NB ? blk[(r / NB) * CA + a] : -1;
+        const int o = r % NB;
+        double x[KA];
+#pragma unroll
+        for (int m = 0; m < KA; ++m)
+            x[m] = (b >= 0 && m < NB) ? A[b * stride + o * NB + m] : 0.0;
+        put_piece<NB>(panel, A_PLANE, r, a, x);
+    }
+}
+
+// B panels (one CTA per entry = (N group h, K group kk)): row r = (slot r / NB of h,
+// orbital o of j), K = (atom a of kk, orbital m): B_kj[m][o], found through block (j, k)
+// of row j and the transpose map.
+template <int NB>
+__global__ void __launch_bounds__(256)
+k_pack_b(const int32_t *ent_group, const int32_t *ent_kappa, const int32_t *h_atoms,
+         const int32_t *kg_atoms, const int64_t *rp, const int32_t *col, const int64_t *tr,
+         const double *__restrict__ B, int stride, uint8_t *panels)
+{
+    constexpr int GJ = NT / NB, CA = KLayout<NB>::CA, KA = KLayout<NB>::MAINW + TAILW;
+    __shared__ int64_t blk[GJ * CA];
+    const int64_t e = blockIdx.x;
+    const int h = ent_group[e], kk = ent_kappa[e];
+    for (int q = threadIdx.x; q < GJ * CA; q += blockDim.x) {
+        const int j = h_atoms[(int64_t)h * GJ + q / CA], k = kg_atoms[(int64_t)kk * CA + q % CA];
+        const int64_t jk = (j >= 0 && k >= 0) ? find_block(rp, col, j, k) : -1;
+        blk[q] = jk >= 0 ? tr[jk] : -1;
+    }
+    __syncthreads();
+    uint8_t *panel = panels + e * B_CHUNK;
+    for (int q = threadIdx.x; q < NT * CA; q += blockDim.x) {
+        const int a = q / NT, r = q % NT;
+        const int64_t b = r < GJ * NB ? blk[(r / NB) * CA + a] : -1;
+        const int o = r % NB;
+        double x[KA];
+#pragma unroll
+        for (int m = 0; m < KA; ++m)
+            x[m] = (b >= 0 && m < NB) ? B[b * stride + m * NB + o] : 0.0;
+        put_piece<NB>(panel, B_PLANE, r, a, x);
+    }
 }
 
 __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x)
@@ -284,16 +368,13 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x)
 }
 
 struct SplitArgs {
-    int n_tiles;
-    const int2 *tiles;
-    const int64_t *kstart;
-    const int32_t *klist;
-    const int32_t *table;
-    const int32_t *g_atoms, *h_atoms;
-    const int64_t *a_rp, *b_rp, *c_rp;
-    const int32_t *a_col, *b_col, *c_col;
-    const int64_t *b_tr;
-    const __nv_bfloat16 *sa_main[3], *sa_tail[3], *sb_main[3], *sb_tail[3];
+    int n_tiles;              // tiles of this launch
+    const int64_t *kstart;    // chunk range of each tile (n_tiles + 1, into chunks)
+    const int2 *chunks;       // (A panel entry, B panel entry) per chunk
+    const int32_t *cidx;      // C block of each (M slot, N slot) pair of each tile
+    const uint8_t *panel_a;   // A panels of entries [ea0, ...)
+    int64_t ea0;
+    const uint8_t *panel_b;   // all B panels
     double *C;
     int c_stride;
     double alpha, beta;
@@ -307,15 +388,24 @@ constexpr int SMEM = NS * STAGE + BAR_BYTES;  // pipeline stages + barriers
 // ---------------------------------------------------------------- host side
 
 struct Groups {
-    int gi = 0, gj = 0, n_g = 0, n_h = 0, ca = 0;  // atoms per M, N group; atoms per K chunk
-    DevBuf g_atoms, h_atoms, g_of, h_of;
+    int gi = 0, gj = 0, ca = 0;      // atoms per M, N and K group
+    int n_g = 0, n_h = 0, n_kappa = 0;
+    DevBuf g_atoms, h_atoms, kg_atoms, g_of, h_of, kg_of;
 };
 
-struct SplitTiles {
+struct Batch {
+    int tile0, tile1;   // tiles [tile0, tile1)
+    int64_t e0, e1;     // A panel entries [e0, e1)
+};
+
+struct SplitPlan {
     int n_tiles = 0;
-    int64_t n_k = 0;
+    int64_t n_chunks = 0, n_ga = 0, n_hb = 0;
     double mma_flops = 0.0;  // tensor-core flops of one product over these tiles
-    DevBuf tiles, kstart, klist, table;
+    std::vector<Batch> batches;
+    std::vector<int64_t> batch_chunks;
+    DevBuf tiles, kstart, tile_kappa, chunks, cidx;
+    DevBuf ga_ptr, ga_kappa, ga_group, hb_ptr, hb_kappa, hb_group;
 };
 
 // Morton order of the atoms (positions quantised to 1024 per box edge).
@@ -346,6 +436,16 @@ std::vector<int32_t> spatial_order(const Geometry &g)
     return order;
 }
 
+cq_status upload(cq_ctx *ctx, DevBuf &buf, const void *host, size_t bytes)
+{
+    cq_status st = cq_alloc(ctx, buf, bytes ? bytes : 4);
+    if (st != CQ_OK) return st;
+    if (bytes)
+        st = cq_check_cuda(ctx, cudaMemcpyAsync(buf.ptr, host, bytes, cudaMemcpyHostToDevice,
+                                                ctx->stream), "upload");
+    return st;
+}
+
 cq_status get_groups(cq_ctx *ctx, const cq_pattern *p, Groups **out)
 {
     auto key = std::make_tuple(1, p->geo->id, (uint64_t)0, (uint64_t)0);
@@ -362,47 +462,84 @@ cq_status get_groups(cq_ctx *ctx, const cq_pattern *p, Groups **out)
     gr->ca = nb == 9 ? KLayout<9>::CA : KLayout<4>::CA;
     gr->n_g = (g.n_atoms + gr->gi - 1) / gr->gi;
     gr->n_h = (g.n_atoms + gr->gj - 1) / gr->gj;
+    gr->n_kappa = (g.n_atoms + gr->ca - 1) / gr->ca;
     std::vector<int32_t> order = spatial_order(g);
-    std::vector<int32_t> ga((size_t)gr->n_g * gr->gi, -1), ha((size_t)gr->n_h * gr->gj, -1);
-    std::vector<int32_t> gof(g.n_atoms), hof(g.n_atoms);
+    std::vector<int32_t> ga((size_t)gr->n_g * gr->gi, -1), ha((size_t)gr->n_h * gr->gj, -1),
+        ka((size_t)gr->n_kappa * gr->ca, -1);
+    std::vector<int32_t> gof(g.n_atoms), hof(g.n_atoms), kof(g.n_atoms);
     for (int r = 0; r < g.n_atoms; ++r) {
-        ga[r] = order[r];
+        ga[r] = ha[r] = ka[r] = order[r];
         gof[order[r]] = r / gr->gi;
-        ha[r] = order[r];
         hof[order[r]] = r / gr->gj;
+        kof[order[r]] = r / gr->ca;
     }
     cq_status st;
-    if ((st = cq_alloc(ctx, gr->g_atoms, 4 * ga.size())) != CQ_OK ||
-        (st = cq_alloc(ctx, gr->h_atoms, 4 * ha.size())) != CQ_OK ||
-        (st = cq_alloc(ctx, gr->g_of, 4 * gof.size())) != CQ_OK ||
-        (st = cq_alloc(ctx, gr->h_of, 4 * hof.size())) != CQ_OK)
+    if ((st = upload(ctx, gr->g_atoms, ga.data(), 4 * ga.size())) != CQ_OK ||
+        (st = upload(ctx, gr->h_atoms, ha.data(), 4 * ha.size())) != CQ_OK ||
+        (st = upload(ctx, gr->kg_atoms, ka.data(), 4 * ka.size())) != CQ_OK ||
+        (st = upload(ctx, gr->g_of, gof.data(), 4 * gof.size())) != CQ_OK ||
+        (st = upload(ctx, gr->h_of, hof.data(), 4 * hof.size())) != CQ_OK ||
+        (st = upload(ctx, gr->kg_of, kof.data(), 4 * kof.size())) != CQ_OK)
         return st;
-    cudaMemcpyAsync(gr->g_atoms.ptr, ga.data(), 4 * ga.size(), cudaMemcpyHostToDevice, ctx->stream);
-    cudaMemcpyAsync(gr->h_atoms.ptr, ha.data(), 4 * ha.size(), cudaMemcpyHostToDevice, ctx->stream);
-    cudaMemcpyAsync(gr->g_of.ptr, gof.data(), 4 * gof.size(), cudaMemcpyHostToDevice, ctx->stream);
-    cudaMemcpyAsync(gr->h_of.ptr, hof.data(), 4 * hof.size(), cudaMemcpyHostToDevice, ctx->stream);
     if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "groups")) != CQ_OK) return st;
     *out = gr.get();
     ctx->aux[key] = gr;
     return CQ_OK;
 }
 
-cq_status get_tiles(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
-                    const cq_pattern *pC, const Groups *gr, SplitTiles **out)
+// K-group lists of n_groups atom groups in a pattern: ptr (n_groups + 1), kappa (ascending
+// per group), group (entry -> group); ptr_host receives ptr.
+cq_status group_lists(cq_ctx *ctx, const Groups *gr, int n_groups, int gsize,
+                      const int32_t *atoms, const cq_pattern *p, DevBuf &ptr, DevBuf &kappa,
+                      DevBuf &group, std::vector<int64_t> &ptr_host)
+{
+    cudaStream_t s = ctx->stream;
+    cq_status st;
+    void *vc;
+    if ((st = cq_scratch(ctx, "split_cnt", 8 * ((size_t)n_groups + 1), &vc)) != CQ_OK) return st;
+    if ((st = cq_alloc(ctx, ptr, 8 * ((size_t)n_groups + 1))) != CQ_OK) return st;
+    const size_t shm = 4 * (size_t)((gr->n_kappa + 31) / 32);
+    cudaFuncSetAttribute(k_group_kappa<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(k_group_kappa<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k_group_kappa<false><<<n_groups, 256, shm, s>>>(gsize, atoms, p->row_ptr.as<int64_t>(),
+                                                    p->col.as<int32_t>(), gr->kg_of.as<int32_t>(),
+                                                    gr->n_kappa, (int64_t *)vc, nullptr, nullptr);
+    cq_count_launch();
+    if ((st = cq_scan_i64(ctx, (int64_t *)vc, ptr.as<int64_t>(), n_groups)) != CQ_OK) return st;
+    ptr_host.assign((size_t)n_groups + 1, 0);
+    cudaMemcpyAsync(ptr_host.data(), ptr.ptr, 8 * ptr_host.size(), cudaMemcpyDeviceToHost, s);
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "group lists")) != CQ_OK) return st;
+    const int64_t n = ptr_host[n_groups];
+    if ((st = cq_alloc(ctx, kappa, 4 * (size_t)(n + 1))) != CQ_OK) return st;
+    k_group_kappa<true><<<n_groups, 256, shm, s>>>(gsize, atoms, p->row_ptr.as<int64_t>(),
+                                                   p->col.as<int32_t>(), gr->kg_of.as<int32_t>(),
+                                                   gr->n_kappa, nullptr, ptr.as<int64_t>(),
+                                                   kappa.as<int32_t>());
+    cq_count_launch();
+    std::vector<int32_t> grp((size_t)n);
+    for (int q = 0; q < n_groups; ++q)
+        for (int64_t e = ptr_host[q]; e < ptr_host[q + 1]; ++e) grp[e] = q;
+    if ((st = upload(ctx, group, grp.data(), 4 * grp.size())) != CQ_OK) return st;
+    return cq_check_cuda(ctx, cudaStreamSynchronize(s), "group lists");
+}
+
+cq_status get_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
+                   const cq_pattern *pC, const Groups *gr, SplitPlan **out)
 {
     auto key = std::make_tuple(2, pA->id, pB->id, pC->id);
     auto it = ctx->aux.find(key);
     if (it != ctx->aux.end()) {
-        *out = static_cast<SplitTiles *>(it->second.get());
+        *out = static_cast<SplitPlan *>(it->second.get());
         return CQ_OK;
     }
     cudaStream_t s = ctx->stream;
-    auto st_ = std::make_shared<SplitTiles>();
+    auto pl = std::make_shared<SplitPlan>();
+    cq_status st;
+    // tiles, sorted by (g, h)
     const int64_t nbits = (int64_t)gr->n_g * gr->n_h;
     const int64_t nwords = (nbits + 31) / 32;
     void *vb;
-    cq_status st = cq_scratch(ctx, "split_bits", 4 * nwords, &vb);
-    if (st != CQ_OK) return st;
+    if ((st = cq_scratch(ctx, "split_bits", 4 * nwords, &vb)) != CQ_OK) return st;
     cudaMemsetAsync(vb, 0, 4 * nwords, s);
     if (pC->n_blocks > 0) {
         k_tile_mark<<<(unsigned)((pC->n_blocks + 255) / 256), 256, 0, s>>>(
@@ -415,63 +552,145 @@ cq_status get_tiles(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
     if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "tile mark")) != CQ_OK) return st;
     std::vector<int2> tiles;
     for (int64_t b = 0; b < nbits; ++b)
-        if (bits[b >> 5] & (1u << (b & 31))) tiles.push_back(make_int2((int)(b / gr->n_h), (int)(b % gr->n_h)));
-    st_->n_tiles = (int)tiles.size();
-    if ((st = cq_alloc(ctx, st_->tiles, sizeof(int2) * (tiles.size() + 1))) != CQ_OK ||
-        (st = cq_alloc(ctx, st_->kstart, sizeof(int64_t) * (tiles.size() + 1))) != CQ_OK)
+        if (bits[b >> 5] & (1u << (b & 31)))
+            tiles.push_back(make_int2((int)(b / gr->n_h), (int)(b % gr->n_h)));
+    pl->n_tiles = (int)tiles.size();
+    if ((st = upload(ctx, pl->tiles, tiles.data(), sizeof(int2) * tiles.size())) != CQ_OK) return st;
+    // K-group lists of the M groups (rows of P_A) and of the N groups (rows of P_B)
+    std::vector<int64_t> ga_host, hb_host;
+    if ((st = group_lists(ctx, gr, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA, pl->ga_ptr,
+                          pl->ga_kappa, pl->ga_group, ga_host)) != CQ_OK ||
+        (st = group_lists(ctx, gr, gr->n_h, gr->gj, gr->h_atoms.as<int32_t>(), pB, pl->hb_ptr,
+                          pl->hb_kappa, pl->hb_group, hb_host)) != CQ_OK)
         return st;
-    cudaMemcpyAsync(st_->tiles.ptr, tiles.data(), sizeof(int2) * tiles.size(),
-                    cudaMemcpyHostToDevice, s);
+    pl->n_ga = ga_host[gr->n_g];
+    pl->n_hb = hb_host[gr->n_h];
+    if (tiles.empty()) {
+        *out = pl.get();
+        ctx->aux[key] = pl;
+        return CQ_OK;
+    }
+    // K groups and chunk table of every tile
     const int n_atoms = pA->geo->n_atoms;
-    const size_t shm = 2 * 4 * (size_t)((n_atoms + 31) / 32);
+    const size_t shm = 4 * (size_t)(2 * ((n_atoms + 31) / 32) + (gr->n_kappa + 31) / 32);
     if (shm > 200 * 1024) return cq_fail(ctx, CQ_ERR_INVALID, "split product: too many atoms");
     void *vc;
-    if ((st = cq_scratch(ctx, "split_kcnt", 8 * (tiles.size() + 1), &vc)) != CQ_OK) return st;
-    if (!tiles.empty()) {
-        cudaFuncSetAttribute(k_tile_klist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-        cudaFuncSetAttribute(k_tile_klist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-        k_tile_klist<false><<<st_->n_tiles, 256, shm, s>>>(
-            n_atoms, st_->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
-            gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
-            pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), (int64_t *)vc, nullptr, nullptr);
-        cq_count_launch();
-    }
-    if ((st = cq_scan_i64(ctx, (int64_t *)vc, st_->kstart.as<int64_t>(), st_->n_tiles)) != CQ_OK)
+    if ((st = cq_scratch(ctx, "split_cnt", 8 * (tiles.size() + 1), &vc)) != CQ_OK) return st;
+    if ((st = cq_alloc(ctx, pl->kstart, 8 * (tiles.size() + 1))) != CQ_OK) return st;
+    cudaFuncSetAttribute(k_tile_kappa<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(k_tile_kappa<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k_tile_kappa<false><<<pl->n_tiles, 256, shm, s>>>(
+        n_atoms, pl->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
+        gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
+        pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), gr->kg_of.as<int32_t>(), gr->n_kappa,
+        (int64_t *)vc, nullptr, nullptr);
+    cq_count_launch();
+    if ((st = cq_scan_i64(ctx, (int64_t *)vc, pl->kstart.as<int64_t>(), pl->n_tiles)) != CQ_OK)
         return st;
-    cudaMemcpyAsync(&st_->n_k, st_->kstart.as<int64_t>() + st_->n_tiles, 8, cudaMemcpyDeviceToHost, s);
-    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "k lists")) != CQ_OK) return st;
-    if ((st = cq_alloc(ctx, st_->klist, 4 * (st_->n_k + 1))) != CQ_OK) return st;
-    {
-        std::vector<int64_t> ks(st_->n_tiles + 1);
-        cudaMemcpyAsync(ks.data(), st_->kstart.ptr, 8 * ks.size(), cudaMemcpyDeviceToHost, s);
-        if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "k lists")) != CQ_OK) return st;
-        double chunks = 0.0;
-        for (int q = 0; q < st_->n_tiles; ++q)
-            chunks += (double)((ks[q + 1] - ks[q] + gr->ca - 1) / gr->ca);
-        st_->mma_flops = chunks * 6.0 * KSTEPS * 2.0 * MT * NT * 16;
+    std::vector<int64_t> ks(pl->n_tiles + 1);
+    cudaMemcpyAsync(ks.data(), pl->kstart.ptr, 8 * ks.size(), cudaMemcpyDeviceToHost, s);
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "tile chunks")) != CQ_OK) return st;
+    pl->n_chunks = ks[pl->n_tiles];
+    pl->mma_flops = (double)pl->n_chunks * 6.0 * KSTEPS * 2.0 * MT * NT * 16;
+    if ((st = cq_alloc(ctx, pl->tile_kappa, 4 * (size_t)(pl->n_chunks + 1))) != CQ_OK ||
+        (st = cq_alloc(ctx, pl->chunks, sizeof(int2) * (size_t)(pl->n_chunks + 1))) != CQ_OK ||
+        (st = cq_alloc(ctx, pl->cidx, 4 * ((size_t)pl->n_tiles * gr->gi * gr->gj + 1))) != CQ_OK)
+        return st;
+    k_tile_kappa<true><<<pl->n_tiles, 256, shm, s>>>(
+        n_atoms, pl->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
+        gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
+        pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), gr->kg_of.as<int32_t>(), gr->n_kappa,
+        nullptr, pl->kstart.as<int64_t>(), pl->tile_kappa.as<int32_t>());
+    k_tile_chunks<<<pl->n_tiles, 256, 0, s>>>(
+        pl->tiles.as<int2>(), pl->kstart.as<int64_t>(), pl->tile_kappa.as<int32_t>(),
+        pl->ga_ptr.as<int64_t>(), pl->ga_kappa.as<int32_t>(), pl->hb_ptr.as<int64_t>(),
+        pl->hb_kappa.as<int32_t>(), pl->chunks.as<int2>());
+    k_tile_cidx<<<pl->n_tiles, 256, 0, s>>>(
+        pl->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
+        gr->h_atoms.as<int32_t>(), pC->row_ptr.as<int64_t>(), pC->col.as<int32_t>(),
+        pl->cidx.as<int32_t>());
+    cq_count_launch(3);
+    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "split plan")) != CQ_OK) return st;
+    // batches of whole M groups (tiles are sorted by g) whose A panels fit A_PANEL_CAP
+    const int64_t cap = std::max<int64_t>(1, (int64_t)(A_PANEL_CAP / A_CHUNK));
+    int t0 = 0;
+    while (t0 < pl->n_tiles) {
+        const int g0 = tiles[t0].x;
+        int t1 = t0, g1 = g0;
+        while (t1 < pl->n_tiles) {
+            const int g = tiles[t1].x;
+            if (g != g1) {  // the next M group starts; keep it only if its panels still fit
+                if (ga_host[g + 1] - ga_host[g0] > cap) break;
+                g1 = g;
+            }
+            ++t1;
+        }
+        pl->batches.push_back({t0, t1, ga_host[g0], ga_host[g1 + 1]});
+        pl->batch_chunks.push_back(ks[t1] - ks[t0]);
+        t0 = t1;
     }
-    if (!tiles.empty()) {
-        k_tile_klist<true><<<st_->n_tiles, 256, shm, s>>>(
-            n_atoms, st_->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
-            gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
-            pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), nullptr, st_->kstart.as<int64_t>(),
-            st_->klist.as<int32_t>());
+    *out = pl.get();
+    ctx->aux[key] = pl;
+    return CQ_OK;
+}
+
+template <int NB>
+cq_status run_split(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double alpha,
+                    const cq_pattern *pA, const double *A, const cq_pattern *pB,
+                    const double *B, double beta, const cq_pattern *pC, double *C, double flops)
+{
+    cudaStream_t s = ctx->stream;
+    cq_status st;
+    size_t a_bytes = 0;
+    for (const Batch &b : pl->batches) a_bytes = std::max(a_bytes, (size_t)(b.e1 - b.e0) * A_CHUNK);
+    void *va, *vb;
+    if ((st = cq_scratch(ctx, "split_A", a_bytes, &va)) != CQ_OK) return st;
+    if ((st = cq_scratch(ctx, "split_B", (size_t)pl->n_hb * B_CHUNK, &vb)) != CQ_OK) return st;
+    static bool attr_set = false;  // once per process (outside any graph capture)
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_bsmm_split<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        cudaFuncSetAttribute(k_bsmm_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        attr_set = true;
+    }
+    if (pl->n_hb > 0) {
+        k_pack_b<NB><<<(unsigned)pl->n_hb, 256, 0, s>>>(
+            pl->hb_group.as<int32_t>(), pl->hb_kappa.as<int32_t>(), gr->h_atoms.as<int32_t>(),
+            gr->kg_atoms.as<int32_t>(), pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(),
+            pB->transpose.as<int64_t>(), B, pB->uniform, (uint8_t *)vb);
         cq_count_launch();
     }
-    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "k lists")) != CQ_OK) return st;
-    const int w = gr->gi + gr->gj;
-    if ((st = cq_alloc(ctx, st_->table, 4 * (size_t)(st_->n_k + 1) * w)) != CQ_OK) return st;
-    if (!tiles.empty()) {
-        k_tile_index<<<st_->n_tiles, 256, 0, s>>>(
-            st_->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
-            gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
-            pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), pB->transpose.as<int64_t>(),
-            st_->kstart.as<int64_t>(), st_->klist.as<int32_t>(), st_->table.as<int32_t>());
+    for (size_t q = 0; q < pl->batches.size(); ++q) {
+        const Batch &b = pl->batches[q];
+        if (b.e1 > b.e0) {
+            k_pack_a<NB><<<(unsigned)(b.e1 - b.e0), 256, 0, s>>>(
+                b.e0, pl->ga_group.as<int32_t>(), pl->ga_kappa.as<int32_t>(),
+                gr->g_atoms.as<int32_t>(), gr->kg_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(),
+                pA->col.as<int32_t>(), A, pA->uniform, (uint8_t *)va);
+            cq_count_launch();
+        }
+        SplitArgs a;
+        a.n_tiles = b.tile1 - b.tile0;
+        a.kstart = pl->kstart.as<int64_t>() + b.tile0;
+        a.chunks = pl->chunks.as<int2>();
+        a.cidx = pl->cidx.as<int32_t>() + (int64_t)b.tile0 * gr->gi * gr->gj;
+        a.panel_a = (const uint8_t *)va;
+        a.ea0 = b.e0;
+        a.panel_b = (const uint8_t *)vb;
+        a.C = C;
+        a.c_stride = pC->uniform;
+        a.alpha = alpha;
+        a.beta = beta;
+        a.flag = ctx->flag.as<int32_t>();
+        // this launch's share of the product's useful and tensor-core flops
+        const double share =
+            pl->n_chunks > 0 ? (double)pl->batch_chunks[q] / (double)pl->n_chunks : 0.0;
+        const int grid = std::min(a.n_tiles, ctx->num_sms);
+        cq_timing_begin(ctx, flops * share, pl->mma_flops * share);
+        k_bsmm_split<NB><<<grid, ST, SMEM, s>>>(a);
+        cq_timing_end(ctx);
         cq_count_launch();
+        if ((st = cq_check_cuda(ctx, cudaGetLastError(), "bsmm_split")) != CQ_OK) return st;
     }
-    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "tile index")) != CQ_OK) return st;
-    *out = st_.get();
-    ctx->aux[key] = st_;
     return CQ_OK;
 }
 
@@ -486,78 +705,12 @@ cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_
         return cq_fail(ctx, CQ_ERR_INVALID,
                        "split-BF16 product: needs a uniform basis of 4 or 9 orbitals per atom");
     if (pC->n_blocks == 0) return CQ_OK;
-    cudaStream_t s = ctx->stream;
     Groups *gr;
-    SplitTiles *tiles;
+    SplitPlan *pl;
     cq_status st = get_groups(ctx, pC, &gr);
     if (st != CQ_OK) return st;
-    if ((st = get_tiles(ctx, pA, pB, pC, gr, &tiles)) != CQ_OK) return st;
-    // operands in split form: per plane a main array (8 values per block row, nb = 9) and a
-    // tail array (4 values per block row)
-    const int mainw = nb == 9 ? KLayout<9>::MAINW : KLayout<4>::MAINW;
-    const int ka = mainw + TAILW;
-    const int64_t ra = pA->n_blocks * nb, rb = pB->n_blocks * nb;  // block rows
-    void *va, *vb;
-    if ((st = cq_scratch(ctx, "split_A", 3 * 2 * (size_t)(ra * ka), &va)) != CQ_OK) return st;
-    if ((st = cq_scratch(ctx, "split_B", 3 * 2 * (size_t)(rb * ka), &vb)) != CQ_OK) return st;
-    SplitPlanes pa, pb;
-    {
-        __nv_bfloat16 *x = (__nv_bfloat16 *)va, *y = (__nv_bfloat16 *)vb;
-        for (int q = 0; q < 3; ++q) {
-            pa.main[q] = x + q * ra * mainw;
-            pb.main[q] = y + q * rb * mainw;
-        }
-        for (int q = 0; q < 3; ++q) {
-            pa.tail[q] = x + 3 * ra * mainw + q * ra * TAILW;
-            pb.tail[q] = y + 3 * rb * mainw + q * rb * TAILW;
-        }
-    }
-    if (ra > 0)
-        k_split_a<<<(unsigned)((ra * ka + 255) / 256), 256, 0, s>>>(ra * ka, nb, mainw,
-                                                                   pA->uniform, A, pa);
-    if (rb > 0)
-        k_split_b<<<(unsigned)((rb * ka + 255) / 256), 256, 0, s>>>(rb * ka, nb, mainw,
-                                                                   pB->uniform, B, pb);
-    cq_count_launch((ra > 0) + (rb > 0));
-    SplitArgs a;
-    a.n_tiles = tiles->n_tiles;
-    a.tiles = tiles->tiles.as<int2>();
-    a.kstart = tiles->kstart.as<int64_t>();
-    a.klist = tiles->klist.as<int32_t>();
-    a.table = tiles->table.as<int32_t>();
-    a.g_atoms = gr->g_atoms.as<int32_t>();
-    a.h_atoms = gr->h_atoms.as<int32_t>();
-    a.a_rp = pA->row_ptr.as<int64_t>();
-    a.b_rp = pB->row_ptr.as<int64_t>();
-    a.c_rp = pC->row_ptr.as<int64_t>();
-    a.a_col = pA->col.as<int32_t>();
-    a.b_col = pB->col.as<int32_t>();
-    a.c_col = pC->col.as<int32_t>();
-    a.b_tr = pB->transpose.as<int64_t>();
-    for (int q = 0; q < 3; ++q) {
-        a.sa_main[q] = pa.main[q];
-        a.sa_tail[q] = pa.tail[q];
-        a.sb_main[q] = pb.main[q];
-        a.sb_tail[q] = pb.tail[q];
-    }
-    a.C = C;
-    a.c_stride = pC->uniform;
-    a.alpha = alpha;
-    a.beta = beta;
-    a.flag = ctx->flag.as<int32_t>();
-    const int grid = std::min(tiles->n_tiles, ctx->num_sms);
-    cq_timing_begin(ctx, tl->flops, tiles->mma_flops);
-    static bool attr_set = false;  // once per process (outside any graph capture)
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_bsmm_split<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        cudaFuncSetAttribute(k_bsmm_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        attr_set = true;
-    }
-    if (nb == 9)
-        k_bsmm_split<9><<<grid, ST, SMEM, s>>>(a);
-    else
-        k_bsmm_split<4><<<grid, ST, SMEM, s>>>(a);
-    cq_timing_end(ctx);
-    cq_count_launch();
-    return cq_check_cuda(ctx, cudaGetLastError(), "bsmm_split");
+    if ((st = get_plan(ctx, pA, pB, pC, gr, &pl)) != CQ_OK) return st;
+    if (pl->n_tiles == 0) return CQ_OK;
+    return nb == 9 ? run_split<9>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops)
+                   : run_split<4>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops);
 }
