@@ -348,6 +348,12 @@ def cubic_min(w1, w2, w3):
     return a if a > 0.0 else None
 
 
+def fallback_alpha(a2, n_values, dd):
+    """Step when the cubic has no minimiser (it falls without bound along D): 2 a2, but at
+    most the step that changes L by 0.01 RMS over its n_values stored values."""
+    return min(2.0 * a2, 0.01 * math.sqrt(n_values / dd)) if dd > 0.0 else 2.0 * a2
+
+
 class LNV:
     """Li-Nunes-Vanderbilt minimisation of E = 2 Tr[(3LSL - 2LSLSL) H] at fixed
     N = 2 Tr[(3LSL - 2LSLSL) S] = n_electrons, over L on the pattern P_L.
@@ -444,7 +450,7 @@ class LNV:
         alpha = cubic_min(gE - mu * gN, e2 - mu * n2, e3 - mu * n3)
         fallback = alpha is None
         if fallback:
-            alpha = 2.0 * a2
+            alpha = fallback_alpha(a2, G.shape[0], dot(D, D))
         self.L = self.L + alpha * D
         self.evaluate()
         ncorr = self.correct_n()

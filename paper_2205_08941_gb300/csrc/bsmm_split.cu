@@ -53,7 +53,8 @@ constexpr int B_CHUNK = 3 * B_PLANE;         // one packed B panel
 constexpr int STAGE = A_CHUNK + B_CHUNK;
 constexpr int BAR_BYTES = 256;
 constexpr int DRAIN = 4;                     // chunks per FP32 accumulation period
-constexpr int TMEM_COLS = 2 * NT;            // two FP32 accumulators
+constexpr int NACC = 4;                      // FP32 accumulators in tensor memory
+constexpr int TMEM_COLS = NACC * NT;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 constexpr size_t A_PANEL_CAP = (size_t)12 << 30;  // scratch bound for one batch of A panels
 

@@ -5,8 +5,9 @@
 //               into a free stage with two TMA bulk copies that complete on the stage's
 //               "full" barrier; the warp's lanes load the chunk table 32 entries at a time;
 //   warp 1      lane 0 issues the 18 MMAs of a chunk (3 K steps x 6 split products) into
-//               one of two TMEM accumulators and commits them to the stage's "empty"
-//               barrier, and at the end of a drain period to the accumulator's "full" barrier;
+//               one of NACC TMEM accumulators (one per drain period, in rotation) and
+//               commits them to the stage's "empty" barrier, and at the end of a drain
+//               period to the accumulator's "full" barrier;
 //   warps 2-9   drain: every DRAIN chunks they read the FP32 accumulator (warp w: TMEM lane
 //               quarter w % 4, columns 32 * ((w - 2) / 4) ..) into double-float (hi, lo)
 //               sums in registers, release the accumulator, and write C after a tile's last
@@ -22,7 +23,7 @@ constexpr int N_DRAIN = 256;           // drain threads
 constexpr int W_PROD = 0, W_MMA = 1;   // producer warp, MMA warp
 
 struct Bars {
-    uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], done;
+    uint64_t full[NS], empty[NS], acc_full[NACC], acc_empty[NACC], done;
     uint32_t tmem_slot;
     int abort_flag;
 };
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->empty[s])),
                          "r"(1));
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
                              smem_u32(&bars->acc_full[b])),
                          "r"(1));
@@ -208,12 +209,16 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
             uint32_t cg = 0, pg = 0;
             bool ok = true, issued = false;
             const int pq[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
+            // descriptors of stage 0; a stage, plane or K step only moves the 14-bit start
+            // address field (shared addresses stay below 256 KB, so no carry leaves it)
+            const uint64_t da0 = smem_desc(sm0), db0 = smem_desc(sm0 + A_CHUNK);
             for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
                 const int nch = (int)(p.kstart[tile + 1] - p.kstart[tile]);
                 for (int c = 0; c < nch; ++c, ++cg) {
-                    const uint32_t b = pg & 1u;
-                    if (c % DRAIN == 0 && pg >= 2 &&
-                        !bar_wait(smem_u32(&bars->acc_empty[b]), ((pg / 2) + 1) & 1u, abort_flag)) {
+                    const uint32_t b = pg % NACC;
+                    if (c % DRAIN == 0 && pg >= (uint32_t)NACC &&
+                        !bar_wait(smem_u32(&bars->acc_empty[b]), ((pg / NACC) + 1) & 1u,
+                                  abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -223,14 +228,15 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t ab = sm0 + s * STAGE, bb = ab + A_CHUNK;
+                    const uint64_t sa = da0 + (uint64_t)((s * STAGE) >> 4);
+                    const uint64_t sb = db0 + (uint64_t)((s * STAGE) >> 4);
                     const uint32_t acc_addr = tmem + b * NT;
 #pragma unroll
                     for (int ks = 0; ks < KSTEPS; ++ks)
 #pragma unroll
                         for (int x = 0; x < 6; ++x) {
-                            const uint64_t ad = smem_desc(ab + pq[x][0] * A_PLANE + ks * 256);
-                            const uint64_t bd = smem_desc(bb + pq[x][1] * B_PLANE + ks * 256);
+                            const uint64_t ad = sa + (uint64_t)((pq[x][0] * A_PLANE + ks * 256) >> 4);
+                            const uint64_t bd = sb + (uint64_t)((pq[x][1] * B_PLANE + ks * 256) >> 4);
                             const uint32_t acc = (c % DRAIN == 0 && ks == 0 && x == 0) ? 0u : 1u;
                             asm volatile(
                                 "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -277,8 +283,8 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
 #pragma unroll
             for (int x = 0; x < 32; ++x) hi[x] = lo[x] = 0.f;
             for (int d = 0; d < np; ++d, ++pg) {
-                const uint32_t b = pg & 1u;
-                if (!bar_wait(smem_u32(&bars->acc_full[b]), (pg / 2) & 1u, abort_flag)) {
+                const uint32_t b = pg % NACC;
+                if (!bar_wait(smem_u32(&bars->acc_full[b]), (pg / NACC) & 1u, abort_flag)) {
                     ok = false;
                     break;
                 }

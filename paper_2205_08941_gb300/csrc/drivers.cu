@@ -616,6 +616,17 @@ extern "C" cq_status cq_lnv_step(cq_lnv *s, cq_lnv_report *rep)
         ok[c] = cubic_min(gE[c] - mu[c] * gNd[c], e2 - mu[c] * n2, e3 - mu[c] * n3, &a);
         alpha[c] = ok[c] ? a : 2.0 * a2[c];
     }
+    // Without a minimiser the cubic falls without bound along D (the functional runs away
+    // from idempotency): step 2*alpha_2, but at most until the RMS change of L reaches 0.01
+    // per stored value.
+    if (std::find(ok.begin(), ok.end(), false) != ok.end()) {
+        std::vector<double> dd;
+        CQ_TRY(dots(s, D, D, dd));
+        for (int c = 0; c < nc; ++c)
+            if (!ok[c] && dd[c] > 0.0)
+                alpha[c] = std::fmin(alpha[c],
+                                     0.01 * std::sqrt((double)pL->seg_scalars[c] / dd[c]));
+    }
     CQ_TRY(axpby_c(ctx, pL, alpha, D, one, s->L));
     std::vector<int> ncorr;
     CQ_TRY(lnv_evaluate_corrected(s, ncorr));

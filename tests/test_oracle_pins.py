@@ -315,3 +315,15 @@ def test_lnv_truncated_monotone(c1):
         assert rec["E"] - mu * rec["N"] <= E_prev - mu * 256.0 + 1e-9
         E_prev = rec["E"]
     assert abs(lnv.N - 256.0) < 1e-8
+
+
+def test_fallback_step_is_bounded_by_the_rms_change_of_L():
+    """Without a minimiser of the exact cubic the step is 2 a2, capped where the RMS change
+    of L over its stored values reaches 0.01."""
+    rng = np.random.default_rng(8)
+    D = rng.normal(size=1000)
+    dd = float(D @ D)
+    a = O.fallback_alpha(10.0, D.size, dd)          # 2 a2 = 20 is far beyond the cap
+    assert np.sqrt(np.mean((a * D) ** 2)) == pytest.approx(0.01, rel=1e-12)
+    small = 1e-6                                      # 2 a2 below the cap is kept
+    assert O.fallback_alpha(small, D.size, dd) == 2.0 * small
