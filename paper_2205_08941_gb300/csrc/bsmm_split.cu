@@ -1,9 +1,9 @@
 // Split-BF16 block-sparse product on the 5th-generation tensor cores (tcgen05 + TMEM).
 //
-// C <- beta C + alpha mask_{P_C}(A.B) with every FP64 operand value split into three BF16
-// terms x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1); the
-// residuals are exact in FP64) and the product formed as the six cross products
-// A_p B_q with p + q <= 2, accumulated in FP32 in tensor memory.  Every DRAIN chunks the
+// C <- beta C + alpha mask_{P_C}(A.B) with every FP64 operand value rounded to FP32 and
+// split into three BF16 terms f = x0 + x1 + x2 (x0 = bf16(f), x1 = bf16(f - x0),
+// x2 = bf16(f - x0 - x1); the residuals are exact in FP32) and the product formed as the
+// six cross products A_p B_q with p + q <= 2, accumulated in FP32 in tensor memory.  Every DRAIN chunks the
 // FP32 accumulator is drained into a per-thread double-float (hi, lo) sum, so FP32
 // rounding only acts within a drain period; the result is written back in FP64.
 //
@@ -95,14 +95,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                            ((uint32_t)(MT >> 4) << 24);
 
+// x rounded once to FP32 (24 significand bits, what three BF16 terms can hold), then split
+// in FP32: b0 = bf16(f), b1 = bf16(f - b0), b2 = bf16(f - b0 - b1); both differences are
+// exact in FP32.  One FP64 operation per value (the FP64 pipe is the scarce unit here).
 __device__ __forceinline__ void split3(double x, __nv_bfloat16 &b0, __nv_bfloat16 &b1,
                                        __nv_bfloat16 &b2)
 {
-    b0 = __double2bfloat16(x);
-    double r = x - (double)__bfloat162float(b0);
-    b1 = __double2bfloat16(r);
-    r = r - (double)__bfloat162float(b1);
-    b2 = __double2bfloat16(r);
+    const float f = (float)x;
+    b0 = __float2bfloat16_rn(f);
+    const float r1 = f - __bfloat162float(b0);
+    b1 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(b1);
+    b2 = __float2bfloat16_rn(r2);
 }
 
 // index of block (row, col) in a pattern, or -1
@@ -273,27 +277,68 @@ k_tile_cidx(const int2 *tiles, int gi, int gj, const int32_t *g_atoms, const int
 
 // ---------------------------------------------------------------- panel packing
 
-// Writes one row of one atom's K pieces (three planes) of a panel: x[m], m < MAINW + 4,
-// split into BF16 terms; the main piece is one 16-byte store, the tail one 8-byte store.
-template <int NB>
-__device__ __forceinline__ void put_piece(uint8_t *panel, int plane_bytes, int r, int a,
-                                          const double (&x)[KLayout<NB>::MAINW + TAILW])
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi)
 {
-    constexpr int MW = KLayout<NB>::MAINW;
-    __align__(16) __nv_bfloat16 v[3][MW + TAILW];
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// Writes one row of the K pieces of a pair of atoms (a0 even, a0 + 1) of a panel, three
+// planes: x0[m], x1[m] (m < MAINW + 4) split into BF16 terms.  Every store is a whole
+// 16-byte core-matrix row: the two main pieces and the column the two tails share.
+template <int NB>
+__device__ __forceinline__ void put_pair(uint8_t *panel, int plane_bytes, int r, int a0,
+                                         const double (&x0)[KLayout<NB>::MAINW + TAILW],
+                                         const double (&x1)[KLayout<NB>::MAINW + TAILW])
+{
+    constexpr int MW = KLayout<NB>::MAINW, KA = MW + TAILW;
+    __nv_bfloat16 v0[3][KA], v1[3][KA];
 #pragma unroll
-    for (int m = 0; m < MW + TAILW; ++m) split3(x[m], v[0][m], v[1][m], v[2][m]);
+    for (int m = 0; m < KA; ++m) {
+        split3(x0[m], v0[0][m], v0[1][m], v0[2][m]);
+        split3(x1[m], v1[0][m], v1[1][m], v1[2][m]);
+    }
 #pragma unroll
     for (int pl = 0; pl < 3; ++pl) {
         uint8_t *base = panel + pl * plane_bytes;
         if (MW) {
-            uint4 w;
-            memcpy(&w, &v[pl][0], 16);
-            *reinterpret_cast<uint4 *>(base + tile_off(r, KLayout<NB>::main_col(a), 0)) = w;
+            uint4 w0, w1;
+            w0.x = pack_bf16x2(v0[pl][0], v0[pl][1]);
+            w0.y = pack_bf16x2(v0[pl][2], v0[pl][3]);
+            w0.z = pack_bf16x2(v0[pl][4], v0[pl][5]);
+            w0.w = pack_bf16x2(v0[pl][6], v0[pl][7]);
+            w1.x = pack_bf16x2(v1[pl][0], v1[pl][1]);
+            w1.y = pack_bf16x2(v1[pl][2], v1[pl][3]);
+            w1.z = pack_bf16x2(v1[pl][4], v1[pl][5]);
+            w1.w = pack_bf16x2(v1[pl][6], v1[pl][7]);
+            *reinterpret_cast<uint4 *>(base + tile_off(r, KLayout<NB>::main_col(a0), 0)) = w0;
+            *reinterpret_cast<uint4 *>(base + tile_off(r, KLayout<NB>::main_col(a0 + 1), 0)) = w1;
         }
-        uint2 w2;
-        memcpy(&w2, &v[pl][MW], 8);
-        *reinterpret_cast<uint2 *>(base + tile_off(r, KLayout<NB>::tail_col(a), (a & 1) * 8)) = w2;
+        uint4 t;
+        t.x = pack_bf16x2(v0[pl][MW], v0[pl][MW + 1]);
+        t.y = pack_bf16x2(v0[pl][MW + 2], v0[pl][MW + 3]);
+        t.z = pack_bf16x2(v1[pl][MW], v1[pl][MW + 1]);
+        t.w = pack_bf16x2(v1[pl][MW + 2], v1[pl][MW + 3]);
+        *reinterpret_cast<uint4 *>(base + tile_off(r, KLayout<NB>::tail_col(a0), 0)) = t;
+    }
+}
+
+// Block index of every (slot, K-group atom) pair of every panel entry (one CTA per entry):
+// A side (LEFT): block (i_slot, k) of P_A; B side: block (k, j_slot) of P_B, found as
+// block (j, k) of row j and its transpose.  -1 where the pattern has no block.  Patterns
+// do not change between products, so the table is built once per pattern triple.
+template <bool LEFT>
+__global__ void __launch_bounds__(256)
+k_panel_index(int gsize, int ca, const int32_t *ent_group, const int32_t *ent_kappa,
+              const int32_t *atoms, const int32_t *kg_atoms, const int64_t *rp,
+              const int32_t *col, const int64_t *tr, int32_t *index)
+{
+    const int64_t e = blockIdx.x;
+    const int grp = ent_group[e], kk = ent_kappa[e];
+    for (int q = threadIdx.x; q < gsize * ca; q += blockDim.x) {
+        const int x = atoms[(int64_t)grp * gsize + q / ca], k = kg_atoms[(int64_t)kk * ca + q % ca];
+        int64_t b = (x >= 0 && k >= 0) ? find_block(rp, col, x, k) : -1;
+        if (!LEFT && b >= 0) b = tr[b];
+        index[e * gsize * ca + q] = (int32_t)b;
     }
 }
 
@@ -301,61 +346,51 @@ __device__ __forceinline__ void put_piece(uint8_t *panel, int plane_bytes, int r
 // row r = (slot r / NB of g, orbital o = r % NB), K = (atom a of kk, orbital m): A_ik[o][m].
 template <int NB>
 __global__ void __launch_bounds__(256)
-k_pack_a(int64_t e0, const int32_t *ent_group, const int32_t *ent_kappa, const int32_t *g_atoms,
-         const int32_t *kg_atoms, const int64_t *rp, const int32_t *col,
-         const double *__restrict__ A, int stride, uint8_t *panels)
+k_pack_a(int64_t e0, const int32_t *index, const double *__restrict__ A, int stride,
+         uint8_t *panels)
 {
     constexpr int GI = MT / NB, CA = KLayout<NB>::CA, KA = KLayout<NB>::MAINW + TAILW;
-    __shared__ int64_t blk[GI * CA];
-    const int64_t e = e0 + blockIdx.x;
-    const int g = ent_group[e], kk = ent_kappa[e];
-    for (int q = threadIdx.x; q < GI * CA; q += blockDim.x) {
-        const int i = g_atoms[(int64_t)g * GI + q / CA], k = kg_atoms[(int64_t)kk * CA + q % CA];
-        blk[q] = (i >= 0 && k >= 0) ? find_block(rp, col, i, k) : -1;
-    }
-    __syncthreads();
+    const int32_t *blk = index + (e0 + blockIdx.x) * (GI * CA);
     uint8_t *panel = panels + (int64_t)blockIdx.x * A_CHUNK;
-    for (int q = threadIdx.x; q < MT * CA; q += blockDim.x) {
-        const int a = q / MT, r = q % MT;
-        const int64_t b = r < GI * NB ? blk[(r / NB) * CA + a] : -1;
+    for (int q = threadIdx.x; q < MT * (CA / 2); q += blockDim.x) {
+        const int a0 = 2 * (q / MT), r = q % MT;
+        const bool row = r < GI * NB;
+        const int64_t b0 = row ? __ldg(&blk[(r / NB) * CA + a0]) : -1;
+        const int64_t b1 = row ? __ldg(&blk[(r / NB) * CA + a0 + 1]) : -1;
         const int o = r % NB;
-        double x[KA];
+        double x0[KA], x1[KA];
 #pragma unroll
-        for (int m = 0; m < KA; ++m)
-            x[m] = (b >= 0 && m < NB) ? A[b * stride + o * NB + m] : 0.0;
-        put_piece<NB>(panel, A_PLANE, r, a, x);
+        for (int m = 0; m < KA; ++m) {
+            x0[m] = (b0 >= 0 && m < NB) ? A[b0 * stride + o * NB + m] : 0.0;
+            x1[m] = (b1 >= 0 && m < NB) ? A[b1 * stride + o * NB + m] : 0.0;
+        }
+        put_pair<NB>(panel, A_PLANE, r, a0, x0, x1);
     }
 }
 
 // B panels (one CTA per entry = (N group h, K group kk)): row r = (slot r / NB of h,
-// orbital o of j), K = (atom a of kk, orbital m): B_kj[m][o], found through block (j, k)
-// of row j and the transpose map.
+// orbital o of j), K = (atom a of kk, orbital m): B_kj[m][o].
 template <int NB>
 __global__ void __launch_bounds__(256)
-k_pack_b(const int32_t *ent_group, const int32_t *ent_kappa, const int32_t *h_atoms,
-         const int32_t *kg_atoms, const int64_t *rp, const int32_t *col, const int64_t *tr,
-         const double *__restrict__ B, int stride, uint8_t *panels)
+k_pack_b(const int32_t *index, const double *__restrict__ B, int stride, uint8_t *panels)
 {
     constexpr int GJ = NT / NB, CA = KLayout<NB>::CA, KA = KLayout<NB>::MAINW + TAILW;
-    __shared__ int64_t blk[GJ * CA];
     const int64_t e = blockIdx.x;
-    const int h = ent_group[e], kk = ent_kappa[e];
-    for (int q = threadIdx.x; q < GJ * CA; q += blockDim.x) {
-        const int j = h_atoms[(int64_t)h * GJ + q / CA], k = kg_atoms[(int64_t)kk * CA + q % CA];
-        const int64_t jk = (j >= 0 && k >= 0) ? find_block(rp, col, j, k) : -1;
-        blk[q] = jk >= 0 ? tr[jk] : -1;
-    }
-    __syncthreads();
+    const int32_t *blk = index + e * (GJ * CA);
     uint8_t *panel = panels + e * B_CHUNK;
-    for (int q = threadIdx.x; q < NT * CA; q += blockDim.x) {
-        const int a = q / NT, r = q % NT;
-        const int64_t b = r < GJ * NB ? blk[(r / NB) * CA + a] : -1;
+    for (int q = threadIdx.x; q < NT * (CA / 2); q += blockDim.x) {
+        const int a0 = 2 * (q / NT), r = q % NT;
+        const bool row = r < GJ * NB;
+        const int64_t b0 = row ? __ldg(&blk[(r / NB) * CA + a0]) : -1;
+        const int64_t b1 = row ? __ldg(&blk[(r / NB) * CA + a0 + 1]) : -1;
         const int o = r % NB;
-        double x[KA];
+        double x0[KA], x1[KA];
 #pragma unroll
-        for (int m = 0; m < KA; ++m)
-            x[m] = (b >= 0 && m < NB) ? B[b * stride + m * NB + o] : 0.0;
-        put_piece<NB>(panel, B_PLANE, r, a, x);
+        for (int m = 0; m < KA; ++m) {
+            x0[m] = (b0 >= 0 && m < NB) ? B[b0 * stride + m * NB + o] : 0.0;
+            x1[m] = (b1 >= 0 && m < NB) ? B[b1 * stride + m * NB + o] : 0.0;
+        }
+        put_pair<NB>(panel, B_PLANE, r, a0, x0, x1);
     }
 }
 
@@ -407,6 +442,7 @@ struct SplitPlan {
     std::vector<int64_t> batch_chunks;
     DevBuf tiles, kstart, tile_kappa, chunks, cidx;
     DevBuf ga_ptr, ga_kappa, ga_group, hb_ptr, hb_kappa, hb_group;
+    DevBuf ga_index, hb_index;  // block of every (slot, K-group atom) pair of every entry
 };
 
 // Morton order of the atoms (positions quantised to 1024 per box edge).
@@ -566,6 +602,24 @@ cq_status get_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
         return st;
     pl->n_ga = ga_host[gr->n_g];
     pl->n_hb = hb_host[gr->n_h];
+    if ((st = cq_alloc(ctx, pl->ga_index, 4 * ((size_t)pl->n_ga * gr->gi * gr->ca + 1))) != CQ_OK ||
+        (st = cq_alloc(ctx, pl->hb_index, 4 * ((size_t)pl->n_hb * gr->gj * gr->ca + 1))) != CQ_OK)
+        return st;
+    if (pl->n_ga > 0) {
+        k_panel_index<true><<<(unsigned)pl->n_ga, 256, 0, s>>>(
+            gr->gi, gr->ca, pl->ga_group.as<int32_t>(), pl->ga_kappa.as<int32_t>(),
+            gr->g_atoms.as<int32_t>(), gr->kg_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(),
+            pA->col.as<int32_t>(), nullptr, pl->ga_index.as<int32_t>());
+        cq_count_launch();
+    }
+    if (pl->n_hb > 0) {
+        k_panel_index<false><<<(unsigned)pl->n_hb, 256, 0, s>>>(
+            gr->gj, gr->ca, pl->hb_group.as<int32_t>(), pl->hb_kappa.as<int32_t>(),
+            gr->h_atoms.as<int32_t>(), gr->kg_atoms.as<int32_t>(), pB->row_ptr.as<int64_t>(),
+            pB->col.as<int32_t>(), pB->transpose.as<int64_t>(), pl->hb_index.as<int32_t>());
+        cq_count_launch();
+    }
+    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "panel index")) != CQ_OK) return st;
     if (tiles.empty()) {
         *out = pl.get();
         ctx->aux[key] = pl;
@@ -654,19 +708,15 @@ cq_status run_split(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double a
         attr_set = true;
     }
     if (pl->n_hb > 0) {
-        k_pack_b<NB><<<(unsigned)pl->n_hb, 256, 0, s>>>(
-            pl->hb_group.as<int32_t>(), pl->hb_kappa.as<int32_t>(), gr->h_atoms.as<int32_t>(),
-            gr->kg_atoms.as<int32_t>(), pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(),
-            pB->transpose.as<int64_t>(), B, pB->uniform, (uint8_t *)vb);
+        k_pack_b<NB><<<(unsigned)pl->n_hb, 256, 0, s>>>(pl->hb_index.as<int32_t>(), B,
+                                                         pB->uniform, (uint8_t *)vb);
         cq_count_launch();
     }
     for (size_t q = 0; q < pl->batches.size(); ++q) {
         const Batch &b = pl->batches[q];
         if (b.e1 > b.e0) {
             k_pack_a<NB><<<(unsigned)(b.e1 - b.e0), 256, 0, s>>>(
-                b.e0, pl->ga_group.as<int32_t>(), pl->ga_kappa.as<int32_t>(),
-                gr->g_atoms.as<int32_t>(), gr->kg_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(),
-                pA->col.as<int32_t>(), A, pA->uniform, (uint8_t *)va);
+                b.e0, pl->ga_index.as<int32_t>(), A, pA->uniform, (uint8_t *)va);
             cq_count_launch();
         }
         SplitArgs a;
