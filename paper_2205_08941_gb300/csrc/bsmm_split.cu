@@ -1,11 +1,11 @@
 // Split-BF16 block-sparse product on the 5th-generation tensor cores (tcgen05 + TMEM).
 //
-// C <- beta C + alpha mask_{P_C}(A.B) with every FP64 operand value rounded to FP32 and
-// split into three BF16 terms f = x0 + x1 + x2 (x0 = bf16(f), x1 = bf16(f - x0),
-// x2 = bf16(f - x0 - x1); the residuals are exact in FP32) and the product formed as the
-// six cross products A_p B_q with p + q <= 2, accumulated in FP32 in tensor memory.  Every DRAIN chunks the
-// FP32 accumulator is drained into a per-thread double-float (hi, lo) sum, so FP32
-// rounding only acts within a drain period; the result is written back in FP64.
+// C <- beta C + alpha mask_{P_C}(A.B) with every FP64 operand value split into three BF16
+// terms x ~ x0 + x1 + x2 (about 26 bits; see split3) and the product formed as the six
+// cross products A_p B_q with p + q <= 2, accumulated in FP32 in tensor memory.  Every
+// DRAIN chunks the FP32 accumulator is drained into a per-thread double-float (hi, lo)
+// sum, so FP32 rounding only acts within a drain period; the result is written back in
+// FP64.
 //
 // Local densification.  9x9 blocks do not fit MMA shapes, so atoms are grouped in space
 // (Morton order): an M group holds floor(128/nb) atoms (126 rows for nb = 9), an N group
@@ -95,17 +95,31 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                            ((uint32_t)(MT >> 4) << 24);
 
-// x rounded once to FP32 (24 significand bits, what three BF16 terms can hold), then split
-// in FP32: b0 = bf16(f), b1 = bf16(f - b0), b2 = bf16(f - b0 - b1); both differences are
-// exact in FP32.  One FP64 operation per value (the FP64 pipe is the scarce unit here).
+// Three-term BF16 split of an FP64 value without FP64 instructions (the FP64 pipe is the
+// scarce unit on this GPU): the double's bits give an FP32 head h (its significand cut to
+// 24 bits) and an FP32 tail l (the 29 bits cut off, rounded to 24), x = h + l; then
+// b0 = bf16(h), b1 = bf16(h - b0), b2 = bf16((h - b0 - b1) + l), the first two differences
+// exact in FP32.  |x - (b0 + b1 + b2)| is about 2^-26 |x|.  Zeros, subnormals and values
+// below the FP32 normal range give zero terms; the operands here are far inside the range.
 __device__ __forceinline__ void split3(double x, __nv_bfloat16 &b0, __nv_bfloat16 &b1,
                                        __nv_bfloat16 &b2)
 {
-    const float f = (float)x;
-    b0 = __float2bfloat16_rn(f);
-    const float r1 = f - __bfloat162float(b0);
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((u >> 52) & 0x7FF) - 1023 + 127;  // FP32 exponent field
+    const unsigned long long m = u & ((1ull << 52) - 1);
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    float h = 0.f, l = 0.f;
+    if (e >= 1 && e <= 254) {
+        h = __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)(m >> 29));
+        if (e > 52) {  // the tail's scale 2^(exponent - 52) is a normal FP32 number
+            l = (float)(unsigned)(m & ((1u << 29) - 1)) * __uint_as_float((unsigned)(e - 52) << 23);
+            if (sign) l = -l;
+        }
+    }
+    b0 = __float2bfloat16_rn(h);
+    const float r1 = h - __bfloat162float(b0);
     b1 = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(b1);
+    const float r2 = (r1 - __bfloat162float(b1)) + l;
     b2 = __float2bfloat16_rn(r2);
 }
 
