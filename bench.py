@@ -94,6 +94,11 @@ def parse():
                     help="skip the FP64 leg (profiling the tensor-core path)")
     ap.add_argument("--hotelling-steps", type=int, default=12)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--sweep", default=None,
+                    help="comma-separated cells per edge (e.g. 4,6,8,10,12): seconds per LNV step "
+                         "against atom count (linear scaling), split-BF16 at every size, FP64 "
+                         "up to --sweep-fp64-max cells per edge")
+    ap.add_argument("--sweep-fp64-max", type=int, default=8)
     ap.add_argument("--converge", action="store_true",
                     help="time full minimisations (plain FP64 vs learned guess + split-BF16 + "
                          "FP64 refinement) instead of the step benchmark")
@@ -652,8 +657,75 @@ def run_converge(args, dev):
     ctx.close()
 
 
+def run_sweep(args, dev):
+    """Seconds per LNV step against the number of atoms, one GPU: for each cell size the
+    patterns, Hotelling inverse and PM start are built (untimed), the LNV object takes two
+    untimed steps, then one step is timed with CUDA events.  Split-BF16 at every size; FP64
+    up to --sweep-fp64-max cells per edge (its step is ~7x longer)."""
+    import torch
+
+    from paper_2205_08941_gb300 import build as B
+    B.build()
+    from paper_2205_08941_gb300 import cq
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    t = lambda a, dt: torch.tensor(a, dtype=dt, device=f"cuda:{dev}")
+    rows = []
+    for ncell in [int(x) for x in args.sweep.split(",")]:
+        cell, Spb, Hpb = make_inputs(ncell)
+        n_e = 4.0 * cell.n_atoms
+        precs = [("split", cq.CQ_SPLIT_BF16X3)]
+        if ncell <= args.sweep_fp64_max:
+            precs.append(("fp64", cq.CQ_FP64))
+        row = {"ncell": ncell, "n_atoms": cell.n_atoms}
+        for name, prec in precs:
+            ctx = cq.Context(dev)
+            pos, nb = t(cell.pos, torch.float64), t(cell.nb, torch.int32)
+            pS = ctx.pattern(pos, cell.box, nb, WORKLOAD["r_S"])
+            pL = ctx.pattern(pos, cell.box, nb, WORKLOAD["r_L"])
+            up = lambda p, pb: ctx.scatter(p, t(pb.i, torch.int32), t(pb.j, torch.int32),
+                                           t(pb.off, torch.int64), t(pb.values, torch.float64))
+            S, H = up(pS, Spb), up(pS, Hpb)
+            T = ctx.zeros(pL)
+            ctx.hotelling_init(pS, S, pL, T)
+            for _ in range(args.hotelling_steps):
+                ctx.hotelling_step(pS, S, pL, T)
+            L = ctx.zeros(pL)
+            ctx.pm_guess(pS, S, H, pL, T, pL, L, n_e / 2.0)
+            del T
+            lnv = ctx.lnv(pS, S, H, pL, L, n_e, prec=prec)
+            for _ in range(2):
+                lnv.step()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            rep = lnv.step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            row[name] = {"s_per_step": ms / 1e3, "gflops": rep["flops"] / (ms * 1e-3) / 1e9,
+                         "tflop_per_step": rep["flops"] / 1e12, "n_products": rep["n_products"],
+                         "energy_per_atom": rep["energy"] / cell.n_atoms,
+                         "gnorm": rep["gnorm"]}
+            lnv.close()
+            ctx.close()
+            del S, H, L
+            torch.cuda.empty_cache()
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    base = rows[0]
+    for r in rows:
+        r["split_s_per_step_per_atom_rel"] = ((r["split"]["s_per_step"] / r["n_atoms"]) /
+                                              (base["split"]["s_per_step"] / base["n_atoms"]))
+    print(json.dumps({"mode": "sweep", "workload": "Si diamond SZP, a = 10.26 bohr, sigma 0.1, "
+                      "r_S 14, r_L 16", "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
+    if args.sweep:
+        run_sweep(args, int(os.environ.get("LOCAL_RANK", 0)))
+        return
     if args.converge:
         run_converge(args, int(os.environ.get("LOCAL_RANK", 0)))
         return
