@@ -59,8 +59,58 @@ k_bsmm_f64_uniform(int64_t n_items, const int64_t *__restrict__ seg,
     }
 }
 
+// One C row of the mixed-basis product with NJ columns: the Q lanes of the row's group take
+// tasks q, q + Q, ..., keep NJ partial sums and combine them with a fixed xor tree over the
+// group (gmask: the group's lanes, so that groups of different widths may branch apart).
+// NJ == CQ_MAX_NB is the catch-all for widths without their own instance (nj_rt columns).
+template <int NJ, int Q>
+__device__ __forceinline__ void generic_row(unsigned gmask, int q, int64_t c, int r, int ni,
+                                            int nj_rt, const int64_t *__restrict__ seg,
+                                            const int2 *__restrict__ tasks,
+                                            const int32_t *__restrict__ nb,
+                                            const int32_t *__restrict__ a_col,
+                                            const int64_t *__restrict__ a_off,
+                                            const int64_t *__restrict__ b_off,
+                                            const int64_t *__restrict__ c_off,
+                                            const double *__restrict__ A,
+                                            const double *__restrict__ B, double *__restrict__ C,
+                                            double alpha, double beta)
+{
+    constexpr bool ANY = NJ == CQ_MAX_NB;
+    const int nj = ANY ? nj_rt : NJ;
+    double acc[NJ];
+#pragma unroll
+    for (int x = 0; x < NJ; ++x) acc[x] = 0.0;
+    const int64_t t1 = seg[c + 1];
+    for (int64_t t = seg[c] + q; t < t1; t += Q) {
+        const int2 tk = __ldg(&tasks[t]);
+        const int nk = nb[a_col[tk.x]];
+        const double *a = A + a_off[tk.x] + (int64_t)r * nk;
+        const double *b = B + b_off[tk.y];
+        for (int m = 0; m < nk; ++m) {
+            const double av = __ldg(a + m);
+#pragma unroll
+            for (int x = 0; x < NJ; ++x)
+                if (!ANY || x < nj) acc[x] = fma(av, __ldg(b + m * nj + x), acc[x]);
+        }
+    }
+#pragma unroll
+    for (int o = Q >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int x = 0; x < NJ; ++x) acc[x] += __shfl_xor_sync(gmask, acc[x], o);
+    if (q == 0 && r < ni) {
+        double *cp = C + c_off[c] + (int64_t)r * nj;
+#pragma unroll
+        for (int x = 0; x < NJ; ++x)
+            if (!ANY || x < nj)
+                cp[x] = (beta == 0.0) ? alpha * acc[x] : beta * cp[x] + alpha * acc[x];
+    }
+}
+
 // Mixed orbital counts (1..16 per atom): item -> C block by binary search over the prefix
-// of block row counts; block offsets from the patterns' val_off.
+// of block row counts; block offsets from the patterns' val_off.  The row's column count
+// selects an instance with exactly that many accumulators (4, 5, 9, 13: the bases of the
+// mixed-species cells), so no FMA slot or shuffle is spent on absent columns.
 template <int Q>
 __global__ void __launch_bounds__(256)
 k_bsmm_f64_generic(int64_t n_items, int64_t n_c, const int64_t *__restrict__ rowitem,
@@ -75,51 +125,31 @@ k_bsmm_f64_generic(int64_t n_items, int64_t n_c, const int64_t *__restrict__ row
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t item = gt / Q;
     const int q = (int)(gt % Q);
-    const bool active = item < n_items;
-    int64_t c = 0;
-    int r = 0, nj = 0, ni = 0;
-    if (active) {
-        int64_t lo = 0, hi = n_c;  // largest c with rowitem[c] <= item
-        while (hi - lo > 1) {
-            int64_t mid = (lo + hi) >> 1;
-            if (rowitem[mid] <= item)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        c = lo;
-        r = (int)(item - rowitem[c]);
-        ni = nb[c_row[c]];
-        nj = nb[c_col[c]];
+    if (item >= n_items) return;  // whole Q groups leave together (blockDim is a multiple of Q)
+    int64_t lo = 0, hi = n_c;     // largest c with rowitem[c] <= item
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (rowitem[mid] <= item)
+            lo = mid;
+        else
+            hi = mid;
     }
-    double acc[CQ_MAX_NB];
-#pragma unroll
-    for (int x = 0; x < CQ_MAX_NB; ++x) acc[x] = 0.0;
-    if (active) {
-        const int64_t t1 = seg[c + 1];
-        for (int64_t t = seg[c] + q; t < t1; t += Q) {
-            const int2 tk = __ldg(&tasks[t]);
-            const int nk = nb[a_col[tk.x]];
-            const double *a = A + a_off[tk.x] + (int64_t)r * nk;
-            const double *b = B + b_off[tk.y];
-            for (int m = 0; m < nk; ++m) {
-                const double av = __ldg(a + m);
-#pragma unroll
-                for (int x = 0; x < CQ_MAX_NB; ++x)
-                    if (x < nj) acc[x] = fma(av, __ldg(b + m * nj + x), acc[x]);
-            }
-        }
+    const int64_t c = lo;
+    const int r = (int)(item - rowitem[c]);
+    const int ni = nb[c_row[c]], nj = nb[c_col[c]];
+    const unsigned gmask =
+        Q == 32 ? 0xffffffffu : (((1u << Q) - 1u) << ((threadIdx.x & 31) & ~(Q - 1)));
+#define CQ_ROW(NJ)                                                                           \
+    generic_row<NJ, Q>(gmask, q, c, r, ni, nj, seg, tasks, nb, a_col, a_off, b_off, c_off, A, \
+                       B, C, alpha, beta)
+    switch (nj) {
+    case 4: CQ_ROW(4); break;
+    case 5: CQ_ROW(5); break;
+    case 9: CQ_ROW(9); break;
+    case 13: CQ_ROW(13); break;
+    default: CQ_ROW(CQ_MAX_NB); break;
     }
-#pragma unroll
-    for (int o = Q >> 1; o > 0; o >>= 1)
-#pragma unroll
-        for (int x = 0; x < CQ_MAX_NB; ++x) acc[x] += __shfl_xor_sync(0xffffffffu, acc[x], o);
-    if (active && q == 0 && r < ni) {
-        double *cp = C + c_off[c] + (int64_t)r * nj;
-#pragma unroll
-        for (int x = 0; x < CQ_MAX_NB; ++x)
-            if (x < nj) cp[x] = (beta == 0.0) ? alpha * acc[x] : beta * cp[x] + alpha * acc[x];
-    }
+#undef CQ_ROW
 }
 
 int pick_q(const TaskList *tl)
