@@ -498,6 +498,47 @@ def run_cq(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------- convergence criteria
+
+def run_until(lnv, gtol, cap, trace=None, t0=0.0, fp64=True, stall=None):
+    """LNV steps until the RMS gradient is <= gtol (at most cap steps), or, with stall, until
+    it has fallen by less than the factor stall over two steps -- split-BF16 gradients stop
+    improving near their rounding floor (about 1e-6 RMS on the 4096-atom cell).  trace gets
+    (seconds since t0, energy, RMS gradient, whether the step's products were FP64) per
+    step.  Returns (steps, last report)."""
+    it, st = 0, lnv.state()
+    hist = [st["gnorm"]]
+    while st["gnorm"] > gtol and it < cap:
+        st = lnv.step()
+        it += 1
+        hist.append(st["gnorm"])
+        if trace is not None:
+            trace.append((time.perf_counter() - t0, st["energy"], st["gnorm"], fp64))
+        if stall is not None and len(hist) >= 3 and hist[-1] > stall * hist[-3]:
+            break
+    return it, st
+
+
+def settled(trace, e_ref, tol):
+    """Seconds until every later FP64-product energy of the trace stays within tol of e_ref
+    (split-product energies carry the split's bias and do not count); None if never."""
+    fp = [x for x in trace if x[3]]
+    for k in range(len(fp)):
+        if all(abs(y[1] - e_ref) <= tol for y in fp[k:]):
+            return fp[k][0]
+    return None
+
+
+def de_stop(trace, tol):
+    """The intrinsic stop rule: the first FP64 step whose energy differs from the previous
+    FP64 step's by less than tol, as (seconds, energy); (None, None) if none."""
+    fp = [x for x in trace if x[3]]
+    for k in range(1, len(fp)):
+        if abs(fp[k][1] - fp[k - 1][1]) < tol:
+            return fp[k][0], fp[k][1]
+    return None, None
+
+
 def run_converge(args, dev):
     """Full minimisations on the 4096-atom cell, both to RMS gradient 1e-8:
     (a) plain: PM start, FP64 LNV;
@@ -535,38 +576,7 @@ def run_converge(args, dev):
         return float(torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref))
 
     def run(lnv, gtol, cap, trace=None, t0=0.0, fp64=True, stall=None):
-        """Steps until the RMS gradient is <= gtol, or (with stall) until it has fallen by
-        less than the factor stall over two steps -- split-BF16 gradients stop improving
-        near their rounding floor (about 1e-6 RMS here); trace gets (seconds since t0,
-        energy, RMS gradient, whether the step's products were FP64) per step."""
-        it, st = 0, lnv.state()
-        hist = [st["gnorm"]]
-        while st["gnorm"] > gtol and it < cap:
-            st = lnv.step()
-            it += 1
-            hist.append(st["gnorm"])
-            if trace is not None:
-                trace.append((time.perf_counter() - t0, st["energy"], st["gnorm"], fp64))
-            if stall is not None and len(hist) >= 3 and hist[-1] > stall * hist[-3]:
-                break
-        return it, st
-
-    def settled(trace, e_ref, tol):
-        """Seconds until every later FP64-product energy stays within tol of e_ref."""
-        fp = [x for x in trace if x[3]]
-        for k in range(len(fp)):
-            if all(abs(y[1] - e_ref) <= tol for y in fp[k:]):
-                return fp[k][0]
-        return None
-
-    def de_stop(trace, tol):
-        """First FP64 step whose energy change from the previous FP64 step is below tol:
-        (seconds, energy)."""
-        fp = [x for x in trace if x[3]]
-        for k in range(1, len(fp)):
-            if abs(fp[k][1] - fp[k - 1][1]) < tol:
-                return fp[k][0], fp[k][1]
-        return None, None
+        return run_until(lnv, gtol, cap, trace, t0, fp64, stall)
 
     # training set: converged L of small thermally displaced cells
     t0 = time.perf_counter()

@@ -1,0 +1,78 @@
+"""The convergence criteria the full-minimisation benchmark reports (CPU, no GPU).
+
+The benchmark times two solvers to the same targets: the energy settled within a tolerance
+of the converged FP64 energy (counted on FP64-product energies only, since split-product
+energies carry the split's bias), the first FP64 step whose energy change falls below a
+tolerance, and the switch out of the split phase when its gradient stops improving.
+These tests drive the criteria with synthetic traces and a scripted solver.
+"""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_settled_ignores_split_energies_and_waits_for_the_last_excursion():
+    e_ref, tol = -100.0, 1e-3
+    trace = [(1.0, -100.0, 1e-3, False),      # split energy inside tol: not counted
+             (2.0, -99.9, 1e-4, True),         # FP64, outside
+             (3.0, -100.0005, 1e-5, True),     # inside ...
+             (4.0, -99.99, 1e-6, True),        # ... but leaves again
+             (5.0, -100.0002, 1e-7, True),
+             (6.0, -99.9999, 1e-8, True)]
+    assert bench.settled(trace, e_ref, tol) == 5.0
+    assert bench.settled(trace[:2], e_ref, tol) is None
+
+
+def test_de_stop_compares_consecutive_fp64_energies_only():
+    trace = [(1.0, -10.0, 0, False), (2.0, -10.5, 0, True), (3.0, -10.50000001, 0, False),
+             (4.0, -10.6, 0, True), (5.0, -10.6000005, 0, True)]
+    # the split energy at t=3 sits next to the FP64 one at t=2 but must not stop the run
+    assert bench.de_stop(trace, 1e-6) == (5.0, -10.6000005)
+    assert bench.de_stop(trace[:4], 1e-6) == (None, None)
+
+
+class ScriptedLnv:
+    """Stands in for the LNV object: each step returns the next scripted RMS gradient."""
+
+    def __init__(self, gnorms):
+        self.g = list(gnorms)
+        self.k = 0
+
+    def state(self):
+        return {"gnorm": self.g[0], "energy": 0.0}
+
+    def step(self):
+        self.k += 1
+        return {"gnorm": self.g[self.k], "energy": -float(self.k)}
+
+
+def test_run_until_stops_at_the_gradient_target():
+    lnv = ScriptedLnv([1e-2, 5e-3, 1e-3, 5e-4, 1e-4])
+    it, st = bench.run_until(lnv, 6e-4, 50)
+    assert it == 3 and st["gnorm"] == 5e-4
+
+
+def test_run_until_leaves_a_stalled_split_phase():
+    # falls by 10x per step, then sits at a floor of 1.05e-6 above the 1e-6 target
+    g = [1e-3, 1e-4, 1e-5, 1.2e-6, 1.06e-6, 1.05e-6, 1.05e-6, 1.05e-6]
+    trace = []
+    it, st = bench.run_until(ScriptedLnv(g), 1e-6, 50, trace, 0.0, fp64=False, stall=0.9)
+    # step 5 (1.05e-6) still fell by more than 10% against step 3 (1.2e-6); step 6
+    # (1.05e-6) did not against step 4 (1.06e-6), so the phase ends there
+    assert it == 6 and st["gnorm"] == 1.05e-6
+    assert len(trace) == 6 and not any(x[3] for x in trace)
+    # without the stall rule the same run only ends at the step cap
+    it, _ = bench.run_until(ScriptedLnv(g + [1.05e-6] * 10), 1e-6, 12)
+    assert it == 12
+
+
+@pytest.mark.parametrize("n", [1, 2])
+def test_run_until_needs_two_steps_before_judging_a_stall(n):
+    g = [1e-3] + [1e-3] * 4
+    it, _ = bench.run_until(ScriptedLnv(g), 1e-9, n, stall=0.9)
+    assert it == n
