@@ -159,7 +159,11 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  * P_B (the sparse matrix multiplication of the paper's Background and Exascale sections).
  * With beta == 0 the old C is not read.  The (i, k, j) task list of each (P_A, P_B, P_C)
  * triple is built on the device on first use and cached in the context.  C must not alias
- * A or B.  prec selects FP64 FMAs or the split-BF16 tensor-core product.  The call is
+ * A or B.  prec selects FP64 FMAs or the split-BF16 tensor-core product.  The split product
+ * needs a uniform basis of 4 or 9 orbitals per atom (else CQ_ERR_INVALID); it packs both
+ * operands into context-owned scratch panels before every call (about 2x the FP64 size of
+ * the operands, the A side in batches of at most 12 GB), and its accuracy is FP32-class:
+ * about 1e-7 relative per block, with FP32 partial sums drained to double-float.  The call is
  * asynchronous on the context stream; if a bounded wait inside the split kernel ran out (a
  * tensor-core completion not seen within about two seconds), the next synchronising call on
  * the context (cq_ctx_sync, a trace, a dot, an LNV or Hotelling step) returns
