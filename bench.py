@@ -99,6 +99,10 @@ def parse():
                          "against atom count (linear scaling), split-BF16 at every size, FP64 "
                          "up to --sweep-fp64-max cells per edge")
     ap.add_argument("--sweep-fp64-max", type=int, default=8)
+    ap.add_argument("--apply-only", action="store_true",
+                    help="with --converge: only the learned start and its split-BF16 phase on "
+                         "the cell (no plain FP64 solve, no FP64 refinement), for cells whose "
+                         "FP64 solve is too long for the bench")
     ap.add_argument("--converge", action="store_true",
                     help="time full minimisations (plain FP64 vs learned guess + split-BF16 + "
                          "FP64 refinement) instead of the step benchmark")
@@ -605,6 +609,31 @@ def run_converge(args, dev):
     cell, Spb, Hpb = make_inputs(args.ncell)
     n_e = 4.0 * cell.n_atoms
     pS, pL, S, H, T = setup(cell, Spb, Hpb, args.hotelling_steps)
+    if args.apply_only:
+        # the network trained on 216-atom cells applied to this cell, then split-BF16 steps
+        L2 = ctx.zeros(pL)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lnv, used, info = learned.guarded_start(ctx, guess, pS, S, H, pL, T, pL, L2, n_e,
+                                                prec=cq.CQ_SPLIT_BF16X3)
+        torch.cuda.synchronize()
+        t_start = time.perf_counter() - t0
+        tr = []
+        it, st = run(lnv, 1e-6, 120, tr, t0, fp64=False, stall=0.9)
+        torch.cuda.synchronize()
+        t_all = time.perf_counter() - t0
+        lnv.close()
+        print(json.dumps({
+            "mode": "learned_apply", "workload": workload_name(cell.n_atoms),
+            "n_atoms": cell.n_atoms, "learned_start_used": used, "start": info,
+            "start_seconds": t_start, "split_steps": it, "split_seconds": t_all - t_start,
+            "gnorm": st["gnorm"], "energy_per_atom": st["energy"] / cell.n_atoms,
+            "gnorm_trace": [x[2] for x in tr],
+            "training": {"cells": 6, "atoms_per_cell": 216, "samples": n_samples,
+                         "seconds": t_train}}), flush=True)
+        guess.close()
+        ctx.close()
+        return
     # (a) plain FP64 from the PM start
     L = ctx.zeros(pL)
     torch.cuda.synchronize()
