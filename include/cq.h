@@ -28,6 +28,9 @@
  *  call.  Scratch (task lists, intermediate products) belongs to the context or the LNV
  *  object; nothing returned needs to be freed by the caller.
  *
+ *  Devices: calls on a context expect its device to be the current CUDA device (the one
+ *  passed to cq_ctx_create), as with other CUDA libraries; the library does not switch.
+ *
  *  Streams: all device work is enqueued on the stream given to cq_ctx_create, in order.
  *  Calls returning host scalars synchronise that stream.
  *

@@ -715,11 +715,21 @@ cq_status run_split(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double a
     void *va, *vb;
     if ((st = cq_scratch(ctx, "split_A", a_bytes, &va)) != CQ_OK) return st;
     if ((st = cq_scratch(ctx, "split_B", (size_t)pl->n_hb * B_CHUNK, &vb)) != CQ_OK) return st;
-    static bool attr_set = false;  // once per process (outside any graph capture)
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_bsmm_split<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        cudaFuncSetAttribute(k_bsmm_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        attr_set = true;
+    // the shared-memory limit is a per-device attribute: set it once per device, on the
+    // first split product there (which runs eagerly: building its plan synchronises)
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cq_fail(ctx, CQ_ERR_INVALID, "split product: device index");
+    if (!attr_set[dev]) {
+        if ((st = cq_check_cuda(ctx, cudaFuncSetAttribute(k_bsmm_split<9>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          SMEM), "split attribute")) != CQ_OK ||
+            (st = cq_check_cuda(ctx, cudaFuncSetAttribute(k_bsmm_split<4>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          SMEM), "split attribute")) != CQ_OK)
+            return st;
+        attr_set[dev] = true;
     }
     if (pl->n_hb > 0) {
         k_pack_b<NB><<<(unsigned)pl->n_hb, 256, 0, s>>>(pl->hb_index.as<int32_t>(), B,
