@@ -3,8 +3,9 @@ FP32 accumulation drained into double-float sums) against the FP64 oracle.
 
 Error model per product term a*b: operand truncation after three terms and the dropped
 cross terms (A1B2, A2B1, A2B2) give at most ~4 * 2^-24 |a||b| (2.4e-7); FP32 accumulation
-over one drain period (4 chunks = 96 tensor-core accumulations) adds at most
-96 * 2^-24 (5.7e-6) of the summed magnitudes.  The per-block bound tested is therefore
+over one drain period (4 chunks of 3 K steps = 12 accumulations per split product into
+the tensor-memory accumulator, 72 in all) adds at most 72 * 2^-24 (4.3e-6) of the summed
+magnitudes.  The per-block bound tested is therefore
 ||dC_ij||_F <= 1e-5 * sum_k ||A_ik||_F ||B_kj||_F, and the typical (RMS) error is checked at
 1e-6 of the same scale.
 """
