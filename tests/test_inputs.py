@@ -64,3 +64,18 @@ def test_random_blocks_symmetric_and_seeded():
     assert np.array_equal(a.values, b.values)
     d = I.dense_from_pairs(cell, a)
     assert np.array_equal(d, d.T)
+
+
+@pytest.mark.parametrize("ncell,sigma,seed,ranges", [
+    (2, 0.05, 1, (10.0, 12.0, 22.0, 32.0)),          # the 64-atom cell
+    (8, 0.10, 2, (14.0, 16.0, 30.0, 44.0)),          # the 4096-atom benchmark cell
+])
+def test_no_pair_sits_on_a_cutoff(ncell, sigma, seed, ranges):
+    """Pattern membership d^2 < R^2 must not hinge on rounding: no minimum-image pair
+    distance of the seeded cells lies within 1e-9 bohr of a cutoff they are used with."""
+    from scipy.spatial import cKDTree
+    cell = I.diamond_cell(ncell, a=10.26, sigma=sigma, seed=seed, norb=9)
+    tree = cKDTree(cell.pos % cell.box, boxsize=cell.box)
+    d = tree.sparse_distance_matrix(tree, max(ranges) + 1.0, output_type="ndarray")["v"]
+    for R in ranges:
+        assert np.abs(d - R).min() > 1e-9, R
