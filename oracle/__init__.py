@@ -373,10 +373,29 @@ class LNV:
         self.max_corr = max_corr
         self.G_prev = None
         self.D_prev = None
+        self.Z_prev = None
         self.alpha_prev = None
+        self.precond = None
         self.history = []
         self.evaluate()
         self.n_corrections_initial = self.correct_n()
+
+    def set_preconditioner(self, pT, T, pTL):
+        """Search directions from Z = sym(mask_L(T G T)) in place of G, with T ~ S^-1 from
+        Hotelling on P_T (the covariant gradient raised with the inverse overlap, the
+        tensorially consistent steepest-descent direction in a non-orthogonal basis).  T G
+        lands on pTL, which must reach r_T + r_L.  Resets the search history."""
+        self.precond = (pT, np.array(T, dtype=np.float64), pTL)
+        self.G_prev = self.D_prev = self.Z_prev = self.alpha_prev = None
+
+    def direction_of(self, G):
+        """G itself, or with a preconditioner Z = (mask_L(T G T) + its transpose) / 2."""
+        if self.precond is None:
+            return G
+        pT, T, pTL = self.precond
+        TG = bsmm(1.0, pT, T, self.pL, G, 0.0, pTL)
+        Z = bsmm(1.0, pTL, TG, pT, T, 0.0, self.pL)
+        return 0.5 * (Z + gather(self.pL, Z, self.pL, transpose=True))
 
     # E and N from the five products that a trial point needs
     def energy_number(self, L):
@@ -425,18 +444,20 @@ class LNV:
         GN = self.GN
         gn2 = dot(GN, GN)
         mu, G = self.mu_and_g()
+        Zg = self.direction_of(G)  # G itself unless a preconditioner is set
         restart = self.G_prev is None
         if restart:
-            D = -G
+            D = -Zg
         else:
-            beta = max(0.0, dot(G, G - self.G_prev) / dot(self.G_prev, self.G_prev))
-            D = -G + beta * self.D_prev
+            # Polak-Ribiere in the preconditioned form <G, Z - Z_prev> / <G_prev, Z_prev>
+            beta = max(0.0, dot(G, Zg - self.Z_prev) / dot(self.G_prev, self.Z_prev))
+            D = -Zg + beta * self.D_prev
         D = D - (dot(D, GN) / gn2) * GN
         if dot(G, D) >= 0.0:
-            D = -G
+            D = -Zg
             restart = True
         if self.alpha_prev is None:
-            a1 = 0.1 * math.sqrt(G.shape[0]) / math.sqrt(dot(G, G))
+            a1 = 0.1 * math.sqrt(G.shape[0]) / math.sqrt(dot(Zg, Zg))
         else:
             a1 = self.alpha_prev
         a2 = 2.0 * a1
@@ -454,7 +475,7 @@ class LNV:
         self.L = self.L + alpha * D
         self.evaluate()
         ncorr = self.correct_n()
-        self.G_prev, self.D_prev, self.alpha_prev = G, D, alpha
+        self.G_prev, self.D_prev, self.Z_prev, self.alpha_prev = G, D, Zg, alpha
         mu_new, G_new = self.mu_and_g()
         rec = {"E": self.E, "N": self.N, "mu": mu_new,
                "gnorm": math.sqrt(dot(G_new, G_new) / G_new.shape[0]),

@@ -327,3 +327,58 @@ def test_fallback_step_is_bounded_by_the_rms_change_of_L():
     assert np.sqrt(np.mean((a * D) ** 2)) == pytest.approx(0.01, rel=1e-12)
     small = 1e-6                                      # 2 a2 below the cap is kept
     assert O.fallback_alpha(small, D.size, dd) == 2.0 * small
+
+
+# ------------------------------------------------------------------ preconditioned LNV
+
+def _c1_start(c1):
+    cell, pS, pL, pX, pU, S, H = _lnv_setup(c1)
+    T = O.hotelling_init(pS, S, pL)
+    for _ in range(12):
+        T, _ = O.hotelling_step(pS, S, pL, T, pX)
+    L0 = O.pm_guess(pS, S, H, pL, T, pX, pL, 128.0)
+    return cell, pS, pL, pX, pU, S, H, T, L0
+
+
+def _steps_to(lnv, tol=1e-8, cap=80):
+    k = 0
+    while lnv.gnorm_rms() > tol and k < cap:
+        lnv.step()
+        k += 1
+    return k
+
+
+def test_identity_preconditioner_reproduces_plain_steps(c1):
+    cell, pS, pL, pX, pU, S, H, T, L0 = _c1_start(c1)
+    plain = O.LNV(pS, S, H, pL, L0, 256.0, pX, pU)
+    pre = O.LNV(pS, S, H, pL, L0, 256.0, pX, pU)
+    pre.set_preconditioner(pL, O.identity(pL), O.Pattern.of_cell(cell, 24.0))
+    for k in range(6):
+        a, b = plain.step(), pre.step()
+        assert b["E"] == pytest.approx(a["E"], abs=1e-10 * 64), k
+        assert b["alpha"] == pytest.approx(a["alpha"], rel=1e-8), k
+        assert (b["restart"], b["fallback"], b["n_corr"]) == (a["restart"], a["fallback"],
+                                                              a["n_corr"]), k
+
+
+def test_inverse_overlap_preconditioner_converges_in_fewer_steps(c1):
+    cell, pS, pL, pX, pU, S, H, T, L0 = _c1_start(c1)
+    plain = O.LNV(pS, S, H, pL, L0, 256.0, pX, pU)
+    pre = O.LNV(pS, S, H, pL, L0, 256.0, pX, pU)
+    pre.set_preconditioner(pL, T, O.Pattern.of_cell(cell, 24.0))
+    n_plain, n_pre = _steps_to(plain), _steps_to(pre)
+    assert pre.gnorm_rms() <= 1e-8 and plain.gnorm_rms() <= 1e-8
+    assert n_pre < n_plain                      # 21 against 28 on this cell
+    assert pre.E == pytest.approx(plain.E, abs=1e-10 * 64)
+    assert abs(pre.N - 256.0) < 1e-8
+
+
+def test_preconditioned_dense_limit_is_the_band_energy(c1):
+    cell, pS, pD, S, H = _dense_setup(c1)
+    T = O.from_dense(pD, np.linalg.inv(O.to_dense(pS, S)))
+    L0 = O.pm_guess(pS, S, H, pD, T, pD, pD, 128.0)
+    lnv = O.LNV(pS, S, H, pD, L0, 256.0, pD, pD)
+    lnv.set_preconditioner(pD, T, pD)
+    _steps_to(lnv, 1e-9, 60)
+    e = sl.eigh(O.to_dense(pS, H), O.to_dense(pS, S), eigvals_only=True)
+    assert lnv.E == pytest.approx(2.0 * e[:128].sum(), abs=1e-8)
