@@ -1,8 +1,8 @@
 /*
  * Oracle: plain, slow CPU FP64 restatement of the atom-blocked sparse-matrix operations of a
- * linear-scaling density-matrix solver (the paper's Background: "sparse matrix storage and
- * operations to ensure locality"; Development Priorities: "linear scaling optimisation of the
- * density matrix", "linear scaling inversion of the overlap matrix").
+ * linear-scaling density-matrix solver (Background: sparse storage keeps every operation
+ * local; Development Priorities: density-matrix minimisation and overlap inversion, both in
+ * linear-scaling time).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links or calls this file; it is
  * used by tests/, by __graft_entry__.smoke() and by bench.py's CPU-baseline leg.  It shares
