@@ -3,10 +3,10 @@
  *
  * The paper (Bowler, Miyazaki, Nakata, Truflandier, "The CONQUEST code: large scale and
  * linear scaling DFT") states the method in words: a linear-scaling ground-state solver
- * built on "sparse matrix storage and operations to ensure locality" (Background), driven
- * by "linear scaling optimisation of the density matrix" with a "linear scaling inversion of
- * the overlap matrix" (Development Priorities), whose first GPU kernel is the sparse matrix
- * multiplication (Meeting the Exascale Challenges).  The calls below expose exactly that hot
+ * that keeps its matrices sparse so every operation stays local (Background), minimises
+ * the energy over the density matrix and inverts the overlap, both in linear-scaling time
+ * (Development Priorities), and names the sparse matrix product as the first kernel to move
+ * to GPUs (Meeting the Exascale Challenges).  The calls below expose exactly that hot
  * path: range-cutoff patterns, the atom-blocked product kept on C's pattern, traces, the
  * Hotelling inversion step T <- 2T - TST, the Li-Nunes-Vanderbilt (LNV) density-matrix step
  * with K = 3LSL - 2LSLSL, its Palser-Manolopoulos start and McWeeny purification.
@@ -297,9 +297,22 @@ int32_t cq_lnv_cells(const cq_lnv *lnv);
  * precision (with electron-number corrections) so the next step starts from consistent
  * values; the search history is reset.  Synchronises. */
 cq_status cq_lnv_set_precision(cq_lnv *lnv, cq_precision prec);
+/* Precondition the search directions of later steps (Development Priorities: the overlap
+ * inversion feeding the density-matrix optimisation; T applied on both sides of the
+ * covariant gradient gives the contravariant direction).  pT, T: an approximate S^-1 on
+ * its own range-cutoff pattern (e.g. from cq_hotelling), device values in pT's layout; same
+ * atoms and basis as the LNV patterns.  Each step then forms Z = sym(mask_L(T G T)) with
+ * two more products (T G on the pattern of range r_T + r_L, owned by the context) and uses
+ * Z where the plain step uses G: D = -Z + beta D_prev with
+ * beta = max(0, <G, Z - Z_prev> / <G_prev, Z_prev>), restarts to -Z, and the first trial
+ * step 0.1 sqrt(n) / ||Z||.  With T = identity the steps are those of the plain gradient.
+ * T is copied (the caller keeps its buffer); pT must outlive the preconditioner.  T = NULL
+ * or pT = NULL switches it off.  The search history is reset either way.  Synchronises. */
+cq_status cq_lnv_set_preconditioner(cq_lnv *lnv, const cq_pattern *pT, const double *T);
 /* Current E, N, mu and RMS gradient (as after the last evaluation), one report per cell. */
 cq_status cq_lnv_state(const cq_lnv *lnv, cq_lnv_report *report_host);
-/* Useful flops of one LNV step's products (full evaluation + two trial points). */
+/* Useful flops of one LNV step's products (full evaluation + two trial points, plus the two
+ * preconditioner products when one is set). */
 cq_status cq_lnv_step_flops(cq_lnv *lnv, double *flops_host);
 void cq_lnv_destroy(cq_lnv *lnv);
 

@@ -71,6 +71,7 @@ SIGNATURES = {
                             ctypes.POINTER(_vp)]),
     "cq_lnv_step": (_st, [_vp, _vp]),
     "cq_lnv_set_precision": (_st, [_vp, ctypes.c_int]),
+    "cq_lnv_set_preconditioner": (_st, [_vp, _vp, _vp]),
     "cq_lnv_state": (_st, [_vp, _vp]),
     "cq_lnv_step_flops": (_st, [_vp, ctypes.POINTER(_d)]),
     "cq_lnv_destroy": (None, [_vp]),
@@ -390,6 +391,14 @@ class Lnv:
 
     def set_precision(self, prec: int):
         self.ctx._check(lib().cq_lnv_set_precision(self.h, int(prec)))
+
+    def set_preconditioner(self, pT=None, T=None):
+        """Precondition later search directions with T (an approximate S^-1 on pT, e.g. from
+        hotelling()); None switches back to the plain gradient.  T is copied; pT must stay
+        alive while the preconditioner is set."""
+        self._keep_T = pT
+        self.ctx._check(lib().cq_lnv_set_preconditioner(
+            self.h, pT.h if pT is not None else None, _ptr(T) if T is not None else None))
 
     def state(self):
         return self._reports(lib().cq_lnv_state)

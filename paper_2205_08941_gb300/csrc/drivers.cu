@@ -232,6 +232,11 @@ struct cq_lnv {
     cq_precision prec = CQ_FP64;
     DevBuf X, Y, U, Z, R1, R2, R3, GE, GN, G, Gp, D, Dp, Lt;
     bool have_prev = false, have_alpha = false;
+    // optional preconditioner: search directions from Zs = sym(mask_L(T G T))
+    bool precond = false;
+    const cq_pattern *pT = nullptr;
+    cq_pattern *pTL = nullptr;      // reaches r_T + r_L (holds T G)
+    DevBuf T, TG, Zr, Zs, Zp;       // copy of T; T G; raw, symmetrised and previous Z
     double n_tol = 1e-10;
     double n_tol_split = 1e-9;
     int max_corr = 5;
@@ -549,21 +554,36 @@ extern "C" cq_status cq_lnv_step(cq_lnv *s, cq_lnv_report *rep)
     s->products = 0;
     std::vector<double> mu, gn2;
     CQ_TRY(lnv_mu_g(s, mu, gn2));
+    // direction source Zc: G itself, or with a preconditioner Zs = sym(mask_L(T G T)); Zq is
+    // the previous step's (G_prev, or Z_prev)
+    const double *Zc = G, *Zq = s->Gp.as<double>();
+    if (s->precond) {
+        double *TG = s->TG.as<double>(), *Zr = s->Zr.as<double>(), *Zs = s->Zs.as<double>();
+        const double *T = s->T.as<double>();
+        CQ_TRY(bsmm(ctx, 1.0, s->pT, T, pL, G, 0.0, s->pTL, TG, s->prec, &s->flops));
+        CQ_TRY(bsmm(ctx, 1.0, s->pTL, TG, s->pT, T, 0.0, pL, Zr, s->prec, &s->flops));
+        s->products += 2;
+        CQ_TRY(copy_vals(ctx, Zs, Zr, n));
+        CQ_TRY(cq_gather(ctx, pL, Zr, pL, Zs, 1, 0.5, 0.5));  // Zs = (Zr + Zr^T) / 2
+        Zc = Zs;
+        Zq = s->Zp.as<double>();
+    }
     std::vector<bool> restart(nc, !s->have_prev);
     if (!s->have_prev) {
-        CQ_TRY(axpby_c(ctx, pL, neg1, G, zero, D));
+        CQ_TRY(axpby_c(ctx, pL, neg1, Zc, zero, D));
     } else {
-        // beta = max(0, <G, G - G_prev> / <G_prev, G_prev>), D = -G + beta D_prev
-        CQ_TRY(copy_vals(ctx, D, G, n));
-        CQ_TRY(axpby_c(ctx, pL, neg1, s->Gp.as<double>(), one, D));
+        // beta = max(0, <G, Z - Z_prev> / <G_prev, Z_prev>) (Z = G without a preconditioner),
+        // D = -Z + beta D_prev
+        CQ_TRY(copy_vals(ctx, D, Zc, n));
+        CQ_TRY(axpby_c(ctx, pL, neg1, Zq, one, D));
         CQ_TRY(dot_q(ctx, pL, G, D, 0));
-        CQ_TRY(dot_q(ctx, pL, s->Gp.as<double>(), s->Gp.as<double>(), 1));
+        CQ_TRY(dot_q(ctx, pL, s->Gp.as<double>(), Zq, 1));
         std::vector<std::vector<double>> d;
         CQ_TRY(fetch_q(ctx, nc, 2, d));
         std::vector<double> beta(nc);
         for (int c = 0; c < nc; ++c) beta[c] = std::fmax(0.0, d[0][c] / d[1][c]);
         CQ_TRY(copy_vals(ctx, D, s->Dp.as<double>(), n));
-        CQ_TRY(axpby_c(ctx, pL, neg1, G, beta, D));
+        CQ_TRY(axpby_c(ctx, pL, neg1, Zc, beta, D));
     }
     std::vector<double> dg;
     CQ_TRY(dots(s, D, GN, dg));
@@ -581,11 +601,11 @@ extern "C" cq_status cq_lnv_step(cq_lnv *s, cq_lnv_report *rep)
             ra[c] = -1.0;
             rb[c] = 0.0;
         }
-    if (any_restart) CQ_TRY(axpby_c(ctx, pL, ra, G, rb, D));
+    if (any_restart) CQ_TRY(axpby_c(ctx, pL, ra, Zc, rb, D));
     std::vector<double> a1(nc), a2(nc);
     if (!s->have_alpha) {
         std::vector<double> gg;
-        CQ_TRY(dots(s, G, G, gg));
+        CQ_TRY(dots(s, Zc, Zc, gg));
         for (int c = 0; c < nc; ++c)
             a1[c] = 0.1 * std::sqrt((double)pL->seg_scalars[c]) / std::sqrt(gg[c]);
     } else {
@@ -632,6 +652,7 @@ extern "C" cq_status cq_lnv_step(cq_lnv *s, cq_lnv_report *rep)
     CQ_TRY(lnv_evaluate_corrected(s, ncorr));
     std::swap(s->G.ptr, s->Gp.ptr);  // G_prev <- G
     std::swap(s->D.ptr, s->Dp.ptr);  // D_prev <- D
+    if (s->precond) std::swap(s->Zs.ptr, s->Zp.ptr);  // Z_prev <- Z
     s->have_prev = true;
     s->have_alpha = true;
     s->alpha_prev = alpha;
@@ -658,6 +679,28 @@ extern "C" cq_status cq_lnv_set_precision(cq_lnv *s, cq_precision prec)
     s->have_prev = false;
     s->have_alpha = false;
     return lnv_evaluate_corrected(s, s->n_corr_initial);
+}
+
+extern "C" cq_status cq_lnv_set_preconditioner(cq_lnv *s, const cq_pattern *pT, const double *T)
+{
+    if (!s || !s->ctx) return CQ_ERR_INVALID;
+    cq_ctx *ctx = s->ctx;
+    s->have_prev = false;
+    s->have_alpha = false;
+    if (!pT || !T) {
+        s->precond = false;
+        return CQ_OK;
+    }
+    CQ_TRY(same_ctx(ctx, pT, s->pL));
+    CQ_TRY(cq_pattern_derived(ctx, s->pL, 1.0, pT, 1.0, s->pL, &s->pTL));
+    const size_t bl = sizeof(double) * s->pL->n_values;
+    CQ_TRY(cq_alloc(ctx, s->T, sizeof(double) * pT->n_values));
+    CQ_TRY(cq_alloc(ctx, s->TG, sizeof(double) * s->pTL->n_values));
+    for (DevBuf *b : {&s->Zr, &s->Zs, &s->Zp}) CQ_TRY(cq_alloc(ctx, *b, bl));
+    CQ_TRY(copy_vals(ctx, s->T.as<double>(), T, pT->n_values));
+    s->pT = pT;
+    s->precond = true;
+    return cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "lnv_set_preconditioner");
 }
 
 extern "C" cq_status cq_lnv_state(const cq_lnv *cs, cq_lnv_report *rep)
@@ -699,6 +742,12 @@ extern "C" cq_status cq_lnv_step_flops(cq_lnv *s, double *flops_host)
     // two trial points (X, Y, U, R1, R3) + one evaluation without corrections (7 products)
     *flops_host = 2.0 * (2 * a->flops + b->flops + 2 * c->flops) +
                   (2 * a->flops + 2 * b->flops + 3 * c->flops);
+    if (s->precond) {  // T G on P_(T+L), then (T G) T on P_L
+        TaskList *d, *e;
+        CQ_TRY(cq_get_tasks(s->ctx, s->pT, s->pL, s->pTL, &d));
+        CQ_TRY(cq_get_tasks(s->ctx, s->pTL, s->pT, s->pL, &e));
+        *flops_host += d->flops + e->flops;
+    }
     return CQ_OK;
 }
 
@@ -708,7 +757,8 @@ void cq_lnv_detach(cq_lnv *s)
 {
     s->ctx = nullptr;
     for (DevBuf *b : {&s->X, &s->Y, &s->U, &s->Z, &s->R1, &s->R2, &s->R3, &s->GE, &s->GN,
-                      &s->G, &s->Gp, &s->D, &s->Dp, &s->Lt})
+                      &s->G, &s->Gp, &s->D, &s->Dp, &s->Lt, &s->T, &s->TG, &s->Zr, &s->Zs,
+                      &s->Zp})
         b->ctx = nullptr;
 }
 
