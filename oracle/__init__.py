@@ -13,6 +13,7 @@ methods that solver is built from, restated from their mathematics:
 
 * masked block product  C = mask_{P_C}(A B)               (the sparse matrix product)
 * Hotelling / Schulz     T <- 2T - T S T                   (overlap inversion)
+* least-squares inverse  min ||I - S T||_F over T on P_T, by linear CG (overlap inversion)
 * Li-Nunes-Vanderbilt    K = 3LSL - 2LSLSL, E = 2Tr(KH), N = 2Tr(KS)  (density matrix)
 * McWeeny purification   L <- 3LSL - 2LSLSL
 * Palser-Manolopoulos    initial L from T ~ S^-1 and Gershgorin bounds of TH
@@ -282,6 +283,45 @@ def hotelling_step(pS: Pattern, S, pT: Pattern, T, pV: Pattern):
     r = frob_minus_identity(pV, V)
     W = bsmm(1.0, pT, T, pV, V, 0.0, pT)
     return 2.0 * T - W, r
+
+
+def overlap_inverse_cg(pS: Pattern, S, pT: Pattern, T, pV: Pattern, max_iter: int,
+                       gtol: float = 0.0):
+    """Overlap inverse as the best T on P_T: minimise f(T) = ||I - S T||_F^2 over symmetric T
+    stored on P_T, by linear conjugate gradients from the given T (an alternative to the
+    Hotelling iteration; Development Priorities, improved linear-scaling inversion of the
+    overlap).
+
+    R = I - S T lives on P_V (P_V must reach r_S + r_T, so R is the whole residual).  For a
+    symmetric change dT on P_T, df = -2 <S R, dT>, so the gradient on P_T is
+    G = -(W + W^T) with W = mask_{P_T}(S R).  Along D, f is the quadratic
+    ||R||^2 - 2a<R, S D> + a^2 ||S D||^2, minimised at a = -<G, D> / (2 ||S D||^2); then
+    T += a D, R -= a S D, and the next direction is -G + (<G, G> / <G_prev, G_prev>) D
+    (Fletcher-Reeves, exact for a quadratic with exact line searches).
+    Stops after max_iter steps, or once ||G||_F <= gtol * ||G_0||_F.
+
+    Returns (T, resid, gnorm): resid[k] = ||I - S T_k||_F and gnorm[k] = ||G_k||_F for every
+    iterate T_0 (the start) ... T_n, so n = len(resid) - 1 steps were taken.
+    """
+    T = np.array(T, dtype=np.float64, copy=True)
+    R = identity(pV) - bsmm(1.0, pS, S, pT, T, 0.0, pV)
+    D, gg_prev = None, None
+    resid, gnorm = [], []
+    for k in range(max_iter + 1):
+        W = bsmm(1.0, pS, S, pV, R, 0.0, pT)
+        G = -(W + gather(pT, W, pT, transpose=True))
+        gg = dot(G, G)
+        resid.append(float(np.sqrt(dot(R, R))))
+        gnorm.append(float(np.sqrt(gg)))
+        if k == max_iter or gnorm[-1] <= gtol * gnorm[0]:
+            break
+        D = -G if D is None else -G + (gg / gg_prev) * D
+        SD = bsmm(1.0, pS, S, pT, D, 0.0, pV)
+        a = -dot(G, D) / (2.0 * dot(SD, SD))
+        T += a * D
+        R -= a * SD
+        gg_prev = gg
+    return T, resid, gnorm
 
 
 # ---------------------------------------------------------------------------------------

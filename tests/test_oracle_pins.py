@@ -382,3 +382,79 @@ def test_preconditioned_dense_limit_is_the_band_energy(c1):
     _steps_to(lnv, 1e-9, 60)
     e = sl.eigh(O.to_dense(pS, H), O.to_dense(pS, S), eigvals_only=True)
     assert lnv.E == pytest.approx(2.0 * e[:128].sum(), abs=1e-8)
+
+
+# ------------------------------------------------------------------ CG overlap inverse
+
+def _best_sparse_inverse(pS, S, pT):
+    """The exact minimiser of ||I - S T||_F over symmetric T on P_T, by a direct sparse
+    least-squares solve: unknowns t_u for the scalar pairs a <= b stored in P_T, columns
+    vec(S E_u) with E_u = e_a e_b^T + e_b e_a^T (e_a e_a^T on the diagonal), normal
+    equations solved by scipy.sparse.linalg.spsolve."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    Sd = O.to_dense(pS, S)
+    n = Sd.shape[0]
+    mask = O.to_dense(pT, np.ones(pT.n_values)) != 0
+    ia, ib = np.nonzero(np.triu(mask))
+    rows, cols, vals = [], [], []
+    for u, (a, b) in enumerate(zip(ia, ib)):
+        for src, dst in ((a, b), (b, a)) if a != b else ((a, b),):
+            r = np.nonzero(Sd[:, src])[0]
+            rows.append(r * n + dst)           # (r, dst) of S E_u, row-major vec
+            cols.append(np.full(r.size, u))
+            vals.append(Sd[r, src])
+    A = sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n * n, ia.size))
+    y = np.eye(n).ravel()
+    t = spl.spsolve((A.T @ A).tocsc(), A.T @ y)
+    Td = np.zeros((n, n))
+    Td[ia, ib] = t
+    Td[ib, ia] = t
+    return O.from_dense(pT, Td), float(np.linalg.norm(A @ t - y))
+
+
+def test_cg_inverse_reaches_the_least_squares_minimiser_on_p_t(c1):
+    cell, Spb, _ = c1
+    pS, pT = O.Pattern.of_cell(cell, 10.0), O.Pattern.of_cell(cell, 5.0)  # nearest neighbours
+    pV = O.Pattern.of_cell(cell, 15.0)
+    S = O.scatter(pS, Spb)
+    T_best, r_best = _best_sparse_inverse(pS, S, pT)
+    # a symmetric start that does not commute with S (I / sigma would hide a transposed
+    # S T in the first residual)
+    T0 = O.hotelling_init(pS, S, pT) + 0.05 * O.scatter(pT, I.random_blocks(cell, 5.0, 31))
+    assert np.array_equal(O.gather(pT, T0, pT, transpose=True), T0)
+    T, resid, gnorm = O.overlap_inverse_cg(pS, S, pT, T0, pV, 200, gtol=1e-13)
+    assert gnorm[-1] <= 1e-13 * gnorm[0] and len(resid) < 200
+    assert np.all(np.diff(resid) <= 1e-14 * resid[0])       # exact line searches
+    assert resid[-1] == pytest.approx(r_best, rel=1e-10)
+    assert np.abs(T - T_best).max() <= 1e-9 * np.abs(T_best).max()
+    # the residual the function reports is the one of the T it returns
+    V = O.bsmm(1.0, pS, S, pT, T, 0.0, pV)
+    assert O.frob_minus_identity(pV, V) == pytest.approx(resid[-1], rel=1e-10)
+
+
+def test_cg_inverse_dense_limit_is_the_inverse(c1):
+    cell, Spb, _ = c1
+    pS, pD = O.Pattern.of_cell(cell, 10.0), O.Pattern.of_cell(cell, 22.0)
+    assert pD.nnzb == cell.n_atoms ** 2
+    S = O.scatter(pS, Spb)
+    T, resid, _ = O.overlap_inverse_cg(pS, S, pD, O.hotelling_init(pS, S, pD), pD, 200,
+                                       gtol=1e-14)
+    Sinv = np.linalg.inv(O.to_dense(pS, S))
+    assert np.abs(O.to_dense(pD, T) - Sinv).max() <= 1e-10 * np.abs(Sinv).max()
+    assert resid[-1] <= 1e-11 * resid[0]
+
+
+def test_cg_inverse_beats_the_truncated_hotelling_fixed_point(c1):
+    cell, Spb, _ = c1
+    pS, pT = O.Pattern.of_cell(cell, 10.0), O.Pattern.of_cell(cell, 12.0)
+    pV = O.Pattern.of_cell(cell, 22.0)
+    S = O.scatter(pS, Spb)
+    T0 = O.hotelling_init(pS, S, pT)
+    Th = T0
+    for _ in range(20):
+        Th, r_hot = O.hotelling_step(pS, S, pT, Th, pV)
+    T, resid, _ = O.overlap_inverse_cg(pS, S, pT, T0, pV, 40)
+    assert resid[-1] < r_hot                               # best T on the same pattern
+    assert np.array_equal(O.gather(pT, T, pT, transpose=True), T)   # stays exactly symmetric
