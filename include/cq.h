@@ -231,6 +231,28 @@ cq_status cq_hotelling_init(cq_ctx *ctx, const cq_pattern *pS, const double *S,
 cq_status cq_hotelling_step(cq_ctx *ctx, const cq_pattern *pS, const double *S,
                             const cq_pattern *pT, double *T, double *resid_host);
 
+/*
+ * Least-squares overlap inverse (Development Priorities: other ways to invert the overlap in
+ * linear-scaling time): the T on P_T that minimises ||I - S T||_F,
+ * found by linear conjugate gradients on the symmetric values of T, started from the T
+ * passed in (e.g. cq_hotelling_init, or a Hotelling result to refine).  R = I - S T is kept
+ * on P_{rS+rT}; the gradient on P_T is G = -(W + W^T) with W = mask_{P_T}(S R); each step
+ * takes the exact minimiser along D (two products per step: S.D and S.R), then
+ * D <- -G + (|G|^2 / |G_prev|^2) D.  Unlike Hotelling's truncated fixed point, the result
+ * is the best inverse the pattern can hold.
+ *   T          in: symmetric start on P_T; out: the last iterate (updated in place).
+ *   max_iter   step limit (>= 0); gtol: stop once ||G||_F <= gtol ||G_0||_F (>= 0).
+ *   resid_host, gnorm_host  NULL or host arrays of max_iter + 1 doubles: ||I - S T_k||_F and
+ *              ||G_k||_F for the start (k = 0) and every iterate.
+ *   iters_host NULL or the number of steps taken.
+ * Single cells only (batch patterns give CQ_ERR_INVALID); FP64; scratch owned by the
+ * context.  A non-finite residual gives CQ_ERR_NUMERIC.  Synchronises every step.
+ */
+cq_status cq_overlap_inverse_cg(cq_ctx *ctx, const cq_pattern *pS, const double *S,
+                                const cq_pattern *pT, double *T, int32_t max_iter,
+                                double gtol, double *resid_host, double *gnorm_host,
+                                int32_t *iters_host);
+
 /* ---------------------------------------------------------------- density matrix */
 
 /*

@@ -288,9 +288,8 @@ def hotelling_step(pS: Pattern, S, pT: Pattern, T, pV: Pattern):
 def overlap_inverse_cg(pS: Pattern, S, pT: Pattern, T, pV: Pattern, max_iter: int,
                        gtol: float = 0.0):
     """Overlap inverse as the best T on P_T: minimise f(T) = ||I - S T||_F^2 over symmetric T
-    stored on P_T, by linear conjugate gradients from the given T (an alternative to the
-    Hotelling iteration; Development Priorities, improved linear-scaling inversion of the
-    overlap).
+    stored on P_T, by linear conjugate gradients from the given T (another route than the
+    Hotelling iteration to the overlap inverse; Development Priorities).
 
     R = I - S T lives on P_V (P_V must reach r_S + r_T, so R is the whole residual).  For a
     symmetric change dT on P_T, df = -2 <S R, dT>, so the gradient on P_T is

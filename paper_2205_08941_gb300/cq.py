@@ -65,6 +65,8 @@ SIGNATURES = {
     "cq_dot": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(_d)]),
     "cq_hotelling_init": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "cq_hotelling_step": (_st, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d)]),
+    "cq_overlap_inverse_cg": (_st, [_vp, _vp, _vp, _vp, _vp, _i32, _d, _vp, _vp,
+                                    ctypes.POINTER(_i32)]),
     "cq_pm_guess": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d]),
     "cq_mcweeny_step": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "cq_lnv_create": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _d, ctypes.c_int,
@@ -277,6 +279,18 @@ class Context:
         self._check(lib().cq_hotelling_step(self.h, pS.h, _ptr(S), pT.h, _ptr(T),
                                             ctypes.byref(r)))
         return float(r.value)
+
+    def overlap_inverse_cg(self, pS, S, pT, T, max_iter: int, gtol: float = 0.0):
+        """Least-squares inverse on P_T by CG from T (updated in place).  Returns
+        (resid, gnorm): ||I - S T_k||_F and ||G_k||_F for the start and every iterate."""
+        r = (_d * (max_iter + 1))()
+        g = (_d * (max_iter + 1))()
+        k = ctypes.c_int32()
+        self._check(lib().cq_overlap_inverse_cg(self.h, pS.h, _ptr(S), pT.h, _ptr(T),
+                                                int(max_iter), float(gtol), r, g,
+                                                ctypes.byref(k)))
+        n = int(k.value) + 1
+        return list(r[:n]), list(g[:n])
 
     def pm_guess(self, pS, S, H, pT, T, pL, L, n_occ: float):
         self._check(lib().cq_pm_guess(self.h, pS.h, _ptr(S), _ptr(H), pT.h, _ptr(T), pL.h,

@@ -129,6 +129,66 @@ extern "C" cq_status cq_hotelling_step(cq_ctx *ctx, const cq_pattern *pS, const 
     return CQ_OK;
 }
 
+// Least-squares overlap inverse: minimise f(T) = ||I - S T||_F^2 over symmetric T on P_T by
+// linear conjugate gradients.  R = I - S T is kept on P_V = P_{rS+rT} (the whole residual);
+// the gradient on P_T is G = -(W + W^T), W = mask_{P_T}(S R); along D the exact minimiser is
+// a = -<G, D> / (2 ||S D||^2); then T += a D, R -= a S D and D <- -G + (<G,G>/<G_prev,G_prev>) D.
+extern "C" cq_status cq_overlap_inverse_cg(cq_ctx *ctx, const cq_pattern *pS, const double *S,
+                                           const cq_pattern *pT, double *T, int32_t max_iter,
+                                           double gtol, double *resid_host, double *gnorm_host,
+                                           int32_t *iters_host)
+{
+    if (!ctx || !S || !T || max_iter < 0 || !(gtol >= 0.0)) return CQ_ERR_INVALID;
+    CQ_TRY(same_ctx(ctx, pS, pT));
+    if (pS->n_cells() != 1 || pT->n_cells() != 1)
+        return cq_fail(ctx, CQ_ERR_INVALID, "overlap_inverse_cg: batch patterns not supported");
+    cq_pattern *pV = nullptr;
+    CQ_TRY(cq_pattern_derived(ctx, pS, 1.0, pS, 1.0, pT, &pV));
+    const int64_t nT = pT->n_values, nV = pV->n_values;
+    void *r, *sd, *w, *g, *d;
+    CQ_TRY(cq_scratch(ctx, "sinv_R", sizeof(double) * nV, &r));
+    CQ_TRY(cq_scratch(ctx, "sinv_SD", sizeof(double) * nV, &sd));
+    CQ_TRY(cq_scratch(ctx, "sinv_W", sizeof(double) * nT, &w));
+    CQ_TRY(cq_scratch(ctx, "sinv_G", sizeof(double) * nT, &g));
+    CQ_TRY(cq_scratch(ctx, "sinv_D", sizeof(double) * nT, &d));
+    double *R = (double *)r, *SD = (double *)sd, *W = (double *)w, *G = (double *)g,
+           *D = (double *)d;
+    CQ_TRY(cq_set_identity(ctx, pV, R, 1.0));
+    CQ_TRY(bsmm(ctx, -1.0, pS, S, pT, T, 1.0, pV, R, CQ_FP64));  // R = I - S T
+    double g0 = 0.0, gg_prev = 0.0;
+    int32_t k = 0;
+    for (;; ++k) {
+        CQ_TRY(bsmm(ctx, 1.0, pS, S, pV, R, 0.0, pT, W, CQ_FP64));
+        CQ_TRY(cq_axpby(ctx, nT, -1.0, W, 0.0, G));
+        CQ_TRY(cq_gather(ctx, pT, W, pT, G, 1, -1.0, 1.0));      // G = -(W + W^T)
+        CQ_TRY(cq_dot_dev(ctx, pT, G, G, 0));
+        CQ_TRY(cq_dot_dev(ctx, pV, R, R, 1));
+        double v[2];
+        CQ_TRY(cq_fetch(ctx, 0, 2, v));
+        if (!std::isfinite(v[0]) || !std::isfinite(v[1]))
+            return cq_fail(ctx, CQ_ERR_NUMERIC, "overlap_inverse_cg: non-finite residual");
+        const double gn = std::sqrt(v[0]);
+        if (resid_host) resid_host[k] = std::sqrt(v[1]);
+        if (gnorm_host) gnorm_host[k] = gn;
+        if (k == 0) g0 = gn;
+        if (k == max_iter || gn <= gtol * g0) break;
+        CQ_TRY(cq_axpby(ctx, nT, -1.0, G, k == 0 ? 0.0 : v[0] / gg_prev, D));
+        CQ_TRY(bsmm(ctx, 1.0, pS, S, pT, D, 0.0, pV, SD, CQ_FP64));
+        CQ_TRY(cq_dot_dev(ctx, pT, G, D, 0));
+        CQ_TRY(cq_dot_dev(ctx, pV, SD, SD, 1));
+        double q[2];
+        CQ_TRY(cq_fetch(ctx, 0, 2, q));
+        if (!(q[1] > 0.0) || !std::isfinite(q[0]))
+            return cq_fail(ctx, CQ_ERR_NUMERIC, "overlap_inverse_cg: degenerate direction");
+        const double a = -q[0] / (2.0 * q[1]);
+        CQ_TRY(cq_axpby(ctx, nT, a, D, 1.0, T));
+        CQ_TRY(cq_axpby(ctx, nV, -a, SD, 1.0, R));
+        gg_prev = v[0];
+    }
+    if (iters_host) *iters_host = k;
+    return CQ_OK;
+}
+
 // ---------------------------------------------------------------- PM start, McWeeny
 
 extern "C" cq_status cq_pm_guess_cells(cq_ctx *ctx, const cq_pattern *pS, const double *S,

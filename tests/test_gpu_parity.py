@@ -185,6 +185,28 @@ def test_hotelling_parity_c1(ctx, c1, rt):
     assert err.max() < 1e-12 * nrm.max()
 
 
+def test_overlap_inverse_cg_parity_c1(ctx, c1):
+    """Least-squares inverse on P_T by CG: residual and gradient histories and the final T
+    against the oracle, from a symmetric start that does not commute with S."""
+    cell, pS, pT, S_o, _, S_g, _ = _setup_c1(ctx, c1, 12.0)
+    pV = O.Pattern.of_cell(cell, 22.0)
+    T0 = (O.hotelling_init(pS.o, S_o, pT.o)
+          + 0.05 * O.scatter(pT.o, I.random_blocks(cell, 12.0, 31)))
+    T_o, r_o, g_o = O.overlap_inverse_cg(pS.o, S_o, pT.o, T0, pV, 25)
+    T_g = pT.up(ctx, T0)
+    r0, g0 = ctx.overlap_inverse_cg(pS.g, S_g, pT.g, T_g, 0)   # no step: start values only
+    assert len(r0) == 1 and r0[0] == pytest.approx(r_o[0], rel=1e-12)
+    assert np.array_equal(pT.down(T_g), T0)
+    r_g, g_g = ctx.overlap_inverse_cg(pS.g, S_g, pT.g, T_g, 25)
+    assert len(r_g) == len(r_o) == 26
+    assert r_g == pytest.approx(r_o, rel=1e-9)
+    assert g_g == pytest.approx(g_o, rel=1e-6, abs=1e-12 * g_o[0])
+    err, nrm = block_errors(pT.o, pT.down(T_g), T_o)
+    assert err.max() < 1e-10 * nrm.max()
+    # the reported residual is the one of the T returned (Hotelling reports the incoming T's)
+    assert ctx.hotelling_step(pS.g, S_g, pT.g, T_g.clone()) == pytest.approx(r_g[-1], rel=1e-10)
+
+
 def test_pm_guess_and_mcweeny_parity_c1(ctx, c1):
     cell, pS, pL, S_o, H_o, S_g, H_g = _setup_c1(ctx, c1, 12.0)
     pX, pU, p2L = (O.Pattern.of_cell(cell, r) for r in (22.0, 32.0, 24.0))
