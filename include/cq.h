@@ -166,7 +166,10 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  * needs a uniform basis of 4 or 9 orbitals per atom (else CQ_ERR_INVALID); it packs both
  * operands into context-owned scratch panels before every call (about 2x the FP64 size of
  * the operands, the A side in batches of at most 12 GB), and its accuracy is FP32-class:
- * about 1e-7 relative per block, with FP32 partial sums drained to double-float.  The call is
+ * about 1e-7 relative per block, with FP32 partial sums drained to double-float.  Each value
+ * is split to about 2^-27 relative for 2^-74 <= |x| < (2 - 2^-8) 2^127 (coarser below,
+ * zero under 2^-126); larger values, infinities and NaNs give NaN in every C value they
+ * reach, so the next trace reports CQ_ERR_NUMERIC as with FP64.  The call is
  * asynchronous on the context stream; if a bounded wait inside the split kernel ran out (a
  * tensor-core completion not seen within about two seconds), the next synchronising call on
  * the context (cq_ctx_sync, a trace, a dot, an LNV or Hotelling step) returns

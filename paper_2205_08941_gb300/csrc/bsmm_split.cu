@@ -38,6 +38,7 @@
 #include <numeric>
 
 #include "cq_internal.cuh"
+#include "split3.cuh"
 
 namespace {
 
@@ -94,34 +95,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
 // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N = 64, M = 128
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                            ((uint32_t)(MT >> 4) << 24);
-
-// Three-term BF16 split of an FP64 value without FP64 instructions (the FP64 pipe is the
-// scarce unit on this GPU): the double's bits give an FP32 head h (its significand cut to
-// 24 bits) and an FP32 tail l (the 29 bits cut off, rounded to 24), x = h + l; then
-// b0 = bf16(h), b1 = bf16(h - b0), b2 = bf16((h - b0 - b1) + l), the first two differences
-// exact in FP32.  |x - (b0 + b1 + b2)| is about 2^-26 |x|.  Zeros, subnormals and values
-// below the FP32 normal range give zero terms; the operands here are far inside the range.
-__device__ __forceinline__ void split3(double x, __nv_bfloat16 &b0, __nv_bfloat16 &b1,
-                                       __nv_bfloat16 &b2)
-{
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((u >> 52) & 0x7FF) - 1023 + 127;  // FP32 exponent field
-    const unsigned long long m = u & ((1ull << 52) - 1);
-    const unsigned sign = (unsigned)(u >> 63) << 31;
-    float h = 0.f, l = 0.f;
-    if (e >= 1 && e <= 254) {
-        h = __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)(m >> 29));
-        if (e > 52) {  // the tail's scale 2^(exponent - 52) is a normal FP32 number
-            l = (float)(unsigned)(m & ((1u << 29) - 1)) * __uint_as_float((unsigned)(e - 52) << 23);
-            if (sign) l = -l;
-        }
-    }
-    b0 = __float2bfloat16_rn(h);
-    const float r1 = h - __bfloat162float(b0);
-    b1 = __float2bfloat16_rn(r1);
-    const float r2 = (r1 - __bfloat162float(b1)) + l;
-    b2 = __float2bfloat16_rn(r2);
-}
 
 // index of block (row, col) in a pattern, or -1
 __device__ __forceinline__ int64_t find_block(const int64_t *rp, const int32_t *cl, int row, int col)

@@ -82,6 +82,40 @@ def test_split_parity_szp_512(ctx, ranges):
     _check_split(ctx, cell, ranges, rows=rows)
 
 
+def test_split_carries_out_of_range_values_as_nan(ctx):
+    """A value beyond the split's range (or infinite, or NaN) in A turns every C value it
+    reaches into NaN instead of vanishing: all values the FP64 oracle makes NaN for a NaN
+    there, and only values of the same scalar row (the densified tile may also reach blocks
+    of that row that the masked product leaves out)."""
+    cell = I.diamond_cell(2, a=10.26, sigma=0.05, seed=1, norb=4)
+    A_, B_, C_ = (Both(ctx, cell, r) for r in (12.0, 10.0, 22.0))
+    A = O.scatter(A_.o, I.random_blocks(cell, 12.0, 1, symmetric=False))
+    B = O.scatter(B_.o, I.random_blocks(cell, 10.0, 2, symmetric=False))
+    blk = 37                                   # an off-diagonal block of A, its value (1, 2)
+    i_atom = int(A_.o.row[blk])
+    pos = int(A_.o.off[blk]) + 1 * int(cell.nb[int(A_.o.col[blk])]) + 2
+    An = A.copy()
+    An[pos] = np.nan
+    reach = np.isnan(O.bsmm(1.0, A_.o, An, B_.o, B, 0.0, C_.o))
+    assert reach.any()
+    # C values of scalar row 1 of atom i_atom (blocks (i_atom, j) of P_C)
+    row1 = np.zeros(C_.o.n_values, dtype=bool)
+    for b in np.nonzero(C_.o.row == i_atom)[0]:
+        nj = int(cell.nb[int(C_.o.col[b])])
+        row1[int(C_.o.off[b]) + nj:int(C_.o.off[b]) + 2 * nj] = True
+    assert not (reach & ~row1).any()
+    Bg = B_.up(ctx, B)
+    for bad in (1e300, -np.inf, np.nan):
+        Ab = A.copy()
+        Ab[pos] = bad
+        Cg = ctx.zeros(C_.g)
+        ctx.bsmm(1.0, A_.g, A_.up(ctx, Ab), B_.g, Bg, 0.0, C_.g, Cg,
+                 prec=cq.CQ_SPLIT_BF16X3)
+        got = C_.down(Cg)
+        assert np.isnan(got[reach]).all(), bad
+        assert np.isfinite(got[~row1]).all(), bad
+
+
 def test_split_rejects_mixed_basis(ctx):
     cell = I.diamond_cell(1, a=10.26, sigma=0.1, seed=3, norb=4)
     cell.nb = np.array([4, 9] * 4, dtype=np.int32)
