@@ -17,8 +17,8 @@ import oracle as O
 from paper_2205_08941_gb300 import cq
 from paper_2205_08941_gb300 import inputs as I
 
-from helpers import (block_errors, from_oracle, gpu_pattern, layout_index, natural_scale,
-                     to_oracle, upload_pairs)
+from helpers import (assert_product_close, block_errors, from_oracle, gpu_pattern,
+                     layout_index, natural_scale, to_oracle, upload_pairs)
 
 pytestmark = pytest.mark.gpu
 
@@ -80,6 +80,34 @@ def test_split_parity_szp_512(ctx, ranges):
     cell = I.diamond_cell(4, a=10.26, sigma=0.1, seed=2, norb=9)
     rows = np.arange(0, cell.n_atoms, 29, dtype=np.int32)
     _check_split(ctx, cell, ranges, rows=rows)
+
+
+def test_blocks_without_triplets_get_exactly_beta_c(ctx):
+    """P_C reaches beyond r_A + r_B, so some C blocks have no (i, k, j) at all (and some
+    split tiles may have no K chunk): those must come out as exactly beta C_ij (zero for
+    beta = 0) in both precisions, the others as the product."""
+    cell = I.diamond_cell(2, a=10.26, sigma=0.05, seed=1, norb=4)
+    A_, B_, C_ = (Both(ctx, cell, r) for r in (5.0, 5.0, 12.0))
+    A = O.scatter(A_.o, I.random_blocks(cell, 5.0, 1, symmetric=False))
+    B = O.scatter(B_.o, I.random_blocks(cell, 5.0, 2, symmetric=False))
+    C0 = O.scatter(C_.o, I.random_blocks(cell, 12.0, 3, symmetric=False))
+    scale = natural_scale(A_.o, A, B_.o, B, C_.o)
+    empty = scale == 0.0                       # no triplet reaches these blocks
+    assert empty.any() and not empty.all()
+    ev = np.repeat(empty, np.diff(C_.o.off))
+    Ag, Bg = A_.up(ctx, A), B_.up(ctx, B)
+    for prec in (cq.CQ_FP64, cq.CQ_SPLIT_BF16X3):
+        for beta in (0.0, 1.3):
+            ref = O.bsmm(-0.7, A_.o, A, B_.o, B, beta, C_.o, C0.copy())
+            Cg = C_.up(ctx, C0)
+            ctx.bsmm(-0.7, A_.g, Ag, B_.g, Bg, beta, C_.g, Cg, prec=prec)
+            got = C_.down(Cg)
+            assert np.array_equal(got[ev], beta * C0[ev]), (prec, beta)
+            if prec == cq.CQ_FP64:
+                assert_product_close(C_.o, got, ref, 0.7 * scale + beta * np.abs(ref).max())
+            else:
+                err, _ = block_errors(C_.o, got, ref)
+                assert (err[~empty] <= 1e-5 * 0.7 * scale[~empty]).all(), (prec, beta)
 
 
 def test_split_carries_out_of_range_values_as_nan(ctx):
