@@ -751,6 +751,8 @@ extern "C" cq_status cq_lnv_set_preconditioner(cq_lnv *s, const cq_pattern *pT, 
         s->precond = false;
         return CQ_OK;
     }
+    if (s->nc != 1)
+        return cq_fail(ctx, CQ_ERR_INVALID, "lnv_set_preconditioner: single cells only");
     CQ_TRY(same_ctx(ctx, pT, s->pL));
     CQ_TRY(cq_pattern_derived(ctx, s->pL, 1.0, pT, 1.0, s->pL, &s->pTL));
     const size_t bl = sizeof(double) * s->pL->n_values;
