@@ -332,8 +332,9 @@ cq_status cq_lnv_set_precision(cq_lnv *lnv, cq_precision prec);
  * beta = max(0, <G, Z - Z_prev> / <G_prev, Z_prev>), restarts to -Z, and the first trial
  * step 0.1 sqrt(n) / ||Z||.  With T = identity the steps are those of the plain gradient.
  * T is copied (the caller keeps its buffer); pT must outlive the preconditioner.  T = NULL
- * or pT = NULL switches it off.  The search history is reset either way.  Single cells
- * only: a batched LNV object (cq_lnv_create_cells) gives CQ_ERR_INVALID.  Synchronises. */
+ * or pT = NULL switches it off, and so does a failed call.  The search history is reset
+ * either way.  Single cells only: a batched LNV object (cq_lnv_create_cells) gives
+ * CQ_ERR_INVALID.  Synchronises. */
 cq_status cq_lnv_set_preconditioner(cq_lnv *lnv, const cq_pattern *pT, const double *T);
 /* Current E, N, mu and RMS gradient (as after the last evaluation), one report per cell. */
 cq_status cq_lnv_state(const cq_lnv *lnv, cq_lnv_report *report_host);

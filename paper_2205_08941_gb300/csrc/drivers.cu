@@ -747,10 +747,8 @@ extern "C" cq_status cq_lnv_set_preconditioner(cq_lnv *s, const cq_pattern *pT, 
     cq_ctx *ctx = s->ctx;
     s->have_prev = false;
     s->have_alpha = false;
-    if (!pT || !T) {
-        s->precond = false;
-        return CQ_OK;
-    }
+    s->precond = false;  // stays off unless every step below succeeds
+    if (!pT || !T) return CQ_OK;
     if (s->nc != 1)
         return cq_fail(ctx, CQ_ERR_INVALID, "lnv_set_preconditioner: single cells only");
     CQ_TRY(same_ctx(ctx, pT, s->pL));
