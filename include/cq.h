@@ -249,7 +249,9 @@ cq_status cq_hotelling_step(cq_ctx *ctx, const cq_pattern *pS, const double *S,
  *              ||G_k||_F for the start (k = 0) and every iterate.
  *   iters_host NULL or the number of steps taken.
  * Single cells only (batch patterns give CQ_ERR_INVALID); FP64; scratch owned by the
- * context.  A non-finite residual gives CQ_ERR_NUMERIC.  Synchronises every step.
+ * context.  A non-finite residual gives CQ_ERR_NUMERIC.  After an error T holds an
+ * iterate of the run (possibly a partly applied step), not the start.  Synchronises every
+ * step.
  */
 cq_status cq_overlap_inverse_cg(cq_ctx *ctx, const cq_pattern *pS, const double *S,
                                 const cq_pattern *pT, double *T, int32_t max_iter,
