@@ -1,4 +1,4 @@
-"""Writes c1_reference.json: reference values of the 64-atom diamond Si cell (2x2x2
+"""Writes si64_reference.json: reference values of the 64-atom diamond Si cell (2x2x2
 conventional cells, a = 10.26 bohr, seeded 0.05-bohr jitter, sp basis, S/H cut at 10 bohr,
 L on 12 bohr) computed by the CPU oracle and, for the dense limit, by scipy.
 
@@ -8,7 +8,7 @@ counts (minimum-image pairs d^2 < R^2 plus self pairs), the Hotelling residuals
 ||S T - I||_F of ten steps from T_0 = I/sigma, the Palser-Manolopoulos start and twenty LNV
 steps at N_e = 256, and the dense-limit band energy 2 sum_occ eps of the generalised
 eigenproblem H c = eps S c.  Every value comes from oracle/ or scipy, never from the CUDA
-path.  Run from the repository root: python tests/golden/make_c1_reference.py
+path.  Run from the repository root: python tests/golden/make_si64_reference.py
 """
 import json
 import os
@@ -62,7 +62,7 @@ def compute():
 
 
 if __name__ == "__main__":
-    out = os.path.join(HERE, "c1_reference.json")
+    out = os.path.join(HERE, "si64_reference.json")
     with open(out, "w") as f:
         json.dump(compute(), f, indent=1)
     print("wrote", out)

@@ -1,6 +1,6 @@
 """The oracle against its stored reference values for the 64-atom Si cell (CPU).
 
-tests/golden/c1_reference.json was written by tests/golden/make_c1_reference.py from the
+tests/golden/si64_reference.json was written by tests/golden/make_si64_reference.py from the
 oracle and scipy alone.  Recomputing it must give the same pattern counts exactly and the
 same residuals, energies and step decisions to rounding, so an accidental change to the
 oracle's arithmetic shows up here.  The stored dense-limit band energy bounds the
@@ -14,9 +14,9 @@ import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.join(HERE, "golden"))
-import make_c1_reference as G  # noqa: E402
+import make_si64_reference as G  # noqa: E402
 
-REF = json.load(open(os.path.join(HERE, "golden", "c1_reference.json")))
+REF = json.load(open(os.path.join(HERE, "golden", "si64_reference.json")))
 
 
 @pytest.fixture(scope="module")

@@ -1,7 +1,7 @@
 """The whole CUDA pipeline against the stored oracle values of the 64-atom Si cell.
 
 Patterns, Hotelling inversion, Palser-Manolopoulos start and twenty LNV steps run on the
-GPU from the raw geometry; the results are compared with tests/golden/c1_reference.json,
+GPU from the raw geometry; the results are compared with tests/golden/si64_reference.json,
 written by the oracle alone (no oracle call at test time): exact pattern counts,
 residuals to 1e-10 relative, energies and electron counts to 1e-10 Ha/atom, and the same
 step decisions.
@@ -18,7 +18,7 @@ from paper_2205_08941_gb300 import inputs as I
 from helpers import gpu_pattern, upload_pairs
 
 pytestmark = pytest.mark.gpu
-REF = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c1_reference.json")))
+REF = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "si64_reference.json")))
 
 
 @pytest.fixture(scope="module")

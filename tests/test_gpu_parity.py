@@ -33,7 +33,7 @@ def ctx():
 
 
 @pytest.fixture(scope="module")
-def c1():
+def si64():
     cell = I.diamond_cell(2, a=10.26, sigma=0.05, seed=1, norb=4)
     S, H = I.overlap_hamiltonian(cell, I.silicon_model(10.0))
     return cell, S, H
@@ -64,8 +64,8 @@ class Both:
 # ------------------------------------------------------------------ A1 patterns
 
 @pytest.mark.parametrize("r", [0.0, 3.0, 10.0, 12.0, 16.5, 22.0, 32.0])
-def test_pattern_bitexact_c1(ctx, c1, r):
-    b = Both(ctx, c1[0], r)  # layout_index asserts row_ptr and col equal
+def test_pattern_bitexact_si64(ctx, si64, r):
+    b = Both(ctx, si64[0], r)  # layout_index asserts row_ptr and col equal
     rp, col, off, tr = b.g.export()
     tr = tr.cpu().numpy()
     assert np.array_equal(tr[tr], np.arange(b.o.nnzb))
@@ -90,8 +90,8 @@ def _random(cell, r, seed, sym=False):
 
 @pytest.mark.parametrize("ranges", [(12.0, 10.0, 22.0), (12.0, 10.0, 12.0), (22.0, 10.0, 32.0),
                                     (32.0, 22.0, 12.0), (6.0, 8.0, 5.0)])
-def test_bsmm_parity_c1(ctx, c1, ranges):
-    cell = c1[0]
+def test_bsmm_parity_si64(ctx, si64, ranges):
+    cell = si64[0]
     A_, B_, C_ = (Both(ctx, cell, r) for r in ranges)
     A = O.scatter(A_.o, _random(cell, ranges[0], 1))
     B = O.scatter(B_.o, _random(cell, ranges[1], 2))
@@ -134,8 +134,8 @@ def test_bsmm_szp_512_long_segments(ctx):
         assert_product_close(C_.o, C_.down(Cg), ref, scale, rows=rows)
 
 
-def test_bsmm_deterministic(ctx, c1):
-    cell = c1[0]
+def test_bsmm_deterministic(ctx, si64):
+    cell = si64[0]
     A_, B_, C_ = (Both(ctx, cell, r) for r in (12.0, 10.0, 22.0))
     A = A_.up(ctx, O.scatter(A_.o, _random(cell, 12.0, 1)))
     B = B_.up(ctx, O.scatter(B_.o, _random(cell, 10.0, 2)))
@@ -160,8 +160,8 @@ def test_trace_and_dot_parity(ctx):
 
 # ------------------------------------------------------------------ A4 Hotelling, A7
 
-def _setup_c1(ctx, c1, rl=12.0):
-    cell, Spb, Hpb = c1
+def _setup_si64(ctx, si64, rl=12.0):
+    cell, Spb, Hpb = si64
     pS, pL = Both(ctx, cell, 10.0), Both(ctx, cell, rl)
     S_o, H_o = O.scatter(pS.o, Spb), O.scatter(pS.o, Hpb)
     S_g, H_g = upload_pairs(ctx, pS.g, Spb), upload_pairs(ctx, pS.g, Hpb)
@@ -170,8 +170,8 @@ def _setup_c1(ctx, c1, rl=12.0):
 
 
 @pytest.mark.parametrize("rt", [12.0, 18.0])
-def test_hotelling_parity_c1(ctx, c1, rt):
-    cell, pS, pT, S_o, _, S_g, _ = _setup_c1(ctx, c1, rt)
+def test_hotelling_parity_si64(ctx, si64, rt):
+    cell, pS, pT, S_o, _, S_g, _ = _setup_si64(ctx, si64, rt)
     pV = O.Pattern.of_cell(cell, 10.0 + rt)
     T_o = O.hotelling_init(pS.o, S_o, pT.o)
     T_g = ctx.zeros(pT.g)
@@ -185,10 +185,10 @@ def test_hotelling_parity_c1(ctx, c1, rt):
     assert err.max() < 1e-12 * nrm.max()
 
 
-def test_overlap_inverse_cg_parity_c1(ctx, c1):
+def test_overlap_inverse_cg_parity_si64(ctx, si64):
     """Least-squares inverse on P_T by CG: residual and gradient histories and the final T
     against the oracle, from a symmetric start that does not commute with S."""
-    cell, pS, pT, S_o, _, S_g, _ = _setup_c1(ctx, c1, 12.0)
+    cell, pS, pT, S_o, _, S_g, _ = _setup_si64(ctx, si64, 12.0)
     pV = O.Pattern.of_cell(cell, 22.0)
     T0 = (O.hotelling_init(pS.o, S_o, pT.o)
           + 0.05 * O.scatter(pT.o, I.random_blocks(cell, 12.0, 31)))
@@ -207,8 +207,8 @@ def test_overlap_inverse_cg_parity_c1(ctx, c1):
     assert ctx.hotelling_step(pS.g, S_g, pT.g, T_g.clone()) == pytest.approx(r_g[-1], rel=1e-10)
 
 
-def test_pm_guess_and_mcweeny_parity_c1(ctx, c1):
-    cell, pS, pL, S_o, H_o, S_g, H_g = _setup_c1(ctx, c1, 12.0)
+def test_pm_guess_and_mcweeny_parity_si64(ctx, si64):
+    cell, pS, pL, S_o, H_o, S_g, H_g = _setup_si64(ctx, si64, 12.0)
     pX, pU, p2L = (O.Pattern.of_cell(cell, r) for r in (22.0, 32.0, 24.0))
     T_o = O.hotelling_init(pS.o, S_o, pL.o)
     T_g = ctx.zeros(pL.g)
@@ -229,8 +229,8 @@ def test_pm_guess_and_mcweeny_parity_c1(ctx, c1):
 
 # ------------------------------------------------------------------ A5/A6 LNV
 
-def test_lnv_parity_c1_20_steps(ctx, c1):
-    cell, pS, pL, S_o, H_o, S_g, H_g = _setup_c1(ctx, c1, 12.0)
+def test_lnv_parity_si64_20_steps(ctx, si64):
+    cell, pS, pL, S_o, H_o, S_g, H_g = _setup_si64(ctx, si64, 12.0)
     pX, pU = O.Pattern.of_cell(cell, 22.0), O.Pattern.of_cell(cell, 32.0)
     T_o = O.hotelling_init(pS.o, S_o, pL.o)
     for _ in range(10):
@@ -257,10 +257,10 @@ def test_lnv_parity_c1_20_steps(ctx, c1):
     assert err.max() < 1e-8 * nrm.max()
 
 
-def _lnv_pair_c1(ctx, c1):
+def _lnv_pair_si64(ctx, si64):
     """Oracle and GPU LNV objects on the 64-atom cell from the same PM start, with the
     Hotelling T (12 steps, on P_L) both sides precondition with."""
-    cell, pS, pL, S_o, H_o, S_g, H_g = _setup_c1(ctx, c1, 12.0)
+    cell, pS, pL, S_o, H_o, S_g, H_g = _setup_si64(ctx, si64, 12.0)
     pX, pU = O.Pattern.of_cell(cell, 22.0), O.Pattern.of_cell(cell, 32.0)
     T_o = O.hotelling_init(pS.o, S_o, pL.o)
     for _ in range(12):
@@ -272,11 +272,11 @@ def _lnv_pair_c1(ctx, c1):
     return cell, pS, pL, T_o, pL.up(ctx, T_o), lo, lg, L_g
 
 
-def test_preconditioned_lnv_parity_c1(ctx, c1):
+def test_preconditioned_lnv_parity_si64(ctx, si64):
     """Search directions from Z = sym(mask_L(T G T)): the GPU steps follow the oracle's
     step by step, and reach the 1e-8 RMS gradient in fewer steps than the plain gradient
     (Development Priorities: overlap inversion feeding the density-matrix minimisation)."""
-    cell, pS, pL, T_o, T_g, lo, lg, L_g = _lnv_pair_c1(ctx, c1)
+    cell, pS, pL, T_o, T_g, lo, lg, L_g = _lnv_pair_si64(ctx, si64)
     lo.set_preconditioner(pL.o, T_o, O.Pattern.of_cell(cell, 24.0))
     lg.set_preconditioner(pL.g, T_g)
     tol = 1e-10 * cell.n_atoms
@@ -303,19 +303,19 @@ def test_preconditioned_lnv_parity_c1(ctx, c1):
             k += 1
         return k
 
-    _, _, _, _, T2, _, pre, _ = _lnv_pair_c1(ctx, c1)
+    _, _, _, _, T2, _, pre, _ = _lnv_pair_si64(ctx, si64)
     pre.set_preconditioner(pL.g, T2)
-    _, _, _, _, _, _, plain, _ = _lnv_pair_c1(ctx, c1)
+    _, _, _, _, _, _, plain, _ = _lnv_pair_si64(ctx, si64)
     n_pre, n_plain = steps_to(pre), steps_to(plain)
     assert pre.state()["gnorm"] <= 1e-8 and plain.state()["gnorm"] <= 1e-8
     assert n_pre < n_plain, (n_pre, n_plain)
     assert pre.state()["energy"] == pytest.approx(plain.state()["energy"], abs=tol)
 
 
-def test_identity_preconditioner_gives_the_plain_steps_c1(ctx, c1):
-    cell, pS, pL, T_o, T_g, lo, lg, L_g = _lnv_pair_c1(ctx, c1)
+def test_identity_preconditioner_gives_the_plain_steps_si64(ctx, si64):
+    cell, pS, pL, T_o, T_g, lo, lg, L_g = _lnv_pair_si64(ctx, si64)
     ident = pL.up(ctx, O.identity(pL.o))
-    _, _, _, _, _, _, plain, _ = _lnv_pair_c1(ctx, c1)
+    _, _, _, _, _, _, plain, _ = _lnv_pair_si64(ctx, si64)
     lg.set_preconditioner(pL.g, ident)
     for k in range(6):
         a, b = plain.step(), lg.step()
@@ -331,8 +331,8 @@ def test_identity_preconditioner_gives_the_plain_steps_c1(ctx, c1):
 
 # ------------------------------------------------------------------ error paths
 
-def test_errors_are_reported_not_raised_on_device(ctx, c1):
-    cell = c1[0]
+def test_errors_are_reported_not_raised_on_device(ctx, si64):
+    cell = si64[0]
     p = gpu_pattern(ctx, cell, 5.0)
     pb = I.random_blocks(cell, 10.0, 1)
     with pytest.raises(cq.CQError) as e:

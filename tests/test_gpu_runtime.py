@@ -21,7 +21,7 @@ def built():
     build.build()
 
 
-def _c1_lnv(ctx, steps, graphs):
+def _si64_lnv(ctx, steps, graphs):
     cell = I.diamond_cell(2, a=10.26, sigma=0.05, seed=1, norb=4)
     Spb, Hpb = I.overlap_hamiltonian(cell, I.silicon_model(10.0))
     pS, pL = gpu_pattern(ctx, cell, 10.0), gpu_pattern(ctx, cell, 12.0)
@@ -45,8 +45,8 @@ def _c1_lnv(ctx, steps, graphs):
 def test_graph_replay_matches_eager_bitwise(built):
     a = cq.Context(0, stream=torch.cuda.Stream())
     b = cq.Context(0, stream=torch.cuda.Stream())
-    eager, _ = _c1_lnv(a, 6, False)
-    graphed, launches = _c1_lnv(b, 6, True)
+    eager, _ = _si64_lnv(a, 6, False)
+    graphed, launches = _si64_lnv(b, 6, True)
     for re, rg in zip(eager, graphed):
         assert re == rg
     assert launches > 0

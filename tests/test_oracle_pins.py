@@ -18,7 +18,7 @@ from paper_2205_08941_gb300 import inputs as I
 
 
 @pytest.fixture(scope="module")
-def c1():
+def si64():
     cell = I.diamond_cell(2, a=10.26, sigma=0.05, seed=1, norb=4)
     S, H = I.overlap_hamiltonian(cell, I.silicon_model(10.0))
     return cell, S, H
@@ -39,8 +39,8 @@ def _mask(p):
 # ------------------------------------------------------------------ patterns
 
 @pytest.mark.parametrize("r", [3.0, 10.0, 12.0, 16.5])
-def test_pattern_matches_periodic_kdtree(c1, r):
-    cell = c1[0]
+def test_pattern_matches_periodic_kdtree(si64, r):
+    cell = si64[0]
     p = O.Pattern.of_cell(cell, r)
     tree = cKDTree(cell.pos, boxsize=cell.box)
     pairs = tree.query_pairs(r, output_type="ndarray")
@@ -64,8 +64,8 @@ def test_pattern_count_closed_form():
         assert abs(per_atom - (rho * 4.0 / 3.0 * math.pi * r ** 3)) / per_atom < 0.1
 
 
-def test_pattern_self_only_and_dense(c1):
-    cell = c1[0]
+def test_pattern_self_only_and_dense(si64):
+    cell = si64[0]
     p0 = O.Pattern.of_cell(cell, 1e-3)
     assert p0.nnzb == cell.n_atoms and np.all(p0.row == p0.col)
     pd = O.Pattern.of_cell(cell, 18.0)  # beyond the largest minimum-image distance
@@ -75,8 +75,8 @@ def test_pattern_self_only_and_dense(c1):
 # ------------------------------------------------------------------ product
 
 @pytest.mark.parametrize("ranges", [(12.0, 10.0, 22.0), (12.0, 10.0, 12.0), (6.0, 8.0, 5.0)])
-def test_bsmm_is_dense_multiply_then_mask(c1, ranges):
-    cell = c1[0]
+def test_bsmm_is_dense_multiply_then_mask(si64, ranges):
+    cell = si64[0]
     ra, rb, rc = ranges
     pA, pB, pC = (O.Pattern.of_cell(cell, r) for r in ranges)
     A = O.scatter(pA, I.random_blocks(cell, ra, 1, symmetric=False))
@@ -127,8 +127,8 @@ def test_trace_and_gather(mixed):
 
 # ------------------------------------------------------------------ Hotelling
 
-def test_hotelling_residual_squares_and_limit(c1):
-    cell, Spb, _ = c1
+def test_hotelling_residual_squares_and_limit(si64):
+    cell, Spb, _ = si64
     pS = O.Pattern.of_cell(cell, 10.0)
     pT = O.Pattern.of_cell(cell, 18.0)   # dense T
     pV = O.Pattern.of_cell(cell, 28.0)
@@ -146,8 +146,8 @@ def test_hotelling_residual_squares_and_limit(c1):
     assert np.abs(O.to_dense(pT, T) - sl.inv(Sd)).max() < 1e-12
 
 
-def test_hotelling_sparse_converges(c1):
-    cell, Spb, _ = c1
+def test_hotelling_sparse_converges(si64):
+    cell, Spb, _ = si64
     pS, pT = O.Pattern.of_cell(cell, 10.0), O.Pattern.of_cell(cell, 12.0)
     pV = O.Pattern.of_cell(cell, 22.0)
     S = O.scatter(pS, Spb)
@@ -162,16 +162,16 @@ def test_hotelling_sparse_converges(c1):
 
 # ------------------------------------------------------------------ PM and McWeeny
 
-def _dense_setup(c1):
-    cell, Spb, Hpb = c1
+def _dense_setup(si64):
+    cell, Spb, Hpb = si64
     pS = O.Pattern.of_cell(cell, 10.0)
     pD = O.Pattern.of_cell(cell, 18.0)
     S, H = O.scatter(pS, Spb), O.scatter(pS, Hpb)
     return cell, pS, pD, S, H
 
 
-def test_pm_guess_trace_and_spectrum(c1):
-    cell, pS, pD, S, H = _dense_setup(c1)
+def test_pm_guess_trace_and_spectrum(si64):
+    cell, pS, pD, S, H = _dense_setup(si64)
     T = O.from_dense(pD, sl.inv(O.to_dense(pS, S)))
     L0 = O.pm_guess(pS, S, H, pD, T, pD, pD, 128.0)
     LS = O.to_dense(pD, L0) @ O.to_dense(pS, S)
@@ -180,8 +180,8 @@ def test_pm_guess_trace_and_spectrum(c1):
     assert ev.min() > -1e-10 and ev.max() < 1.0 + 1e-10
 
 
-def test_mcweeny_sparse_step_is_masked_formula(c1):
-    cell, Spb, _ = c1
+def test_mcweeny_sparse_step_is_masked_formula(si64):
+    cell, Spb, _ = si64
     pS, pL = O.Pattern.of_cell(cell, 10.0), O.Pattern.of_cell(cell, 7.0)
     pX, pU, p2L = (O.Pattern.of_cell(cell, r) for r in (17.0, 27.0, 14.0))
     S = O.scatter(pS, Spb)
@@ -192,8 +192,8 @@ def test_mcweeny_sparse_step_is_masked_formula(c1):
     assert np.abs(O.to_dense(pL, out) - ref).max() < 1e-13
 
 
-def test_mcweeny_purifies_to_idempotent(c1):
-    cell, pS, pD, S, H = _dense_setup(c1)
+def test_mcweeny_purifies_to_idempotent(si64):
+    cell, pS, pD, S, H = _dense_setup(si64)
     T = O.from_dense(pD, sl.inv(O.to_dense(pS, S)))
     L = O.pm_guess(pS, S, H, pD, T, pD, pD, 128.0)
     Sd = O.to_dense(pS, S)
@@ -209,16 +209,16 @@ def test_mcweeny_purifies_to_idempotent(c1):
 
 # ------------------------------------------------------------------ LNV
 
-def _lnv_setup(c1, rl=12.0):
-    cell, Spb, Hpb = c1
+def _lnv_setup(si64, rl=12.0):
+    cell, Spb, Hpb = si64
     pS, pL = O.Pattern.of_cell(cell, 10.0), O.Pattern.of_cell(cell, rl)
     pX, pU = O.Pattern.of_cell(cell, 10.0 + rl), O.Pattern.of_cell(cell, 20.0 + rl)
     S, H = O.scatter(pS, Spb), O.scatter(pS, Hpb)
     return cell, pS, pL, pX, pU, S, H
 
 
-def test_lnv_energy_number_match_dense(c1):
-    cell, pS, pL, pX, pU, S, H = _lnv_setup(c1)
+def test_lnv_energy_number_match_dense(si64):
+    cell, pS, pL, pX, pU, S, H = _lnv_setup(si64)
     L = O.scatter(pL, I.random_blocks(cell, 12.0, 21)) * 0.05
     lnv = O.LNV.__new__(O.LNV)
     lnv.pS, lnv.S, lnv.H, lnv.pL, lnv.pX, lnv.pU = pS, S, H, pL, pX, pU
@@ -229,8 +229,8 @@ def test_lnv_energy_number_match_dense(c1):
     assert N == pytest.approx(2 * np.trace(K @ Sd), rel=1e-12)
 
 
-def test_lnv_gradients_by_finite_differences(c1):
-    cell, pS, pL, pX, pU, S, H = _lnv_setup(c1, rl=8.0)
+def test_lnv_gradients_by_finite_differences(si64):
+    cell, pS, pL, pX, pU, S, H = _lnv_setup(si64, rl=8.0)
     L = O.scatter(pL, I.random_blocks(cell, 8.0, 31)) * 0.05
     lnv = O.LNV.__new__(O.LNV)
     lnv.pS, lnv.S, lnv.H, lnv.pL, lnv.pX, lnv.pU = pS, S, H, pL, pX, pU
@@ -247,8 +247,8 @@ def test_lnv_gradients_by_finite_differences(c1):
         assert O.dot(grad, Dl) == pytest.approx(fd, rel=1e-8)
 
 
-def test_lnv_line_is_exact_cubic(c1):
-    cell, pS, pL, pX, pU, S, H = _lnv_setup(c1)
+def test_lnv_line_is_exact_cubic(si64):
+    cell, pS, pL, pX, pU, S, H = _lnv_setup(si64)
     L = O.scatter(pL, I.random_blocks(cell, 12.0, 41)) * 0.05
     D = O.scatter(pL, I.random_blocks(cell, 12.0, 42)) * 0.05
     lnv = O.LNV.__new__(O.LNV)
@@ -278,8 +278,8 @@ def test_cubic_min_closed_form():
     assert (c2, c3) == (pytest.approx(3.0), pytest.approx(-0.5))
 
 
-def test_lnv_converges_to_ground_state_projector(c1):
-    cell, pS, pD, S, H = _dense_setup(c1)
+def test_lnv_converges_to_ground_state_projector(si64):
+    cell, pS, pD, S, H = _dense_setup(si64)
     pT = pD
     T = O.hotelling_init(pS, S, pT)
     for _ in range(10):
@@ -299,8 +299,8 @@ def test_lnv_converges_to_ground_state_projector(c1):
     assert np.abs(O.to_dense(pD, lnv.L) - P).max() < 1e-4
 
 
-def test_lnv_truncated_monotone(c1):
-    cell, pS, pL, pX, pU, S, H = _lnv_setup(c1)
+def test_lnv_truncated_monotone(si64):
+    cell, pS, pL, pX, pU, S, H = _lnv_setup(si64)
     pT = pL
     T = O.hotelling_init(pS, S, pT)
     for _ in range(10):
@@ -331,8 +331,8 @@ def test_fallback_step_is_bounded_by_the_rms_change_of_L():
 
 # ------------------------------------------------------------------ preconditioned LNV
 
-def _c1_start(c1):
-    cell, pS, pL, pX, pU, S, H = _lnv_setup(c1)
+def _si64_start(si64):
+    cell, pS, pL, pX, pU, S, H = _lnv_setup(si64)
     T = O.hotelling_init(pS, S, pL)
     for _ in range(12):
         T, _ = O.hotelling_step(pS, S, pL, T, pX)
@@ -348,8 +348,8 @@ def _steps_to(lnv, tol=1e-8, cap=80):
     return k
 
 
-def test_identity_preconditioner_reproduces_plain_steps(c1):
-    cell, pS, pL, pX, pU, S, H, T, L0 = _c1_start(c1)
+def test_identity_preconditioner_reproduces_plain_steps(si64):
+    cell, pS, pL, pX, pU, S, H, T, L0 = _si64_start(si64)
     plain = O.LNV(pS, S, H, pL, L0, 256.0, pX, pU)
     pre = O.LNV(pS, S, H, pL, L0, 256.0, pX, pU)
     pre.set_preconditioner(pL, O.identity(pL), O.Pattern.of_cell(cell, 24.0))
@@ -361,8 +361,8 @@ def test_identity_preconditioner_reproduces_plain_steps(c1):
                                                               a["n_corr"]), k
 
 
-def test_inverse_overlap_preconditioner_converges_in_fewer_steps(c1):
-    cell, pS, pL, pX, pU, S, H, T, L0 = _c1_start(c1)
+def test_inverse_overlap_preconditioner_converges_in_fewer_steps(si64):
+    cell, pS, pL, pX, pU, S, H, T, L0 = _si64_start(si64)
     plain = O.LNV(pS, S, H, pL, L0, 256.0, pX, pU)
     pre = O.LNV(pS, S, H, pL, L0, 256.0, pX, pU)
     pre.set_preconditioner(pL, T, O.Pattern.of_cell(cell, 24.0))
@@ -373,8 +373,8 @@ def test_inverse_overlap_preconditioner_converges_in_fewer_steps(c1):
     assert abs(pre.N - 256.0) < 1e-8
 
 
-def test_preconditioned_dense_limit_is_the_band_energy(c1):
-    cell, pS, pD, S, H = _dense_setup(c1)
+def test_preconditioned_dense_limit_is_the_band_energy(si64):
+    cell, pS, pD, S, H = _dense_setup(si64)
     T = O.from_dense(pD, np.linalg.inv(O.to_dense(pS, S)))
     L0 = O.pm_guess(pS, S, H, pD, T, pD, pD, 128.0)
     lnv = O.LNV(pS, S, H, pD, L0, 256.0, pD, pD)
@@ -414,8 +414,8 @@ def _best_sparse_inverse(pS, S, pT):
     return O.from_dense(pT, Td), float(np.linalg.norm(A @ t - y))
 
 
-def test_cg_inverse_reaches_the_least_squares_minimiser_on_p_t(c1):
-    cell, Spb, _ = c1
+def test_cg_inverse_reaches_the_least_squares_minimiser_on_p_t(si64):
+    cell, Spb, _ = si64
     pS, pT = O.Pattern.of_cell(cell, 10.0), O.Pattern.of_cell(cell, 5.0)  # nearest neighbours
     pV = O.Pattern.of_cell(cell, 15.0)
     S = O.scatter(pS, Spb)
@@ -434,8 +434,8 @@ def test_cg_inverse_reaches_the_least_squares_minimiser_on_p_t(c1):
     assert O.frob_minus_identity(pV, V) == pytest.approx(resid[-1], rel=1e-10)
 
 
-def test_cg_inverse_dense_limit_is_the_inverse(c1):
-    cell, Spb, _ = c1
+def test_cg_inverse_dense_limit_is_the_inverse(si64):
+    cell, Spb, _ = si64
     pS, pD = O.Pattern.of_cell(cell, 10.0), O.Pattern.of_cell(cell, 22.0)
     assert pD.nnzb == cell.n_atoms ** 2
     S = O.scatter(pS, Spb)
@@ -446,8 +446,8 @@ def test_cg_inverse_dense_limit_is_the_inverse(c1):
     assert resid[-1] <= 1e-11 * resid[0]
 
 
-def test_cg_inverse_beats_the_truncated_hotelling_fixed_point(c1):
-    cell, Spb, _ = c1
+def test_cg_inverse_beats_the_truncated_hotelling_fixed_point(si64):
+    cell, Spb, _ = si64
     pS, pT = O.Pattern.of_cell(cell, 10.0), O.Pattern.of_cell(cell, 12.0)
     pV = O.Pattern.of_cell(cell, 22.0)
     S = O.scatter(pS, Spb)
