@@ -94,6 +94,8 @@ def parse():
                     help="skip the FP64 leg (profiling the tensor-core path)")
     ap.add_argument("--hotelling-steps", type=int, default=12)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the split-vs-oracle check on the 512-atom SZP cell")
     ap.add_argument("--sweep", default=None,
                     help="comma-separated cells per edge (e.g. 4,6,8,10,12): seconds per LNV step "
                          "against atom count (linear scaling), split-BF16 at every size, FP64 "
@@ -288,6 +290,103 @@ def oracle_sample(cell, Spb, Hpb, stride=64, reps=1):
     return flops / min(times) / 1e9, times, flops, O.num_threads(), desc
 
 
+def oracle_sample_rows(cell, Spb, Hpb, stride):
+    """The oracle's five trial-evaluation products restricted to every `stride`-th output
+    atom row (all five, X and Y included): the same code and per-triplet work as
+    oracle_sample, in a sample small enough for one core.  Rows of X outside the sample
+    stay zero, which changes no operation count.  Returns (GFLOP/s, seconds, threads,
+    description)."""
+    import oracle as O
+    from paper_2205_08941_gb300 import inputs as I
+    rS, rL = WORKLOAD["r_S"], WORKLOAD["r_L"]
+    pS, pL = O.Pattern.of_cell(cell, rS), O.Pattern.of_cell(cell, rL)
+    pX, pU = O.Pattern.of_cell(cell, rL + rS), O.Pattern.of_cell(cell, 2 * rS + rL)
+    S, H = O.scatter(pS, Spb), O.scatter(pS, Hpb)
+    L = O.scatter(pL, I.random_blocks(cell, rL, 77)) * 0.01
+    rows = np.arange(0, cell.n_atoms, stride, dtype=np.int32)
+    flops = (O.triplets(pL, pS, pX, rows)[1] * 2 + O.triplets(pS, pX, pU, rows)[1]
+             + 2 * O.triplets(pU, pX, pL, rows)[1])
+    t0 = time.perf_counter()
+    X = O.bsmm(1.0, pL, L, pS, S, 0.0, pX, rows=rows)
+    Y = O.bsmm(1.0, pL, L, pS, H, 0.0, pX, rows=rows)
+    U = O.bsmm(1.0, pS, S, pX, X, 0.0, pU, rows=rows)
+    O.bsmm(1.0, pU, U, pX, Y, 0.0, pL, rows=rows)
+    O.bsmm(1.0, pU, U, pX, X, 0.0, pL, rows=rows)
+    sec = time.perf_counter() - t0
+    desc = (f"oracle products of one LNV trial evaluation (X=LS, Y=LH, U=SX, R1=UY, R3=UX) "
+            f"on {rows.shape[0]} of {cell.n_atoms} output atom rows ({flops / 1e9:.1f} GFLOP)")
+    return flops / sec / 1e9, sec, O.num_threads(), desc
+
+
+def cpu_one_core(ncell, stride=128):
+    """cpu_baseline on one host core: the oracle in a child process with OMP_NUM_THREADS=1
+    (its OpenMP pool is sized at start-up).  Returns a dict, or None if the child failed."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "c, s, h = bench.make_inputs(%d); "
+            "g, sec, th, d = bench.oracle_sample_rows(c, s, h, %d); "
+            "print(json.dumps([g, sec, th, d]))") % (ROOT, ncell, stride)
+    env = dict(os.environ, OMP_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                           text=True, timeout=600)
+        g, sec, th, d = json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+    return {"value": g, "unit": "GFLOP/s", "cores": th, "kind": "oracle", "sample": d,
+            "seconds": sec}
+
+
+def split_oracle_check(dev, steps=3):
+    """Split-BF16 LNV against the FP64 oracle on the 512-atom SZP cell (the benchmark's
+    recipe at 1/8 of the atoms, where the oracle runs LNV steps in seconds): both start from
+    the oracle's Palser-Manolopoulos L after eight Hotelling steps; after each step the
+    energy difference per atom and ||L - L_oracle|| / ||L_oracle||.  Returns a dict."""
+    import torch
+
+    import oracle as O
+    from paper_2205_08941_gb300 import cq
+    from paper_2205_08941_gb300 import inputs as I
+    rS, rL = WORKLOAD["r_S"], WORKLOAD["r_L"]
+    cell = I.diamond_cell(4, a=WORKLOAD["a_bohr"], sigma=WORKLOAD["sigma_bohr"],
+                          seed=WORKLOAD["seed"], norb=9)
+    Spb, Hpb = I.overlap_hamiltonian(cell, I.silicon_model(rS))
+    oS, oL = O.Pattern.of_cell(cell, rS), O.Pattern.of_cell(cell, rL)
+    oX, oU = O.Pattern.of_cell(cell, rL + rS), O.Pattern.of_cell(cell, 2 * rS + rL)
+    S_o, H_o = O.scatter(oS, Spb), O.scatter(oS, Hpb)
+    T_o = O.hotelling_init(oS, S_o, oL)
+    for _ in range(8):
+        T_o, _ = O.hotelling_step(oS, S_o, oL, T_o, oX)
+    n_e = 4.0 * cell.n_atoms
+    L0 = O.pm_guess(oS, S_o, H_o, oL, T_o, oX, oL, n_e / 2)
+    lo = O.LNV(oS, S_o, H_o, oL, L0, n_e, oX, oU)
+    ctx = cq.Context(dev)
+    t = lambda a, dt: torch.tensor(a, dtype=dt, device=f"cuda:{dev}")
+    pos, nb = t(cell.pos, torch.float64), t(cell.nb, torch.int32)
+    pS, pL = ctx.pattern(pos, cell.box, nb, rS), ctx.pattern(pos, cell.box, nb, rL)
+    up = lambda p, pb: ctx.scatter(p, t(pb.i, torch.int32), t(pb.j, torch.int32),
+                                   t(pb.off, torch.int64), t(pb.values, torch.float64))
+    S, H = up(pS, Spb), up(pS, Hpb)
+    # the same start on the GPU: oracle values placed block by block (same pattern order)
+    _, col, off, _ = pL.export()
+    sizes = np.diff(oL.off)
+    idx = np.repeat(off.cpu().numpy() - oL.off[:-1], sizes) + np.arange(int(oL.off[-1]))
+    idx = t(idx, torch.int64)
+    L = ctx.zeros(pL)
+    L[idx] = t(L0, torch.float64)
+    lg = ctx.lnv(pS, S, H, pL, L, n_e, prec=cq.CQ_SPLIT_BF16X3)
+    rows = []
+    for _ in range(steps):
+        ro, rg = lo.step(), lg.step()
+        Lg = L[idx].cpu().numpy()
+        rows.append({"energy_err_per_atom": abs(rg["energy"] - ro["E"]) / cell.n_atoms,
+                     "L_rel_err": float(np.linalg.norm(Lg - lo.L) / np.linalg.norm(lo.L))})
+    lg.close()
+    ctx.close()
+    return {"workload": workload_name(cell.n_atoms), "steps": steps, "per_step": rows,
+            "energy_err_per_atom": rows[-1]["energy_err_per_atom"],
+            "L_rel_err": rows[-1]["L_rel_err"]}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -391,17 +490,19 @@ def run_cq(args, rank, world, local_rank):
 
     e2e = None
     if not args.no_e2e and not args.only_split:
-        # end to end through the public API: each step copies the iterate L in from pinned
-        # host memory, runs cq_lnv_step, and reads L and the step's scalars back
+        # end to end through the public API over the same K steps from the same start L0:
+        # each step copies the iterate L in from pinned host memory, runs cq_lnv_step and
+        # reads L and the step's scalars back
+        L.copy_(L0)
+        lnv.set_precision(cq.CQ_FP64)  # the same fresh start as the timed FP64 steps
         L_host = torch.empty(L.shape, dtype=torch.float64, pin_memory=True)
         L_host.copy_(L)
         torch.cuda.synchronize()
-        k2 = max(1, min(args.steps, 2))
         e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         e2.record(stream)
         fl2 = 0.0
-        for _ in range(k2):
+        for _ in range(args.steps):
             L.copy_(L_host, non_blocking=True)
             r = lnv.step()
             L_host.copy_(L, non_blocking=True)
@@ -412,7 +513,8 @@ def run_cq(args, rank, world, local_rank):
         e2e = {"value": rep.sum(fl2) / (ms2 * 1e-3) / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": int(L.numel() * 8),
                "d2h_bytes_per_step": int(L.numel() * 8 + 96),
-               "ms_per_step": ms2 / k2}
+               "ms_per_step": ms2 / args.steps, "steps": args.steps,
+               "same_steps_as_value": True}
 
     split = None
     if not args.no_split:
@@ -444,6 +546,9 @@ def run_cq(args, rank, world, local_rank):
                          for x in r["reps"]]}
         split["roofline"]["frac"] = (split["roofline"]["achieved"] / split["roofline"]["peak"]
                                      if split["roofline"]["achieved"] else None)
+        # useful work at the method's own cost: six BF16 products per FP64-equivalent flop
+        uf = split["roofline"]["useful_tflops"]
+        split["roofline"]["useful_frac"] = (6.0 * uf / split["roofline"]["peak"]) if uf else None
         if "fp64" in res:
             E_split = r["reps"][-1]["energy"]
             split["energy_err_per_atom_vs_fp64"] = abs(E_split - E_fp64) / cell.n_atoms
@@ -459,7 +564,11 @@ def run_cq(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g, times, f, cores, desc = oracle_sample(cell, Spb, Hpb)
         cpu = {"value": g, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": desc, "seconds": min(times)}
+               "sample": desc, "seconds": min(times),
+               "one_core": cpu_one_core(args.ncell)}
+
+    if split is not None and rank == 0 and world == 1 and not args.no_oracle_check:
+        split["oracle_check"] = split_oracle_check(dev)
 
     if rank == 0:
         main = res.get("fp64") or res.get("split")
@@ -484,17 +593,20 @@ def run_cq(args, rank, world, local_rank):
                          "peak_source": "in-library FP64 probe (best of FMA and DMMA chains)",
                          "launches": n_launch, "kernel_ms": kern_ms,
                          "kernel_share": kern_ms / ms if ms > 0 else None},
-            "split": split,
+            "lnv": [{k: x[k] for k in ("energy", "n_elec", "gnorm", "alpha", "n_corr",
+                                       "n_products")} for x in main["reps"]],
             "batched": batched,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": main["clk"],
             "gpu_launches": int(main["launches"]),
-            "lnv": [{k: x[k] for k in ("energy", "n_elec", "gnorm", "alpha", "n_corr",
-                                       "n_products")} for x in main["reps"]],
         }
         if "fp64" not in res:
             line["roofline"] = split["roofline"]
+        if split is not None:
+            # last, and compact, so that a reader of the line's tail sees the mixed leg
+            split.pop("lnv", None)
+            line["split"] = split
         print(json.dumps(line), flush=True)
     lnv.close()
     ctx.close()

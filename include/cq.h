@@ -99,6 +99,13 @@ cq_status cq_ctx_set_autotune(cq_ctx *ctx, int on);
  * their second use and replayed afterwards, with identical results.  Needs a context on a
  * created stream (the legacy default stream cannot be captured): CQ_ERR_INVALID otherwise. */
 cq_status cq_ctx_set_graphs(cq_ctx *ctx, int on);
+/* Test hook for the error path of the tensor-core waits (0 = off, the default).  With
+ * cycles > 0 every later split-BF16 product kernel makes its first wait on a barrier that
+ * nothing completes, gives up after `cycles` clock cycles (at most 1e8) and takes the same
+ * path as a real timeout: the CTA stops issuing, retires the copies it issued (with the
+ * normal bounded wait), frees its tensor memory and returns; the next synchronising call
+ * returns CQ_ERR_TIMEOUT and C is incomplete.  Nothing waits without a bound. */
+cq_status cq_ctx_set_test_wait(cq_ctx *ctx, int64_t cycles);
 /* Lanes per C row the FP64 product of this triple uses, and whether the autotuner chose it. */
 cq_status cq_bsmm_config(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
                          const cq_pattern *pC, int32_t *lane_split_host, int32_t *tuned_host);
@@ -191,19 +198,22 @@ cq_status cq_trace_prod(cq_ctx *ctx, const cq_pattern *pA, const double *A,
 
 /*
  * Tr(A.B) as cq_trace_prod computes it, for callers that cannot allocate device memory when
- * they need it: code running while a stream capture is open (cudaMalloc is not allowed in a
- * global-mode capture), code whose device memory is owned by a framework with a fixed
- * budget, or callers that hold no context.  (The paper has no counterpart: this is an
- * interface variant, not part of the method.)
+ * they need it: code whose device memory is owned by a framework with a fixed budget that
+ * forbids raw cudaMalloc, latency-critical loops that must not pay for cudaMalloc (it can
+ * synchronise the device), or callers that hold no context (a pattern outlives the context
+ * that built it).  (The paper has no counterpart: this is an interface variant, not part of
+ * the method.)
  *
  * It allocates nothing: its scratch, one FP64 partial per atom row, is a file-scope
  * __device__ array of 65536 doubles (512 KiB) that every GPU loading the library keeps until
  * the process exits; no cudaMalloc, cudaFree or allocating library routine is called.
- * pA, A, pB, B are as for cq_trace_prod (existing patterns and values); out_dev is a device
- * pointer that receives the trace; cuda_stream is the stream to enqueue on (NULL: legacy
- * default stream).  The call is asynchronous: read out_dev after synchronising the stream.
- * Patterns of more than 65536 atoms are rejected with CQ_ERR_INVALID.  On error,
- * *message_host (if message_host is not NULL) points to a static description.
+ * pA, A, pB, B are as for cq_trace_prod (existing patterns and values); the work runs on
+ * the device the patterns were built on (both must be on the same one, else
+ * CQ_ERR_PATTERN).  out_dev is a device pointer that receives the trace; cuda_stream is
+ * the stream to enqueue on (NULL: legacy default stream).  The call is asynchronous: read
+ * out_dev after synchronising the stream.  Patterns of more than 65536 atoms are rejected
+ * with CQ_ERR_INVALID.  On error, *message_host (if message_host is not NULL) points to a
+ * static description.
  *
  * The first call on a device looks up the array's device address with that device current
  * (cudaGetSymbolAddress); make that first call before any stream capture.  Every call
@@ -247,7 +257,9 @@ cq_status cq_hotelling_step(cq_ctx *ctx, const cq_pattern *pS, const double *S,
  *   max_iter   step limit (>= 0); gtol: stop once ||G||_F <= gtol ||G_0||_F (>= 0).
  *   resid_host, gnorm_host  NULL or host arrays of max_iter + 1 doubles: ||I - S T_k||_F and
  *              ||G_k||_F for the start (k = 0) and every iterate.
- *   iters_host NULL or the number of steps taken.
+ *   iters_host NULL or the number of steps taken (history entries 0..*iters_host hold
+ *              values).  After an error it is the last step whose entries were written (-1:
+ *              none), so the caller knows which entries are valid.
  * Single cells only (batch patterns give CQ_ERR_INVALID); FP64; scratch owned by the
  * context.  A non-finite residual gives CQ_ERR_NUMERIC.  After an error T holds an
  * iterate of the run (possibly a partly applied step), not the start.  Synchronises every

@@ -104,6 +104,7 @@ SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_float), _vp, _vp]),
     "cq_guess_forward": (_st, [_vp, _vp, _i64, _vp]),
     "cq_guess_apply": (_st, [_vp, _vp, _vp]),
+    "cq_ctx_set_test_wait": (_st, [_vp, _i64]),
     "cq_trace_prod_static": (_st, [_vp, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.POINTER(ctypes.c_char_p)]),
 }
@@ -209,6 +210,10 @@ class Context:
 
     def set_autotune(self, on: bool):
         self._check(lib().cq_ctx_set_autotune(self.h, 1 if on else 0))
+
+    def set_test_wait(self, cycles: int):
+        """Test hook: split kernels make their first wait run out after `cycles` (0: off)."""
+        self._check(lib().cq_ctx_set_test_wait(self.h, int(cycles)))
 
     def set_graphs(self, on: bool):
         self._check(lib().cq_ctx_set_graphs(self.h, 1 if on else 0))

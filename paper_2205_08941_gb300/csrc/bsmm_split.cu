@@ -402,6 +402,7 @@ struct SplitArgs {
     int c_stride;
     double alpha, beta;
     int32_t *flag;
+    long long test_wait_cycles;  // > 0: test mode, the MMA thread's first wait runs out
 };
 
 #include "bsmm_split_kernel.cuh"
@@ -729,6 +730,7 @@ cq_status run_split(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double a
         a.alpha = alpha;
         a.beta = beta;
         a.flag = ctx->flag.as<int32_t>();
+        a.test_wait_cycles = ctx->test_wait_cycles;
         // this launch's share of the product's useful and tensor-core flops
         const double share =
             pl->n_chunks > 0 ? (double)pl->batch_chunks[q] / (double)pl->n_chunks : 0.0;

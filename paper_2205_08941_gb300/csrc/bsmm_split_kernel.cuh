@@ -24,6 +24,7 @@ constexpr int W_PROD = 0, W_MMA = 1;   // producer warp, MMA warp
 
 struct Bars {
     uint64_t full[NS], empty[NS], acc_full[NACC], acc_empty[NACC], done;
+    uint64_t never;  // no thread ever arrives here: the test-only wait on it must run out
     uint32_t tmem_slot;
     int abort_flag;
 };
@@ -50,6 +51,21 @@ __device__ __forceinline__ bool bar_wait(uint32_t addr, uint32_t parity, volatil
     while (!bar_try(addr, parity)) {
         if (*abort_flag) return false;
         if (clock64() - t0 > WAIT_CYCLES) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Bounded wait with its own limit in cycles (the test-only short wait).
+__device__ __forceinline__ bool bar_wait_for(uint32_t addr, uint32_t parity,
+                                             volatile int *abort_flag, long long limit)
+{
+    const long long t0 = clock64();
+    while (!bar_try(addr, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             return false;
         }
@@ -144,6 +160,7 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
                          "r"(N_DRAIN));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->done)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars->never)), "r"(1));
         bars->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -208,6 +225,12 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
         if (lane == 0) {
             uint32_t cg = 0, pg = 0;
             bool ok = true, issued = false;
+            // test mode: the first wait is on a barrier nothing completes, with a short limit,
+            // so it runs out; the CTA then takes the same abort path as a real timeout
+            if (p.test_wait_cycles > 0) {
+                bar_wait_for(smem_u32(&bars->never), 0u, abort_flag, p.test_wait_cycles);
+                ok = false;
+            }
             const int pq[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
             // descriptors of stage 0; a stage, plane or K step only moves the 14-bit start
             // address field (shared addresses stay below 256 KB, so no carry leaves it)

@@ -34,6 +34,8 @@ struct DevBuf {
 // Atom positions, box and basis shared by every pattern built on the same geometry.
 struct Geometry {
     uint64_t id = 0;
+    int device = 0;                 // CUDA device holding the pattern arrays (kept after the
+                                    // context is destroyed)
     int32_t n_atoms = 0;
     double box[3] = {0, 0, 0};
     std::vector<double> pos_host;   // n_atoms * 3
@@ -118,6 +120,7 @@ struct cq_ctx {
     bool graphs = false;             // replay LNV evaluation phases as CUDA graphs
     bool capturing = false;          // a graph capture is open on the stream
     uint64_t scratch_gen = 0;        // bumped whenever a scratch buffer is reallocated
+    int64_t test_wait_cycles = 0;    // > 0: split kernels make their first wait run out
 };
 
 // Record a timing event pair around a product launch when timing is on.

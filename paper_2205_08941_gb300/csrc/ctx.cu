@@ -287,10 +287,12 @@ extern "C" void cq_ctx_destroy(cq_ctx *ctx)
     ctx->derived.clear();
     for (cq_pattern *p : ctx->live_patterns) {
         p->ctx = nullptr;
-        for (DevBuf *b : {&p->row_ptr, &p->col, &p->row, &p->val_off, &p->transpose})
+        for (DevBuf *b : {&p->row_ptr, &p->col, &p->row, &p->val_off, &p->transpose,
+                          &p->seg_blk_dev, &p->seg_val_dev})
             b->ctx = nullptr;
-        p->geo->pos.ctx = nullptr;
-        p->geo->nb.ctx = nullptr;
+        for (DevBuf *b : {&p->geo->pos, &p->geo->nb, &p->geo->cell_of, &p->geo->boxes_dev,
+                          &p->geo->cell_start_dev})
+            b->ctx = nullptr;
     }
     ctx->tasks.clear();
     ctx->maps.clear();
@@ -337,6 +339,7 @@ extern "C" cq_status cq_pattern_build(cq_ctx *ctx, int32_t n_atoms, const double
             return cq_fail(ctx, CQ_ERR_INVALID, "pattern_build: box lengths must be > 0");
     auto geo = std::make_shared<Geometry>();
     geo->id = ctx->next_id++;
+    geo->device = ctx->device;
     geo->n_atoms = n_atoms;
     for (int c = 0; c < 3; ++c) geo->box[c] = box_host[c];
     geo->pos_host.resize((size_t)n_atoms * 3);
@@ -646,6 +649,13 @@ extern "C" cq_status cq_ctx_set_graphs(cq_ctx *ctx, int on)
         return cq_fail(ctx, CQ_ERR_INVALID,
                        "graphs need a context on a created stream (the default stream cannot be captured)");
     ctx->graphs = on != 0;
+    return CQ_OK;
+}
+
+extern "C" cq_status cq_ctx_set_test_wait(cq_ctx *ctx, int64_t cycles)
+{
+    if (!ctx || cycles < 0 || cycles > 100000000) return CQ_ERR_INVALID;
+    ctx->test_wait_cycles = cycles;
     return CQ_OK;
 }
 

@@ -139,6 +139,7 @@ extern "C" cq_status cq_overlap_inverse_cg(cq_ctx *ctx, const cq_pattern *pS, co
                                            int32_t *iters_host)
 {
     if (!ctx || !S || !T || max_iter < 0 || !(gtol >= 0.0)) return CQ_ERR_INVALID;
+    if (iters_host) *iters_host = -1;  // no history entry written yet
     CQ_TRY(same_ctx(ctx, pS, pT));
     if (pS->n_cells() != 1 || pT->n_cells() != 1)
         return cq_fail(ctx, CQ_ERR_INVALID, "overlap_inverse_cg: batch patterns not supported");
@@ -170,6 +171,7 @@ extern "C" cq_status cq_overlap_inverse_cg(cq_ctx *ctx, const cq_pattern *pS, co
         const double gn = std::sqrt(v[0]);
         if (resid_host) resid_host[k] = std::sqrt(v[1]);
         if (gnorm_host) gnorm_host[k] = gn;
+        if (iters_host) *iters_host = k;  // entries 0..k of the histories hold values
         if (k == 0) g0 = gn;
         if (k == max_iter || gn <= gtol * g0) break;
         CQ_TRY(cq_axpby(ctx, nT, -1.0, G, k == 0 ? 0.0 : v[0] / gg_prev, D));
@@ -185,7 +187,6 @@ extern "C" cq_status cq_overlap_inverse_cg(cq_ctx *ctx, const cq_pattern *pS, co
         CQ_TRY(cq_axpby(ctx, nV, -a, SD, 1.0, R));
         gg_prev = v[0];
     }
-    if (iters_host) *iters_host = k;
     return CQ_OK;
 }
 

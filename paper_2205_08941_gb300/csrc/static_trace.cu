@@ -1,21 +1,21 @@
 // Tr(A.B) without any device allocation.
 //
 // cq_trace_prod reduces through scratch that the context allocates on first use.  Some
-// callers cannot allocate device memory at the time they need a trace: code that runs while
-// a CUDA stream capture is open (cudaMalloc is not allowed inside a global-mode capture),
-// code whose device memory is owned by a host framework with a fixed budget that forbids
-// raw cudaMalloc, or callers that hold no context at all.  cq_trace_prod_static serves
-// them: its scratch -- one partial sum per atom row -- lives in a file-scope __device__
-// array of CQ_STATIC_TRACE_MAX_ROWS doubles (512 KiB) that every GPU which loads the library
-// keeps until the process exits.  It calls no cudaMalloc, cudaFree or allocating library
-// routine.
+// callers cannot allocate device memory at the time they need a trace: code whose device
+// memory is owned by a host framework with a fixed budget that forbids raw cudaMalloc,
+// latency-critical loops that must not pay for cudaMalloc (which can synchronise the
+// device), or callers that hold no context at all (patterns outlive the context that
+// built them).  cq_trace_prod_static serves them: its scratch -- one partial sum per atom
+// row -- lives in a file-scope __device__ array of CQ_STATIC_TRACE_MAX_ROWS doubles
+// (512 KiB) that every GPU which loads the library keeps until the process exits.  It calls
+// no cudaMalloc, cudaFree or allocating library routine.
 //
 // The caller passes patterns and values that already exist (patterns from cq_pattern_build
-// hold their index arrays on the device) and a device pointer for the result.  Every call
-// shares the one array, which keeps the last call's contents; each call overwrites the rows
-// it uses before reading them, so nothing needs clearing, but calls that overlap on the GPU
-// (on different streams, or from several host threads) race on the array and must be
-// serialised by the caller.
+// hold their index arrays on the device they were built on, which the pattern records) and
+// a device pointer for the result.  Every call shares the one array, which keeps the last
+// call's contents; each call overwrites the rows it uses before reading them, so nothing
+// needs clearing, but calls that overlap on the GPU (on different streams, or from several
+// host threads) race on the array and must be serialised by the caller.
 #include <cstring>
 #include <mutex>
 
@@ -102,7 +102,11 @@ extern "C" cq_status cq_trace_prod_static(const cq_pattern *pA, const double *A,
         return fail(CQ_ERR_INVALID,
                     "trace_prod_static: more than 65536 atoms (the static scratch holds one "
                     "partial per atom row); use cq_trace_prod");
-    const int device = pA->ctx ? pA->ctx->device : 0;
+    // the device the patterns were built on (recorded in their geometry, so it survives
+    // the destruction of the context that built them)
+    const int device = pA->geo->device;
+    if (pB->geo->device != device)
+        return fail(CQ_ERR_PATTERN, "trace_prod_static: patterns on different devices");
     if (device < 0 || device >= CQ_STATIC_TRACE_MAX_DEVICES)
         return fail(CQ_ERR_INVALID, "trace_prod_static: device ordinal beyond 63");
     int current = 0;

@@ -329,6 +329,28 @@ def test_identity_preconditioner_gives_the_plain_steps_si64(ctx, si64):
     assert e.value.status == 2
 
 
+def test_failed_preconditioner_set_leaves_the_plain_step_si64(ctx, si64):
+    """A set that fails (T on a pattern of another context) switches the preconditioner off
+    instead of leaving a half-updated one: the next step is the plain step from the same L,
+    although a valid, non-trivial T was set before."""
+    cell, pS, pL, T_o, T_g, lo, lg, L_g = _lnv_pair_si64(ctx, si64)
+    _, _, _, _, _, _, plain, _ = _lnv_pair_si64(ctx, si64)
+    lg.set_preconditioner(pL.g, T_g)
+    c2 = cq.Context(0)
+    try:
+        foreign = gpu_pattern(c2, cell, 12.0)
+        with pytest.raises(cq.CQError) as e:
+            lg.set_preconditioner(foreign, c2.zeros(foreign))
+        assert e.value.status == 2
+        a, b = plain.step(), lg.step()
+        assert b["energy"] == a["energy"] and b["alpha"] == a["alpha"], (a, b)
+        assert (b["restart"], b["fallback"], b["n_corr"]) == (a["restart"], a["fallback"],
+                                                              a["n_corr"])
+        assert b["flops"] == a["flops"]
+    finally:
+        c2.close()
+
+
 # ------------------------------------------------------------------ error paths
 
 def test_errors_are_reported_not_raised_on_device(ctx, si64):

@@ -182,3 +182,32 @@ def test_split_lnv_then_fp64_refinement(ctx):
         r = lg.step()
     assert abs(r["energy"] - E_ref) / cell.n_atoms < 1e-9
     assert abs(r["n_elec"] - 256.0) < 1e-7
+
+
+def test_timed_out_wait_is_reported_and_the_next_product_is_clean(ctx):
+    """The error path of the tensor-core waits, run for real: with the test hook on, every
+    split kernel's first wait is on a barrier that nothing completes and gives up after 2000
+    cycles; the CTA retires its issued copies, frees its tensor memory and returns, and the
+    next synchronising call reports CQ_ERR_TIMEOUT.  With the hook off again the same
+    product on the same context is correct."""
+    cell = I.diamond_cell(2, a=10.26, sigma=0.05, seed=1, norb=4)
+    A_, B_, C_ = (Both(ctx, cell, r) for r in (12.0, 10.0, 22.0))
+    A = O.scatter(A_.o, I.random_blocks(cell, 12.0, 1, symmetric=False))
+    B = O.scatter(B_.o, I.random_blocks(cell, 10.0, 2, symmetric=False))
+    Ag, Bg = A_.up(ctx, A), B_.up(ctx, B)
+    Cg = ctx.zeros(C_.g)
+    ctx.set_test_wait(2000)
+    try:
+        ctx.bsmm(1.0, A_.g, Ag, B_.g, Bg, 0.0, C_.g, Cg, prec=cq.CQ_SPLIT_BF16X3)
+        with pytest.raises(cq.CQError) as e:
+            ctx.sync()
+        assert e.value.status == 6, e.value
+    finally:
+        ctx.set_test_wait(0)
+    ctx.sync()  # the flag was cleared by the report
+    ctx.bsmm(1.0, A_.g, Ag, B_.g, Bg, 0.0, C_.g, Cg, prec=cq.CQ_SPLIT_BF16X3)
+    ctx.sync()
+    ref = O.bsmm(1.0, A_.o, A, B_.o, B, 0.0, C_.o)
+    err, _ = block_errors(C_.o, C_.down(Cg), ref)
+    scale = natural_scale(A_.o, A, B_.o, B, C_.o)
+    assert (err / np.maximum(scale, 1e-300)).max() <= 1e-5

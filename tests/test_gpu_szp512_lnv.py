@@ -1,0 +1,120 @@
+"""LNV on the benchmark's own basis against the oracle: the 512-atom Si SZP cell (4x4x4
+conventional cells, 9 orbitals per atom, seeded displacement 0.1 bohr, S and H cut at 14
+bohr, L on 16, X on 30, U on 44: the benchmark's 4096-atom recipe at 1/8 of the atoms).
+
+The oracle computes T ~ S^-1 (eight Hotelling steps on P_L), the Palser-Manolopoulos start
+and four LNV steps.  The CUDA path starts from the oracle's T and L0 (its own PM start is
+checked against the oracle's first) and runs the same four steps
+* in FP64: energy and electron count to 1e-10 Ha/atom at every step, identical restart,
+  fallback and electron-number-correction decisions, L per block to 1e-8 of the largest
+  block;
+* in split-BF16 (FP32-class products, about 1e-7 relative per block; the line search
+  and the trajectory amplify them): energy per atom within 2e-6 Ha and
+  ||L - L_oracle||_F / ||L_oracle||_F within 1e-4 of the oracle after every step.
+The measured split errors are printed (pytest -s) for the record.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2205_08941_gb300 import cq
+from paper_2205_08941_gb300 import inputs as I
+
+from helpers import block_errors, from_oracle, gpu_pattern, layout_index, to_oracle, upload_pairs
+
+pytestmark = pytest.mark.gpu
+STEPS = 4
+
+
+class Both:
+    def __init__(self, ctx, cell, r):
+        self.o = O.Pattern.of_cell(cell, r)
+        self.g = gpu_pattern(ctx, cell, r)
+        self.idx = layout_index(self.g, self.o)
+
+    def up(self, ctx, vals):
+        return from_oracle(ctx, self.g, self.idx, vals)
+
+    def down(self, t):
+        return to_oracle(t, self.idx)
+
+
+@pytest.fixture(scope="module")
+def szp512():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_08941_gb300 import build
+    build.build()
+    ctx = cq.Context(0)
+    cell = I.diamond_cell(4, a=10.26, sigma=0.1, seed=2, norb=9)
+    Spb, Hpb = I.overlap_hamiltonian(cell, I.silicon_model(14.0))
+    pS, pL = Both(ctx, cell, 14.0), Both(ctx, cell, 16.0)
+    pX, pU = O.Pattern.of_cell(cell, 30.0), O.Pattern.of_cell(cell, 44.0)
+    S_o, H_o = O.scatter(pS.o, Spb), O.scatter(pS.o, Hpb)
+    T_o = O.hotelling_init(pS.o, S_o, pL.o)
+    for _ in range(8):
+        T_o, _ = O.hotelling_step(pS.o, S_o, pL.o, T_o, pX)
+    n_e = 4.0 * cell.n_atoms
+    L0 = O.pm_guess(pS.o, S_o, H_o, pL.o, T_o, pX, pL.o, n_e / 2)
+    lo = O.LNV(pS.o, S_o, H_o, pL.o, L0, n_e, pX, pU)
+    traj = [dict(E=lo.E, N=lo.N, n_corr=lo.n_corrections_initial, L=lo.L.copy())]
+    for _ in range(STEPS):
+        r = lo.step()
+        traj.append(dict(r, L=lo.L.copy()))
+    S_g, H_g = upload_pairs(ctx, pS.g, Spb), upload_pairs(ctx, pS.g, Hpb)
+    yield dict(ctx=ctx, cell=cell, pS=pS, pL=pL, S_o=S_o, H_o=H_o, T_o=T_o, L0=L0,
+               traj=traj, S_g=S_g, H_g=H_g, n_e=n_e)
+    ctx.close()
+
+
+def test_szp512_pm_start_matches_the_oracle(szp512):
+    d = szp512
+    ctx, pS, pL = d["ctx"], d["pS"], d["pL"]
+    T_g = pL.up(ctx, d["T_o"])
+    L_g = ctx.zeros(pL.g)
+    ctx.pm_guess(pS.g, d["S_g"], d["H_g"], pL.g, T_g, pL.g, L_g, d["n_e"] / 2)
+    err, nrm = block_errors(pL.o, pL.down(L_g), d["L0"])
+    assert err.max() < 1e-12 * nrm.max(), err.max() / nrm.max()
+
+
+def test_szp512_fp64_lnv_steps_match_the_oracle(szp512):
+    d = szp512
+    ctx, pS, pL, cell, traj = d["ctx"], d["pS"], d["pL"], d["cell"], d["traj"]
+    L_g = pL.up(ctx, d["L0"])
+    lg = ctx.lnv(pS.g, d["S_g"], d["H_g"], pL.g, L_g, d["n_e"])
+    tol = 1e-10 * cell.n_atoms
+    st = lg.state()
+    assert st["energy"] == pytest.approx(traj[0]["E"], abs=tol)
+    assert st["n_elec"] == pytest.approx(traj[0]["N"], abs=tol)
+    assert st["n_corr"] == traj[0]["n_corr"]
+    for k in range(1, STEPS + 1):
+        rg, ro = lg.step(), traj[k]
+        assert rg["energy"] == pytest.approx(ro["E"], abs=tol), k
+        assert rg["n_elec"] == pytest.approx(ro["N"], abs=tol), k
+        assert (rg["restart"], rg["fallback"], rg["n_corr"]) == (
+            int(ro["restart"]), int(ro["fallback"]), ro["n_corr"]), k
+        assert rg["gnorm"] == pytest.approx(ro["gnorm"], rel=1e-5, abs=1e-9), k
+        err, nrm = block_errors(pL.o, pL.down(L_g), ro["L"])
+        assert err.max() < 1e-8 * nrm.max(), (k, err.max() / nrm.max())
+    lg.close()
+
+
+def test_szp512_split_lnv_steps_track_the_oracle(szp512):
+    d = szp512
+    ctx, pS, pL, cell, traj = d["ctx"], d["pS"], d["pL"], d["cell"], d["traj"]
+    L_g = pL.up(ctx, d["L0"])
+    lg = ctx.lnv(pS.g, d["S_g"], d["H_g"], pL.g, L_g, d["n_e"], prec=cq.CQ_SPLIT_BF16X3)
+    worst_e, worst_l = 0.0, 0.0
+    for k in range(1, STEPS + 1):
+        rg, ro = lg.step(), traj[k]
+        e_atom = abs(rg["energy"] - ro["E"]) / cell.n_atoms
+        Lk = pL.down(L_g)
+        l_rel = np.linalg.norm(Lk - ro["L"]) / np.linalg.norm(ro["L"])
+        print(f"split step {k}: |E - E_oracle| = {e_atom:.2e} Ha/atom, "
+              f"||L - L_oracle|| / ||L_oracle|| = {l_rel:.2e}, n_corr {rg['n_corr']} "
+              f"(oracle {ro['n_corr']})")
+        worst_e, worst_l = max(worst_e, e_atom), max(worst_l, l_rel)
+        assert e_atom < 2e-6, (k, e_atom)
+        assert l_rel < 1e-4, (k, l_rel)
+    lg.close()

@@ -88,3 +88,39 @@ def test_network_gradients_by_finite_differences():
         bm[idx] -= h
         fd = (G.loss_and_grads(w, bp, X, T, *args)[0] - G.loss_and_grads(w, bm, X, T, *args)[0]) / (2 * h)
         assert gb[idx] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_descriptor_values_of_a_hand_computed_four_atom_case():
+    """Descriptor of pair (0, 1) in a four-atom cluster whose values are fixed by hand.
+
+    Atoms (box 60 bohr, so no periodic image is within the 10-bohr pattern): 0 at the
+    origin, 1 at 4 along z, 2 at (3.2, 0, 2) and 3 at (0, 4.8 s, 2 + 4.8 s), s = 1/sqrt(2).
+    Bond midpoint m = (0, 0, 2): atom 2 sits 3.2 from m along +x (it fixes e1 = x), atom 3
+    sits 4.8 from m along (0, s, s).  So the frame is the identity and the neighbour terms
+    need only exact values: the cosine cut at 8 bohr is (1 + cos(0.4 pi))/2 = (3 + sqrt5)/8
+    at 3.2 and (5 - sqrt5)/8 at 4.8; the radial Gaussians (width 1.2, centres 1.6 n) take
+    the values 1, exp(-8/9), exp(-32/9), exp(-8) at 0, 1, 2, 3 centre spacings; the harmonics
+    (1, z, x, y, (3z^2-1)/2, xz, yz, (x^2-y^2)/2, xy) are (1, 0, 1, 0, -1/2, 0, 0, 1/2, 0)
+    along x and (1, s, 0, s, 1/4, 0, 1/2, -1/4, 0) along (0, s, s).  The pair part: ten
+    Gaussians of r = 4 (width 1.6, centres 1.6 q): exp(-t^2/2) with t = 2.5, 1.5, 0.5,
+    -0.5, ..., -5.5."""
+    s = 1.0 / np.sqrt(2.0)
+    o = np.array([20.0, 20.0, 20.0])
+    pos = np.array([[0, 0, 0], [0, 0, 4.0], [3.2, 0, 2.0], [0, 4.8 * s, 2.0 + 4.8 * s]]) + o
+    cell = I.Cell(pos=pos, box=np.array([60.0, 60.0, 60.0]), nb=np.full(4, 9, np.int32))
+    p = O.Pattern.of_cell(cell, 10.0)
+    b = int(O.block_index(p, 0, 1))
+    F, f = G.frame_and_descriptor(p, b)
+    assert np.allclose(F, np.eye(3), atol=1e-12)
+    expect = np.zeros(64)
+    for q in range(10):
+        expect[q] = np.exp(-0.5 * (2.5 - q) ** 2)
+    g = {0: 1.0, 1: np.exp(-8.0 / 9.0), 2: np.exp(-32.0 / 9.0), 3: np.exp(-8.0)}
+    fc2, fc3 = (3.0 + np.sqrt(5.0)) / 8.0, (5.0 - np.sqrt(5.0)) / 8.0
+    ang2 = np.array([1, 0, 1, 0, -0.5, 0, 0, 0.5, 0])
+    ang3 = np.array([1, s, 0, s, 0.25, 0, 0.5, -0.25, 0])
+    for n in range(6):
+        h2 = g[abs(n - 2)] * fc2      # atom 2 sits at centre n = 2
+        h3 = g[abs(n - 3)] * fc3      # atom 3 sits at centre n = 3
+        expect[10 + 9 * n:19 + 9 * n] = h2 * ang2 + h3 * ang3
+    assert np.allclose(f, expect, rtol=0, atol=1e-13), np.nonzero(~np.isclose(f, expect))

@@ -329,6 +329,40 @@ def test_fallback_step_is_bounded_by_the_rms_change_of_L():
     assert O.fallback_alpha(small, D.size, dd) == 2.0 * small
 
 
+def test_fallback_step_lowers_omega_where_the_cubic_has_no_minimiser(si64):
+    """What the capped fallback step is for.  From L = 3 L_PM, far outside idempotency, the
+    exact cubic of Omega = E - mu N along the first search direction has no positive
+    minimiser (Omega falls without bound along D), so the step takes the fallback.  Checked
+    on dense matrices, independent of the oracle's sparse products: Omega falls without
+    bound along D, the capped step lowers it monotonically over its whole length, and the
+    cap is the active limit (an RMS change of L of exactly 0.01, shorter than 2 a2)."""
+    cell, pS, pL, pX, pU, S, H, T, L0 = _si64_start(si64)
+    lnv = O.LNV(pS, S, H, pL, 3.0 * L0, 256.0, pX, pU, max_corr=0)
+    Lstart = lnv.L.copy()
+    mu, _ = lnv.mu_and_g()
+    rec = lnv.step()
+    assert rec["fallback"]
+    D, alpha = lnv.D_prev, rec["alpha"]
+    Sd, Hd = O.to_dense(pS, S), O.to_dense(pS, H)
+
+    def omega(a):
+        Ld = O.to_dense(pL, Lstart + a * D)
+        LS = Ld @ Sd
+        K = 3.0 * LS @ Ld - 2.0 * LS @ LS @ Ld
+        return 2.0 * np.trace(K @ Hd) - mu * 2.0 * np.trace(K @ Sd)
+
+    # no minimiser: Omega keeps falling far beyond the step
+    far = [omega(a) for a in (0.0, alpha, 4.0 * alpha, 16.0 * alpha, 64.0 * alpha)]
+    assert all(b < a for a, b in zip(far, far[1:])), far
+    # the capped step lowers Omega at every point along it
+    along = [omega(t * alpha) for t in np.linspace(0.0, 1.0, 6)]
+    assert all(b < a for a, b in zip(along, along[1:])), along
+    # the cap, not 2 a2, fixed the length: RMS change of L = 0.01 over its stored values
+    assert alpha < 2.0 * (2.0 * rec["a1"])
+    assert np.sqrt(np.mean((alpha * D) ** 2)) == pytest.approx(0.01, rel=1e-12)
+    assert np.allclose(lnv.L, Lstart + alpha * D, rtol=0, atol=1e-15)
+
+
 # ------------------------------------------------------------------ preconditioned LNV
 
 def _si64_start(si64):
