@@ -35,6 +35,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <numeric>
 
 #include "cq_internal.cuh"
@@ -433,6 +434,19 @@ struct SplitPlan {
     DevBuf ga_index, hb_index;  // block of every (slot, K-group atom) pair of every entry
 };
 
+// L2 budget (bytes) for the A panels of one band of M groups; CQ_SPLIT_BAND_MB overrides
+// the default for tuning sweeps.
+int64_t split_band_budget()
+{
+    static int64_t v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("CQ_SPLIT_BAND_MB");
+        const double mb = e ? std::atof(e) : 40.0;
+        v = (int64_t)(std::max(0.0, mb) * (1 << 20));
+    }
+    return v;
+}
+
 // Morton order of the atoms (positions quantised to 1024 per box edge).
 std::vector<int32_t> spatial_order(const Geometry &g)
 {
@@ -580,7 +594,6 @@ cq_status get_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
         if (bits[b >> 5] & (1u << (b & 31)))
             tiles.push_back(make_int2((int)(b / gr->n_h), (int)(b % gr->n_h)));
     pl->n_tiles = (int)tiles.size();
-    if ((st = upload(ctx, pl->tiles, tiles.data(), sizeof(int2) * tiles.size())) != CQ_OK) return st;
     // K-group lists of the M groups (rows of P_A) and of the N groups (rows of P_B)
     std::vector<int64_t> ga_host, hb_host;
     if ((st = group_lists(ctx, gr, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA, pl->ga_ptr,
@@ -588,6 +601,48 @@ cq_status get_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
         (st = group_lists(ctx, gr, gr->n_h, gr->gj, gr->h_atoms.as<int32_t>(), pB, pl->hb_ptr,
                           pl->hb_kappa, pl->hb_group, hb_host)) != CQ_OK)
         return st;
+    // batches of whole M groups (tiles are sorted by g) whose A panels fit A_PANEL_CAP
+    {
+        const int64_t cap = std::max<int64_t>(1, (int64_t)(A_PANEL_CAP / A_CHUNK));
+        int t0 = 0;
+        while (t0 < pl->n_tiles) {
+            const int g0 = tiles[t0].x;
+            int t1 = t0, g1 = g0;
+            while (t1 < pl->n_tiles) {
+                const int g = tiles[t1].x;
+                if (g != g1) {  // the next M group starts; keep it only if its panels still fit
+                    if (ga_host[g + 1] - ga_host[g0] > cap) break;
+                    g1 = g;
+                }
+                ++t1;
+            }
+            pl->batches.push_back({t0, t1, ga_host[g0], ga_host[g1 + 1]});
+            t0 = t1;
+        }
+    }
+    // Tile order for L2 reuse.  Within a batch, consecutive M groups form bands whose A
+    // panels fit an L2 budget; a band's tiles run ordered by (N group, M group), so the
+    // CTAs in flight share the band's A panels and each N group's B panels while both are
+    // still in L2 (g-major order would re-read every B panel from HBM for each M group).
+    {
+        const int64_t budget = split_band_budget() / A_CHUNK;
+        for (const Batch &bt : pl->batches) {
+            int t0 = bt.tile0;
+            while (t0 < bt.tile1) {
+                const int g0 = tiles[t0].x;
+                int t1 = t0;
+                while (t1 < bt.tile1 &&
+                       (tiles[t1].x == g0 || ga_host[tiles[t1].x + 1] - ga_host[g0] <= budget))
+                    ++t1;
+                std::stable_sort(tiles.begin() + t0, tiles.begin() + t1,
+                                 [](const int2 &a, const int2 &b) {
+                                     return a.y != b.y ? a.y < b.y : a.x < b.x;
+                                 });
+                t0 = t1;
+            }
+        }
+    }
+    if ((st = upload(ctx, pl->tiles, tiles.data(), sizeof(int2) * tiles.size())) != CQ_OK) return st;
     pl->n_ga = ga_host[gr->n_g];
     pl->n_hb = hb_host[gr->n_h];
     if ((st = cq_alloc(ctx, pl->ga_index, 4 * ((size_t)pl->n_ga * gr->gi * gr->ca + 1))) != CQ_OK ||
@@ -654,24 +709,7 @@ cq_status get_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
         pl->cidx.as<int32_t>());
     cq_count_launch(3);
     if ((st = cq_check_cuda(ctx, cudaGetLastError(), "split plan")) != CQ_OK) return st;
-    // batches of whole M groups (tiles are sorted by g) whose A panels fit A_PANEL_CAP
-    const int64_t cap = std::max<int64_t>(1, (int64_t)(A_PANEL_CAP / A_CHUNK));
-    int t0 = 0;
-    while (t0 < pl->n_tiles) {
-        const int g0 = tiles[t0].x;
-        int t1 = t0, g1 = g0;
-        while (t1 < pl->n_tiles) {
-            const int g = tiles[t1].x;
-            if (g != g1) {  // the next M group starts; keep it only if its panels still fit
-                if (ga_host[g + 1] - ga_host[g0] > cap) break;
-                g1 = g;
-            }
-            ++t1;
-        }
-        pl->batches.push_back({t0, t1, ga_host[g0], ga_host[g1 + 1]});
-        pl->batch_chunks.push_back(ks[t1] - ks[t0]);
-        t0 = t1;
-    }
+    for (const Batch &bt : pl->batches) pl->batch_chunks.push_back(ks[bt.tile1] - ks[bt.tile0]);
     *out = pl.get();
     ctx->aux[key] = pl;
     return CQ_OK;
