@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libcq.so")
 CQ_OK = 0
 CQ_FP64 = 0
 CQ_SPLIT_BF16X3 = 1
+CQ_FP64_EMU = 2
 STATUS = {0: "CQ_OK", 1: "CQ_ERR_INVALID", 2: "CQ_ERR_PATTERN", 3: "CQ_ERR_NOMEM",
           4: "CQ_ERR_CUDA", 5: "CQ_ERR_NUMERIC", 6: "CQ_ERR_TIMEOUT", 7: "CQ_ERR_NOT_CONVERGED"}
 

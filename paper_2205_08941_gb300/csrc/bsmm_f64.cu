@@ -260,6 +260,13 @@ cq_status cq_bsmm_f64(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pa
                       const cq_pattern *pC, double *C)
 {
     if (tl->n_c == 0) return CQ_OK;
+    if (!tl->filled) {
+        if (ctx->capturing)
+            return cq_fail(ctx, CQ_ERR_INVALID,
+                           "bsmm: first FP64 product of a triple inside a graph capture");
+        cq_status st = cq_fill_tasks(ctx, pA, pB, pC, const_cast<TaskList *>(tl));
+        if (st != CQ_OK) return st;
+    }
     if (ctx->autotune && tl->q == 0 && !ctx->capturing) {
         cq_status st = tune_q(ctx, tl, pA, A, pB, B, pC);
         if (st != CQ_OK) return st;

@@ -35,10 +35,10 @@
 
 #include <algorithm>
 #include <cmath>
-#include <cstdlib>
 #include <numeric>
 
 #include "cq_internal.cuh"
+#include "digits7.cuh"
 #include "split3.cuh"
 
 namespace {
@@ -407,8 +407,192 @@ struct SplitArgs {
 };
 
 #include "bsmm_split_kernel.cuh"
+#include "bsmm_emu_kernel.cuh"
 
-constexpr int SMEM = NS * STAGE + BAR_BYTES;  // pipeline stages + barriers
+constexpr int SMEM = NS * STAGE + BAR_BYTES;     // pipeline stages + barriers
+constexpr int SMEM_E = NSE * E_STAGE + BAR_BYTES;
+
+// ---------------------------------------------------------------- emulated-FP64 packing
+
+// Byte offset of (row, core-matrix column col of the chunk's K layout, digit plane) in an
+// emulated-FP64 panel: K step col / 2, then the plane, then the canonical no-swizzle
+// K-major image of rows x 16 K (core matrices adjacent along K, 8-row groups 256 B apart).
+__device__ __forceinline__ uint32_t emu_off(int rows, int row, int col, int plane)
+{
+    return (uint32_t)((col >> 1) * EMU_P * rows * 32 + plane * rows * 32 + (row >> 3) * E_SBO +
+                      (col & 1) * 128 + (row & 7) * 16);
+}
+
+// Largest exponent (digits7_exponent) of every scalar row of every A panel entry (one CTA
+// of 128 threads per entry = (M group, K group)): row r = (slot r / NB, orbital r % NB).
+template <int NB>
+__global__ void __launch_bounds__(MT)
+k_emu_rowexp_a(const int32_t *index, const double *__restrict__ A, int stride, int16_t *out)
+{
+    constexpr int GI = MT / NB, CA = KLayout<NB>::CA;
+    const int64_t e = blockIdx.x;
+    const int r = threadIdx.x;
+    int m = EMU_NONE;
+    if (r < GI * NB) {
+        const int32_t *blk = index + e * (GI * CA) + (r / NB) * CA;
+        const int o = r % NB;
+        for (int a = 0; a < CA; ++a) {
+            const int64_t b = __ldg(&blk[a]);
+            if (b < 0) continue;
+            for (int k = 0; k < NB; ++k) m = max(m, digits7_exponent(A[b * stride + o * NB + k]));
+        }
+    }
+    out[e * MT + r] = (int16_t)m;
+}
+
+// The same for every scalar column of every B panel entry (one CTA of 64 threads per entry
+// = (N group, K group)): column c = (slot c / NB, orbital o); values B_kj[m][o].
+template <int NB>
+__global__ void __launch_bounds__(NT)
+k_emu_rowexp_b(const int32_t *index, const double *__restrict__ B, int stride, int16_t *out)
+{
+    constexpr int GJ = NT / NB, CA = KLayout<NB>::CA;
+    const int64_t e = blockIdx.x;
+    const int c = threadIdx.x;
+    int m = EMU_NONE;
+    if (c < GJ * NB) {
+        const int32_t *blk = index + e * (GJ * CA) + (c / NB) * CA;
+        const int o = c % NB;
+        for (int a = 0; a < CA; ++a) {
+            const int64_t b = __ldg(&blk[a]);
+            if (b < 0) continue;
+            for (int k = 0; k < NB; ++k) m = max(m, digits7_exponent(B[b * stride + k * NB + o]));
+        }
+    }
+    out[e * NT + c] = (int16_t)m;
+}
+
+// Group exponent of every (entry, row): the largest row exponent over the entries of the
+// same atom group whose K groups share a scale group (K group >> 2).  The entries of a
+// group are sorted by K group, so those entries are adjacent.
+__global__ void k_emu_group_scale(int width, const int64_t *ptr, const int32_t *kappa,
+                                  const int32_t *group, const int16_t *rowexp, int16_t *scale)
+{
+    const int64_t e = blockIdx.x;
+    const int r = threadIdx.x;
+    const int g = group[e], sg = kappa[e] >> 2;
+    int64_t lo = e, hi = e + 1;
+    while (lo > ptr[g] && (kappa[lo - 1] >> 2) == sg) --lo;
+    while (hi < ptr[g + 1] && (kappa[hi] >> 2) == sg) ++hi;
+    int m = EMU_NONE;
+    for (int64_t f = lo; f < hi; ++f) m = max(m, (int)rowexp[f * width + r]);
+    scale[e * width + r] = (int16_t)m;
+}
+
+// Seven digit planes of n (<= 8) values as seven 16-byte core-matrix rows (one per plane,
+// two BF16 per word, values beyond n zero).
+__device__ __forceinline__ void emu_rows(const double *x, int n, int E, uint4 (&w)[EMU_P])
+{
+    uint32_t u[EMU_P][4];
+#pragma unroll
+    for (int p = 0; p < EMU_P; ++p)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) u[p][k] = 0u;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if (v >= n) break;
+        __nv_bfloat16 d[EMU_P];
+        digits7(x[v], E, d);
+#pragma unroll
+        for (int p = 0; p < EMU_P; ++p)
+            u[p][v >> 1] |= (uint32_t)__bfloat16_as_ushort(d[p]) << (16 * (v & 1));
+    }
+#pragma unroll
+    for (int p = 0; p < EMU_P; ++p) w[p] = make_uint4(u[p][0], u[p][1], u[p][2], u[p][3]);
+}
+
+// One row of the K pieces of a pair of atoms (a0 even, a0 + 1) of an emulated panel: the
+// two main pieces (8 values each) and the core column the two tails (4 values each) share.
+template <int NB>
+__device__ __forceinline__ void put_pair_emu(uint8_t *panel, int rows, int r, int a0, int E,
+                                             const double (&x0)[KLayout<NB>::MAINW + TAILW],
+                                             const double (&x1)[KLayout<NB>::MAINW + TAILW])
+{
+    constexpr int MW = KLayout<NB>::MAINW;
+    uint4 w[EMU_P];
+    if (MW) {
+        emu_rows(x0, MW, E, w);
+#pragma unroll
+        for (int p = 0; p < EMU_P; ++p)
+            *reinterpret_cast<uint4 *>(panel + emu_off(rows, r, KLayout<NB>::main_col(a0), p)) = w[p];
+        emu_rows(x1, MW, E, w);
+#pragma unroll
+        for (int p = 0; p < EMU_P; ++p)
+            *reinterpret_cast<uint4 *>(panel + emu_off(rows, r, KLayout<NB>::main_col(a0 + 1), p)) =
+                w[p];
+    }
+    double t[8];
+#pragma unroll
+    for (int m = 0; m < TAILW; ++m) {
+        t[m] = x0[MW + m];
+        t[TAILW + m] = x1[MW + m];
+    }
+    emu_rows(t, 8, E, w);
+#pragma unroll
+    for (int p = 0; p < EMU_P; ++p)
+        *reinterpret_cast<uint4 *>(panel + emu_off(rows, r, KLayout<NB>::tail_col(a0), p)) = w[p];
+}
+
+// Emulated A panels of entries [e0, e0 + gridDim.x): as k_pack_a, seven digit planes per
+// value against the (entry, row) group exponent.
+template <int NB>
+__global__ void __launch_bounds__(256)
+k_pack_a_emu(int64_t e0, const int32_t *index, const int16_t *scale, const double *__restrict__ A,
+             int stride, uint8_t *panels)
+{
+    constexpr int GI = MT / NB, CA = KLayout<NB>::CA, KA = KLayout<NB>::MAINW + TAILW;
+    const int64_t e = e0 + blockIdx.x;
+    const int32_t *blk = index + e * (GI * CA);
+    uint8_t *panel = panels + (int64_t)blockIdx.x * E_APANEL;
+    for (int q = threadIdx.x; q < MT * (CA / 2); q += blockDim.x) {
+        const int a0 = 2 * (q / MT), r = q % MT;
+        const bool row = r < GI * NB;
+        const int64_t b0 = row ? __ldg(&blk[(r / NB) * CA + a0]) : -1;
+        const int64_t b1 = row ? __ldg(&blk[(r / NB) * CA + a0 + 1]) : -1;
+        const int E = row ? (int)scale[e * MT + r] : EMU_NONE;
+        const int o = r % NB;
+        double x0[KA], x1[KA];
+#pragma unroll
+        for (int m = 0; m < KA; ++m) {
+            x0[m] = (b0 >= 0 && m < NB) ? A[b0 * stride + o * NB + m] : 0.0;
+            x1[m] = (b1 >= 0 && m < NB) ? A[b1 * stride + o * NB + m] : 0.0;
+        }
+        put_pair_emu<NB>(panel, MT, r, a0, E, x0, x1);
+    }
+}
+
+// Emulated B panels (one CTA per entry): row r of the panel = column of C; K = (atom,
+// orbital m): B_kj[m][o], against the (entry, column) group exponent.
+template <int NB>
+__global__ void __launch_bounds__(256)
+k_pack_b_emu(const int32_t *index, const int16_t *scale, const double *__restrict__ B, int stride,
+             uint8_t *panels)
+{
+    constexpr int GJ = NT / NB, CA = KLayout<NB>::CA, KA = KLayout<NB>::MAINW + TAILW;
+    const int64_t e = blockIdx.x;
+    const int32_t *blk = index + e * (GJ * CA);
+    uint8_t *panel = panels + e * E_BPANEL;
+    for (int q = threadIdx.x; q < NT * (CA / 2); q += blockDim.x) {
+        const int a0 = 2 * (q / NT), r = q % NT;
+        const bool row = r < GJ * NB;
+        const int64_t b0 = row ? __ldg(&blk[(r / NB) * CA + a0]) : -1;
+        const int64_t b1 = row ? __ldg(&blk[(r / NB) * CA + a0 + 1]) : -1;
+        const int E = row ? (int)scale[e * NT + r] : EMU_NONE;
+        const int o = r % NB;
+        double x0[KA], x1[KA];
+#pragma unroll
+        for (int m = 0; m < KA; ++m) {
+            x0[m] = (b0 >= 0 && m < NB) ? B[b0 * stride + m * NB + o] : 0.0;
+            x1[m] = (b1 >= 0 && m < NB) ? B[b1 * stride + m * NB + o] : 0.0;
+        }
+        put_pair_emu<NB>(panel, NT, r, a0, E, x0, x1);
+    }
+}
 
 // ---------------------------------------------------------------- host side
 
@@ -433,19 +617,6 @@ struct SplitPlan {
     DevBuf ga_ptr, ga_kappa, ga_group, hb_ptr, hb_kappa, hb_group;
     DevBuf ga_index, hb_index;  // block of every (slot, K-group atom) pair of every entry
 };
-
-// L2 budget (bytes) for the A panels of one band of M groups; CQ_SPLIT_BAND_MB overrides
-// the default for tuning sweeps.
-int64_t split_band_budget()
-{
-    static int64_t v = -1;
-    if (v < 0) {
-        const char *e = std::getenv("CQ_SPLIT_BAND_MB");
-        const double mb = e ? std::atof(e) : 40.0;
-        v = (int64_t)(std::max(0.0, mb) * (1 << 20));
-    }
-    return v;
-}
 
 // Morton order of the atoms (positions quantised to 1024 per box edge).
 std::vector<int32_t> spatial_order(const Geometry &g)
@@ -620,28 +791,6 @@ cq_status get_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
             t0 = t1;
         }
     }
-    // Tile order for L2 reuse.  Within a batch, consecutive M groups form bands whose A
-    // panels fit an L2 budget; a band's tiles run ordered by (N group, M group), so the
-    // CTAs in flight share the band's A panels and each N group's B panels while both are
-    // still in L2 (g-major order would re-read every B panel from HBM for each M group).
-    {
-        const int64_t budget = split_band_budget() / A_CHUNK;
-        for (const Batch &bt : pl->batches) {
-            int t0 = bt.tile0;
-            while (t0 < bt.tile1) {
-                const int g0 = tiles[t0].x;
-                int t1 = t0;
-                while (t1 < bt.tile1 &&
-                       (tiles[t1].x == g0 || ga_host[tiles[t1].x + 1] - ga_host[g0] <= budget))
-                    ++t1;
-                std::stable_sort(tiles.begin() + t0, tiles.begin() + t1,
-                                 [](const int2 &a, const int2 &b) {
-                                     return a.y != b.y ? a.y < b.y : a.x < b.x;
-                                 });
-                t0 = t1;
-            }
-        }
-    }
     if ((st = upload(ctx, pl->tiles, tiles.data(), sizeof(int2) * tiles.size())) != CQ_OK) return st;
     pl->n_ga = ga_host[gr->n_g];
     pl->n_hb = hb_host[gr->n_h];
@@ -782,7 +931,115 @@ cq_status run_split(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double a
     return CQ_OK;
 }
 
+template <int NB>
+cq_status run_emu(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double alpha,
+                  const cq_pattern *pA, const double *A, const cq_pattern *pB, const double *B,
+                  double beta, const cq_pattern *pC, double *C, double flops)
+{
+    cudaStream_t s = ctx->stream;
+    cq_status st;
+    size_t a_bytes = 0;
+    for (const Batch &b : pl->batches) a_bytes = std::max(a_bytes, (size_t)(b.e1 - b.e0) * E_APANEL);
+    void *va, *vb, *ra, *sa, *rb, *sb;
+    if ((st = cq_scratch(ctx, "emu_A", a_bytes, &va)) != CQ_OK ||
+        (st = cq_scratch(ctx, "emu_B", (size_t)pl->n_hb * E_BPANEL, &vb)) != CQ_OK ||
+        (st = cq_scratch(ctx, "emu_ra", 2 * (size_t)pl->n_ga * MT + 2, &ra)) != CQ_OK ||
+        (st = cq_scratch(ctx, "emu_sa", 2 * (size_t)pl->n_ga * MT + 2, &sa)) != CQ_OK ||
+        (st = cq_scratch(ctx, "emu_rb", 2 * (size_t)pl->n_hb * NT + 2, &rb)) != CQ_OK ||
+        (st = cq_scratch(ctx, "emu_sb", 2 * (size_t)pl->n_hb * NT + 2, &sb)) != CQ_OK)
+        return st;
+    // the shared-memory limit is a per-device attribute: set it once per device
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cq_fail(ctx, CQ_ERR_INVALID, "emulated product: device index");
+    if (!attr_set[dev]) {
+        if ((st = cq_check_cuda(ctx, cudaFuncSetAttribute(k_bsmm_emu<9>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          SMEM_E), "emu attribute")) != CQ_OK ||
+            (st = cq_check_cuda(ctx, cudaFuncSetAttribute(k_bsmm_emu<4>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          SMEM_E), "emu attribute")) != CQ_OK)
+            return st;
+        attr_set[dev] = true;
+    }
+    // group exponents and digit planes of B, then of A (all entries: a scale group's
+    // entries may fall in different packing batches)
+    if (pl->n_hb > 0) {
+        k_emu_rowexp_b<NB><<<(unsigned)pl->n_hb, NT, 0, s>>>(pl->hb_index.as<int32_t>(), B,
+                                                              pB->uniform, (int16_t *)rb);
+        k_emu_group_scale<<<(unsigned)pl->n_hb, NT, 0, s>>>(
+            NT, pl->hb_ptr.as<int64_t>(), pl->hb_kappa.as<int32_t>(), pl->hb_group.as<int32_t>(),
+            (const int16_t *)rb, (int16_t *)sb);
+        k_pack_b_emu<NB><<<(unsigned)pl->n_hb, 256, 0, s>>>(
+            pl->hb_index.as<int32_t>(), (const int16_t *)sb, B, pB->uniform, (uint8_t *)vb);
+        cq_count_launch(3);
+    }
+    if (pl->n_ga > 0) {
+        k_emu_rowexp_a<NB><<<(unsigned)pl->n_ga, MT, 0, s>>>(pl->ga_index.as<int32_t>(), A,
+                                                              pA->uniform, (int16_t *)ra);
+        k_emu_group_scale<<<(unsigned)pl->n_ga, MT, 0, s>>>(
+            MT, pl->ga_ptr.as<int64_t>(), pl->ga_kappa.as<int32_t>(), pl->ga_group.as<int32_t>(),
+            (const int16_t *)ra, (int16_t *)sa);
+        cq_count_launch(2);
+    }
+    const double mma_flops = (double)pl->n_chunks * KSTEPS * E_MMAS * 2.0 * MT * NT * 16;
+    for (size_t q = 0; q < pl->batches.size(); ++q) {
+        const Batch &b = pl->batches[q];
+        if (b.e1 > b.e0) {
+            k_pack_a_emu<NB><<<(unsigned)(b.e1 - b.e0), 256, 0, s>>>(
+                b.e0, pl->ga_index.as<int32_t>(), (const int16_t *)sa, A, pA->uniform,
+                (uint8_t *)va);
+            cq_count_launch();
+        }
+        EmuArgs a;
+        a.n_tiles = b.tile1 - b.tile0;
+        a.kstart = pl->kstart.as<int64_t>() + b.tile0;
+        a.chunks = pl->chunks.as<int2>();
+        a.kappa = pl->tile_kappa.as<int32_t>();
+        a.cidx = pl->cidx.as<int32_t>() + (int64_t)b.tile0 * gr->gi * gr->gj;
+        a.panel_a = (const uint8_t *)va;
+        a.ea0 = b.e0;
+        a.panel_b = (const uint8_t *)vb;
+        a.scale_a = (const int16_t *)sa;
+        a.scale_b = (const int16_t *)sb;
+        a.C = C;
+        a.c_stride = pC->uniform;
+        a.alpha = alpha;
+        a.beta = beta;
+        a.flag = ctx->flag.as<int32_t>();
+        const double share =
+            pl->n_chunks > 0 ? (double)pl->batch_chunks[q] / (double)pl->n_chunks : 0.0;
+        const int grid = std::min(a.n_tiles, ctx->num_sms);
+        cq_timing_begin(ctx, flops * share, mma_flops * share);
+        k_bsmm_emu<NB><<<grid, ST, SMEM_E, s>>>(a);
+        cq_timing_end(ctx);
+        cq_count_launch();
+        if ((st = cq_check_cuda(ctx, cudaGetLastError(), "bsmm_emu")) != CQ_OK) return st;
+    }
+    return CQ_OK;
+}
+
 }  // namespace
+
+cq_status cq_bsmm_emu(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pattern *pA,
+                      const double *A, const cq_pattern *pB, const double *B, double beta,
+                      const cq_pattern *pC, double *C)
+{
+    const int nb = pC->geo->uniform_nb;
+    if (nb != 9 && nb != 4)
+        return cq_fail(ctx, CQ_ERR_INVALID,
+                       "emulated-FP64 product: needs a uniform basis of 4 or 9 orbitals per atom");
+    if (pC->n_blocks == 0) return CQ_OK;
+    Groups *gr;
+    SplitPlan *pl;
+    cq_status st = get_groups(ctx, pC, &gr);
+    if (st != CQ_OK) return st;
+    if ((st = get_plan(ctx, pA, pB, pC, gr, &pl)) != CQ_OK) return st;
+    if (pl->n_tiles == 0) return CQ_OK;
+    return nb == 9 ? run_emu<9>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops)
+                   : run_emu<4>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops);
+}
 
 cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pattern *pA,
                         const double *A, const cq_pattern *pB, const double *B, double beta,

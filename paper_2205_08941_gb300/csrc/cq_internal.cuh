@@ -58,7 +58,8 @@ struct TaskList {
     int64_t n_tasks = 0;
     double flops = 0.0;
     DevBuf seg;     // int64 [n_c + 1]
-    DevBuf tasks;   // int2  [n_tasks]: (A block, B block)
+    DevBuf tasks;   // int2  [n_tasks]: (A block, B block), filled on first FP64 use
+    bool filled = false;
     DevBuf c_rowitem;  // int64 [n_c + 1] prefix of n_i over C blocks (bases other than 4, 9)
     int64_t n_items = 0;  // scalar C rows (sum of n_i over C blocks)
     mutable int q = 0;    // lanes per C row of the FP64 kernel chosen by the autotuner (0: none)
@@ -151,6 +152,9 @@ bool cq_same_atoms(const cq_pattern *a, const cq_pattern *b);
 // ---------------------------------------------------------------- tasks (tasks.cu)
 cq_status cq_get_tasks(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
                        const cq_pattern *pC, TaskList **out);
+// Fill the (A block, B block) pairs of a counted task list (first FP64 product on it).
+cq_status cq_fill_tasks(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
+                        const cq_pattern *pC, TaskList *tl);
 // Map from the blocks of pDst to the blocks of pSrc holding (i, j) (or (j, i) when
 // transpose), -1 when absent.  Cached in the context.
 cq_status cq_get_map(cq_ctx *ctx, const cq_pattern *pSrc, const cq_pattern *pDst,
@@ -166,6 +170,9 @@ int cq_lane_split(const TaskList *tl);
 cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pattern *pA,
                         const double *A, const cq_pattern *pB, const double *B, double beta,
                         const cq_pattern *pC, double *C);
+cq_status cq_bsmm_emu(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pattern *pA,
+                      const double *A, const cq_pattern *pB, const double *B, double beta,
+                      const cq_pattern *pC, double *C);
 
 // ---------------------------------------------------------------- reductions (reduce.cu)
 // All scalar results land in ctx->red_out[slot] on the device; cq_fetch copies them out.

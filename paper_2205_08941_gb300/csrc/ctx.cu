@@ -549,11 +549,12 @@ extern "C" cq_status cq_bsmm(cq_ctx *ctx, double alpha, const cq_pattern *pA, co
         return cq_fail(ctx, CQ_ERR_INVALID, "bsmm: C aliases an operand");
     if (!std::isfinite(alpha) || !std::isfinite(beta))
         return cq_fail(ctx, CQ_ERR_INVALID, "bsmm: non-finite alpha/beta");
-    if (prec != CQ_FP64 && prec != CQ_SPLIT_BF16X3)
+    if (prec != CQ_FP64 && prec != CQ_SPLIT_BF16X3 && prec != CQ_FP64_EMU)
         return cq_fail(ctx, CQ_ERR_INVALID, "bsmm: unknown precision");
     TaskList *tl = nullptr;
     if ((st = cq_get_tasks(ctx, pA, pB, pC, &tl)) != CQ_OK) return st;
     if (prec == CQ_FP64) return cq_bsmm_f64(ctx, tl, alpha, pA, A, pB, B, beta, pC, C);
+    if (prec == CQ_FP64_EMU) return cq_bsmm_emu(ctx, tl, alpha, pA, A, pB, B, beta, pC, C);
     return cq_bsmm_split(ctx, tl, alpha, pA, A, pB, B, beta, pC, C);
 }
 

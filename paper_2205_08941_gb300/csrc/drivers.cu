@@ -31,6 +31,7 @@ cq_status bsmm(cq_ctx *ctx, double alpha, const cq_pattern *pA, const double *A,
     if (st != CQ_OK) return st;
     if (flops) *flops += tl->flops;
     if (prec == CQ_FP64) return cq_bsmm_f64(ctx, tl, alpha, pA, A, pB, B, beta, pC, C);
+    if (prec == CQ_FP64_EMU) return cq_bsmm_emu(ctx, tl, alpha, pA, A, pB, B, beta, pC, C);
     return cq_bsmm_split(ctx, tl, alpha, pA, A, pB, B, beta, pC, C);
 }
 
@@ -562,7 +563,7 @@ extern "C" cq_status cq_lnv_create_cells(cq_ctx *ctx, const cq_pattern *pS, cons
     for (int c = 0; c < nc; ++c)
         if (!(n_electrons_host[c] > 0.0 && n_electrons_host[c] < 2.0 * (double)pS->geo->cell_orb[c]))
             return cq_fail(ctx, CQ_ERR_INVALID, "lnv_create: electron count outside (0, 2N)");
-    if (prec != CQ_FP64 && prec != CQ_SPLIT_BF16X3)
+    if (prec != CQ_FP64 && prec != CQ_SPLIT_BF16X3 && prec != CQ_FP64_EMU)
         return cq_fail(ctx, CQ_ERR_INVALID, "lnv_create: unknown precision");
     std::unique_ptr<cq_lnv> s(new cq_lnv());
     s->ctx = ctx;
@@ -734,7 +735,7 @@ extern "C" cq_status cq_lnv_step(cq_lnv *s, cq_lnv_report *rep)
 extern "C" cq_status cq_lnv_set_precision(cq_lnv *s, cq_precision prec)
 {
     if (!s || !s->ctx) return CQ_ERR_INVALID;
-    if (prec != CQ_FP64 && prec != CQ_SPLIT_BF16X3)
+    if (prec != CQ_FP64 && prec != CQ_SPLIT_BF16X3 && prec != CQ_FP64_EMU)
         return cq_fail(s->ctx, CQ_ERR_INVALID, "lnv_set_precision: unknown precision");
     s->prec = prec;
     s->have_prev = false;

@@ -154,15 +154,9 @@ cq_status cq_get_tasks(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
     if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "task count")) != CQ_OK) return st;
     tl->n_tasks = tot[0];
     tl->flops = (double)tot[1];
-    if ((st = cq_alloc(ctx, tl->tasks, sizeof(int2) * (tl->n_tasks + 1))) != CQ_OK) return st;
-    if (n_c > 0) {
-        k_task_fill<<<grid, 256, 0, s>>>(n_c, pC->row.as<int32_t>(), pC->col.as<int32_t>(),
-                                         pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
-                                         pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(),
-                                         pB->transpose.as<int64_t>(), tl->seg.as<int64_t>(),
-                                         tl->tasks.as<int2>());
-        cq_count_launch();
-    }
+    // the (A block, B block) pairs themselves are filled on the first FP64 product
+    // (cq_fill_tasks): tensor-core products need only the counts, and the pairs of the long
+    // products are the largest scratch of all (8 bytes per triplet)
     const int nbu = pC->geo->uniform_nb;
     if (nbu == 9 || nbu == 4) {
         tl->n_items = n_c * nbu;
@@ -183,6 +177,25 @@ cq_status cq_get_tasks(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
     if ((st = cq_check_cuda(ctx, cudaGetLastError(), "task build")) != CQ_OK) return st;
     *out = tl.get();
     ctx->tasks[key] = std::move(tl);
+    return CQ_OK;
+}
+
+cq_status cq_fill_tasks(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
+                        const cq_pattern *pC, TaskList *tl)
+{
+    if (tl->filled) return CQ_OK;
+    cq_status st;
+    if ((st = cq_alloc(ctx, tl->tasks, sizeof(int2) * (tl->n_tasks + 1))) != CQ_OK) return st;
+    const int64_t n_c = tl->n_c;
+    if (n_c > 0) {
+        k_task_fill<<<(unsigned)((n_c + 7) / 8), 256, 0, ctx->stream>>>(
+            n_c, pC->row.as<int32_t>(), pC->col.as<int32_t>(), pA->row_ptr.as<int64_t>(),
+            pA->col.as<int32_t>(), pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(),
+            pB->transpose.as<int64_t>(), tl->seg.as<int64_t>(), tl->tasks.as<int2>());
+        cq_count_launch();
+    }
+    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "task fill")) != CQ_OK) return st;
+    tl->filled = true;
     return CQ_OK;
 }
 

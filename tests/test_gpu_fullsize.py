@@ -6,8 +6,9 @@ The product types of the LNV evaluation in the benchmark's launch configuration:
 P_X (short segments), X.X on P_L (the long-segment regime of the R products, whose k-sums
 run over ~800 blocks), and the two 44-bohr products that dominate the step: S.X on P_U
 (r_U = 44, 10.5M output blocks) and U.Y back onto P_L, with U the oracle's S.X on the
-sampled rows (zero elsewhere: a C row of U.Y needs only the same row of U).  FP64 to the product tolerance of the other parity tests;
-split-BF16 to its error model (per block <= 1e-5 of sum_k ||A_ik|| ||B_kj||, RMS <= 1e-6).
+sampled rows (zero elsewhere: a C row of U.Y needs only the same row of U).  FP64 and
+emulated FP64 to the product tolerance of the other parity tests; split-BF16 to its error
+model (per block <= 1e-5 of sum_k ||A_ik|| ||B_kj||, RMS <= 1e-6).
 """
 import numpy as np
 import pytest
@@ -61,7 +62,7 @@ def _check(data, ra, rb, rc, prec):
     ctx.bsmm(1.0, A_.g, dev[ra], B_.g, dev[rb], 0.0, C_.g, Cg, prec=prec)
     got = C_.down(Cg)
     scale = natural_scale(A_.o, vals[ra], B_.o, vals[rb], C_.o, rows=ROWS)
-    if prec == cq.CQ_FP64:
+    if prec in (cq.CQ_FP64, cq.CQ_FP64_EMU):
         assert_product_close(C_.o, got, ref, scale, rows=ROWS)
         return
     err, _ = block_errors(C_.o, got, ref)
@@ -71,12 +72,12 @@ def _check(data, ra, rb, rc, prec):
     assert np.sqrt(np.mean(rel ** 2)) <= 1e-6, np.sqrt(np.mean(rel ** 2))
 
 
-@pytest.mark.parametrize("prec", [cq.CQ_FP64, cq.CQ_SPLIT_BF16X3])
+@pytest.mark.parametrize("prec", [cq.CQ_FP64, cq.CQ_SPLIT_BF16X3, cq.CQ_FP64_EMU])
 def test_fullsize_l_times_s_on_p_x(data, prec):
     _check(data, 16.0, 14.0, 30.0, prec)
 
 
-@pytest.mark.parametrize("prec", [cq.CQ_FP64, cq.CQ_SPLIT_BF16X3])
+@pytest.mark.parametrize("prec", [cq.CQ_FP64, cq.CQ_SPLIT_BF16X3, cq.CQ_FP64_EMU])
 def test_fullsize_x_times_x_on_p_l(data, prec):
     _check(data, 30.0, 30.0, 16.0, prec)
 
@@ -125,7 +126,7 @@ def _compare_rows(pC, sel_blocks, sizes, got, ref, scale, prec):
     err = np.sqrt(np.bincount(blk, weights=(got - ref) ** 2, minlength=len(sel_blocks)))
     nrm = np.sqrt(np.bincount(blk, weights=ref ** 2, minlength=len(sel_blocks)))
     sc = scale[sel_blocks]
-    if prec == cq.CQ_FP64:
+    if prec in (cq.CQ_FP64, cq.CQ_FP64_EMU):
         bound = 1e-12 * np.maximum(nrm, 1e-3 * sc)
         bad = np.nonzero(err > bound)[0]
         assert bad.size == 0, (bad[:5], err[bad[:5]], bound[bad[:5]])
@@ -146,7 +147,7 @@ def u_data(data):
     yield P44, U_o, n14, n30
 
 
-@pytest.mark.parametrize("prec", [cq.CQ_FP64, cq.CQ_SPLIT_BF16X3])
+@pytest.mark.parametrize("prec", [cq.CQ_FP64, cq.CQ_SPLIT_BF16X3, cq.CQ_FP64_EMU])
 def test_fullsize_s_times_x_on_p_u(data, u_data, prec):
     ctx, P, vals, dev = data
     P44, U_o, n14, n30 = u_data
@@ -157,7 +158,7 @@ def test_fullsize_s_times_x_on_p_u(data, u_data, prec):
     del Ug
 
 
-@pytest.mark.parametrize("prec", [cq.CQ_FP64, cq.CQ_SPLIT_BF16X3])
+@pytest.mark.parametrize("prec", [cq.CQ_FP64, cq.CQ_SPLIT_BF16X3, cq.CQ_FP64_EMU])
 def test_fullsize_u_times_y_on_p_l(data, u_data, prec):
     ctx, P, vals, dev = data
     P44, U_o, n14, n30 = u_data
