@@ -94,6 +94,8 @@ def parse():
                     help="skip the FP64 leg (profiling the tensor-core path)")
     ap.add_argument("--hotelling-steps", type=int, default=12)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-emu", action="store_true",
+                    help="skip the emulated-FP64 (digit planes on tensor cores) leg")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip the split-vs-oracle check on the 512-atom SZP cell")
     ap.add_argument("--sweep", default=None,
@@ -556,6 +558,38 @@ def run_cq(args, rank, world, local_rank):
                                                 torch.linalg.vector_norm(L_fp64))
             split["speedup_vs_fp64_step"] = (res["fp64"]["ms"] / r["ms"])
 
+    emu = None
+    if not args.no_emu and not args.only_split:
+        # FP64-accurate products on the tensor cores: the same K steps from the same L0
+        L.copy_(L0)
+        lnv.set_precision(cq.CQ_FP64_EMU)
+        res["emu"] = timed(args.steps, "emu")
+        r = res["emu"]
+        n_launch, kern_ms, kern_flops, mma_flops = r["stats"]
+        peaks = measured_peaks()
+        bf16 = (peaks or {}).get("bf16_tflops")
+        emu = {"value": r["flops_all"] / (r["ms"] * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "dtype": "f64 emulated: 7 bf16 digit planes, exact level sums",
+               "s_per_lnv_step": r["ms"] / args.steps / 1e3,
+               "speedup_vs_fp64_step": (res["fp64"]["ms"] / r["ms"]) if "fp64" in res else None,
+               "roofline": {"bound": "tensor", "kernel": "k_bsmm_emu",
+                            "achieved": mma_flops / (kern_ms * 1e-3) / 1e12 if kern_ms else None,
+                            "peak": bf16 or BF16_FALLBACK_TFLOPS, "unit": "TFLOP/s",
+                            "useful_tflops": kern_flops / (kern_ms * 1e-3) / 1e12 if kern_ms else None,
+                            "launches": n_launch, "kernel_ms": kern_ms,
+                            "kernel_share": kern_ms / r["ms"] if r["ms"] else None,
+                            "traffic": None},
+               "clocks": r["clk"], "gpu_launches": int(r["launches"])}
+        emu["roofline"]["frac"] = (emu["roofline"]["achieved"] / emu["roofline"]["peak"]
+                                   if emu["roofline"]["achieved"] else None)
+        if "fp64" in res:
+            emu["energy_diff_per_atom_vs_fp64"] = abs(r["reps"][-1]["energy"] - E_fp64) / cell.n_atoms
+            emu["L_rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(L - L_fp64) /
+                                              torch.linalg.vector_norm(L_fp64))
+            emu["same_step_decisions_as_fp64"] = all(
+                (a["restart"], a["fallback"], a["n_corr"]) == (b["restart"], b["fallback"], b["n_corr"])
+                for a, b in zip(r["reps"], res["fp64"]["reps"]))
+
     batched = None
     if not args.no_batch:
         batched = run_batch(args, dev, rep)
@@ -603,6 +637,8 @@ def run_cq(args, rank, world, local_rank):
         }
         if "fp64" not in res:
             line["roofline"] = split["roofline"]
+        if emu is not None:
+            line["fp64_emu"] = emu
         if split is not None:
             # last, and compact, so that a reader of the line's tail sees the mixed leg
             split.pop("lnv", None)

@@ -61,7 +61,7 @@ typedef enum {
 typedef enum {
     CQ_FP64 = 0,          /* block products on FP64 FMAs                                   */
     CQ_SPLIT_BF16X3 = 1,  /* products as 3-term split-BF16 on tensor cores, FP32 accumulate */
-    CQ_FP64_EMU = 2       /* FP64-accurate products on the BF16 tensor cores: 7 digit planes
+    CQ_FP64_EMU = 2       /* FP64-accurate products on the BF16 tensor cores: 8 digit planes
                              per value, exact level sums, three-float drains (see cq_bsmm) */
 } cq_precision;
 
@@ -184,14 +184,14 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  * paper's priorities of GPU products and solver accuracy together, on a GPU whose FP64 pipe
  * is narrow): per scalar row of A and scalar column of B over every sixteen atoms of K (four
  * K groups) a power-of-two scale 2^E with |x| < 2^E; every value is rounded to the grid
- * 2^(E-55) and cut into seven signed 8-bit digits, each exact in BF16; the 28 digit
- * products of levels p + q <= 6 run on the tensor cores, levels 0-3 summed exactly in FP32
- * within a scale period and levels 4-6 together, and every period drains into a three-float
+ * 2^(E-63) and cut into eight signed 8-bit digits, each exact in BF16; the 36 digit
+ * products of levels p + q <= 7 run on the tensor cores, levels 0-4 summed exactly in FP32
+ * within a scale period and levels 5-7 together, and every period drains into a three-float
  * (about 72-bit) sum.  Per block the error stays within the FP64 product bound
  * ||dC_ij|| <= 1e-12 max(||C_ij||, 1e-3 sum_k ||A_ik|| ||B_kj||) for products whose terms
  * lie between about 2^-70 and 2^120 in magnitude (FP32's range holds the drained sums).
- * Same basis requirement as the split (4 or 9 orbitals); its panels take about 2.3x the
- * split's scratch (seven BF16 planes per value).  Infinities and NaNs poison their scale
+ * Same basis requirement as the split (4 or 9 orbitals); its panels take about 2.7x the
+ * split's scratch (eight BF16 planes per value).  Infinities and NaNs poison their scale
  * group: they give NaN in every C value of the rows (of A) or columns (of B) that group
  * reaches.
  *

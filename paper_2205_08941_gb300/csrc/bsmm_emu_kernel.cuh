@@ -1,44 +1,47 @@
 // The tile kernel of the emulated-FP64 product (included by bsmm_split.cu after the split
 // kernel, whose barrier, copy and timeout helpers it shares).
 //
-// Operands are seven BF16 digit planes per value (digits7.cuh): A_p, B_q with planes
+// Operands are eight BF16 digit planes per value (emu_digits.cuh): A_p, B_q with planes
 // pre-scaled by 2^(-8p), so the MMA of planes p and q lands at level p + q.  Per K step the
-// MMA thread issues the 28 products with p + q <= 6 into five FP32 accumulators in tensor
-// memory: levels 0, 1, 2 and 3 each alone (their sums are integers times 2^(-8 level) below
-// 2^24 over one scale period, hence exact) and levels 4-6 together (rounded, but 2^-32 below
-// level 0).  A scale period is a run of chunks whose K groups share a scale group (four K
-// groups, sixteen 9-orbital atoms).  At its end the drain warps combine the levels, scale
-// them by 2^(E_A(row) + E_B(column) - 14) and add them into a three-float sum (h, m, l)
-// kept in tensor memory beside the accumulators, so no register file holds it; after a
+// MMA thread issues the 36 products with p + q <= 7 into six FP32 accumulators in tensor
+// memory: levels 0 to 4 each alone -- over one scale period a level-l sum is an integer
+// times 2^(-8 l) of magnitude at most (l + 1) * 192 * 128^2 < 2^24 (192 K values per
+// period), hence exact -- and levels 5-7 together (rounded, but 2^-40 below level 0, so its
+// rounding stays near 2^-64 of the group's scale, as does the digit split itself).  A scale
+// period is a run of chunks whose K groups share a scale group (four K groups, sixteen
+// 9-orbital atoms).  At its end the drain warps scale every level by
+// 2^(E_A(row) + E_B(column) - 14) and add it into a three-float sum (h, m, l): h and m in
+// tensor memory beside the accumulators, l (the smallest word) in shared memory (column-
+// major, so the lanes of a warp, which own consecutive rows, hit distinct banks).  After a
 // tile's last period C = beta C + alpha (h + m + l) is written in FP64.
 //
 // Warp roles (10 warps, one CTA per SM):
-//   warp 0      producer: lane 0 copies every K step of every chunk (A: 7 planes x 128 rows
-//               x 16 K, 28 KB; B: 7 planes x 64 rows, 14 KB) into a free stage with two TMA
+//   warp 0      producer: lane 0 copies every K step of every chunk (A: 8 planes x 128 rows
+//               x 16 K, 32 KB; B: 8 planes x 64 rows, 16 KB) into a free stage with two TMA
 //               bulk copies completing on the stage's "full" barrier;
-//   warp 1      lane 0 issues the 28 MMAs of each K step and commits the stage to its
+//   warp 1      lane 0 issues the 36 MMAs of each K step and commits the stage to its
 //               "empty" barrier; at a period's end it commits the accumulators to
 //               "acc_full" and, before the next period, waits on "acc_empty";
 //   warps 2-9   drain (lane quarter w % 4, columns 32 ((w - 2) / 4) ..) and epilogue.
-// Tensor memory (512 columns): levels 0-4 at columns 0, 64, ..., 256; h, m, l at 320, 384,
-// 448.  The accumulators are single-buffered (the three-float sum takes the rest), so the
-// MMA thread waits while a period drains.
+// Tensor memory (512 columns): levels 0-5 at columns 0, 64, ..., 320; h and m at 384 and
+// 448.  The accumulators are single-buffered (the sums take the rest), so the MMA thread
+// waits while a period drains.
 //
 // Every wait is bounded as in the split kernel; a CTA that gives up retires its copies and
 // MMAs, frees its tensor memory and sets bit 16 of the context flag.
-constexpr int NSE = 5;                       // shared-memory stages (one K step each)
+constexpr int NSE = 4;                       // shared-memory stages (one K step each)
 constexpr int E_APLANE = MT * 16 * 2;        // 4 KB: one A digit plane of one K step
 constexpr int E_BPLANE = NT * 16 * 2;        // 2 KB
-constexpr int E_AKSTEP = EMU_P * E_APLANE;   // 28 KB
-constexpr int E_BKSTEP = EMU_P * E_BPLANE;   // 14 KB
-constexpr int E_APANEL = KSTEPS * E_AKSTEP;  // 84 KB: one packed A panel
-constexpr int E_BPANEL = KSTEPS * E_BKSTEP;  // 42 KB
+constexpr int E_AKSTEP = EMU_P * E_APLANE;   // 32 KB
+constexpr int E_BKSTEP = EMU_P * E_BPLANE;   // 16 KB
+constexpr int E_APANEL = KSTEPS * E_AKSTEP;  // 96 KB: one packed A panel
+constexpr int E_BPANEL = KSTEPS * E_BKSTEP;  // 48 KB
 constexpr int E_STAGE = E_AKSTEP + E_BKSTEP;
 constexpr int E_SBO = 256;                   // bytes between 8-row groups (2 core columns)
-constexpr int E_LEVELS = 5;
-constexpr int E_COL_H = E_LEVELS * NT, E_COL_M = E_COL_H + NT, E_COL_L = E_COL_M + NT;
+constexpr int E_LEVELS = 6;                  // accumulators: levels 0-4, then 5-7 merged
+constexpr int E_COL_H = E_LEVELS * NT, E_COL_M = E_COL_H + NT;
 constexpr int E_TMEM_COLS = 512;
-constexpr int E_MMAS = EMU_P * (EMU_P + 1) / 2;  // 28 products per K step
+constexpr int E_MMAS = EMU_P * (EMU_P + 1) / 2;  // 36 products per K step
 
 struct EBars {
     uint64_t full[NSE], empty[NSE], acc_full, acc_empty, done;
@@ -46,8 +49,9 @@ struct EBars {
     int abort_flag;
 };
 static_assert(sizeof(EBars) <= BAR_BYTES, "barrier block");
-static_assert(NSE * E_STAGE + BAR_BYTES <= 227 * 1024, "shared memory per CTA");
-static_assert(E_COL_L + NT <= E_TMEM_COLS, "tensor memory columns");
+constexpr int E_LWORDS = MT * NT * 4;         // 32 KB: the three-float sums' smallest words
+static_assert(NSE * E_STAGE + E_LWORDS + BAR_BYTES <= 227 * 1024, "shared memory per CTA");
+static_assert(E_COL_M + NT <= E_TMEM_COLS, "tensor memory columns");
 
 struct EmuArgs {
     int n_tiles;
@@ -131,7 +135,8 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
 {
     constexpr int GI = MT / NB, GJ = NT / NB;
     extern __shared__ __align__(1024) uint8_t smem[];
-    EBars *bars = reinterpret_cast<EBars *>(smem + NSE * E_STAGE);
+    float *lws = reinterpret_cast<float *>(smem + NSE * E_STAGE);  // [column][row]
+    EBars *bars = reinterpret_cast<EBars *>(smem + NSE * E_STAGE + E_LWORDS);
     volatile int *abort_flag = &bars->abort_flag;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const uint32_t sm0 = smem_u32(smem);
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
                                 const uint64_t ad = sa + (uint64_t)((pa * E_APLANE) >> 4);
                                 const uint64_t bd = sb + (uint64_t)((qb * E_BPLANE) >> 4);
                                 // the first product into each accumulator of a period
-                                // overwrites it: (0, q) for q < 5 in this order
+                                // overwrites it: (0, q) for q < 6 in this order
                                 const uint32_t acc =
                                     (first && ks == 0 && pa == 0 && qb < E_LEVELS) ? 0u : 1u;
                                 asm volatile(
@@ -281,6 +286,9 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
         for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
             const int64_t c0 = p.kstart[tile];
             const int nch = (int)(p.kstart[tile + 1] - c0);
+            // the smallest words of this thread's row and 32 columns start at zero per tile
+#pragma unroll
+            for (int x = 0; x < 32; ++x) lws[(half * 32 + x) * MT + arow] = 0.f;
             bool first_period = true;
             for (int c = 0; c < nch && ok;) {
                 // the period: chunks [c, c1) of one scale group
@@ -297,14 +305,13 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const int col0 = half * 32 + q * 16;
-                    uint32_t h[16], m[16], l[16];
+                    uint32_t h[16], m[16];
                     if (first_period) {
 #pragma unroll
-                        for (int x = 0; x < 16; ++x) h[x] = m[x] = l[x] = 0u;
+                        for (int x = 0; x < 16; ++x) h[x] = m[x] = 0u;
                     } else {
                         tm_ld16(lane_addr + E_COL_H + q * 16, h);
                         tm_ld16(lane_addr + E_COL_M + q * 16, m);
-                        tm_ld16(lane_addr + E_COL_L + q * 16, l);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     }
                     int eb[16];
@@ -323,34 +330,30 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
                             const bool poison = ea == EMU_POISON || eb[x] == EMU_POISON;
                             if (!poison && (ea == EMU_NONE || eb[x] == EMU_NONE)) continue;
                             const int e = poison ? 0 : ea + eb[x] - 14;
-                            float hh = __uint_as_float(h[x]), mm = __uint_as_float(m[x]),
-                                  ll = __uint_as_float(l[x]);
+                            float hh = __uint_as_float(h[x]), mm = __uint_as_float(m[x]);
+                            float &ll = lws[(col0 + x) * MT + arow];
                             tf_add(hh, mm, ll, mul_pow2(__uint_as_float(v[x]), e));
                             h[x] = __float_as_uint(hh);
                             m[x] = __float_as_uint(mm);
-                            l[x] = __float_as_uint(ll);
                         }
                     }
                     tm_st16(lane_addr + E_COL_H + q * 16, h);
                     tm_st16(lane_addr + E_COL_M + q * 16, m);
-                    tm_st16(lane_addr + E_COL_L + q * 16, l);
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                    if (c1 == nch) {
+                    if (c1 == nch && arow < GI * NB) {
                         // the tile's last period: C = beta C + alpha (h + m + l) in FP64
                         const int si = arow / NB, a = arow % NB;
-                        if (arow < GI * NB) {
 #pragma unroll
-                            for (int x = 0; x < 16; ++x) {
-                                const int col = col0 + x, jl = col / NB, bo = col % NB;
-                                if (jl >= GJ) continue;
-                                const int32_t blk = __ldg(&p.cidx[((int64_t)tile * GI + si) * GJ + jl]);
-                                if (blk < 0) continue;
-                                double *dst = p.C + (int64_t)blk * p.c_stride + a * NB + bo;
-                                const double vv = ((double)__uint_as_float(h[x]) +
-                                                   (double)__uint_as_float(m[x])) +
-                                                  (double)__uint_as_float(l[x]);
-                                *dst = p.beta == 0.0 ? p.alpha * vv : p.beta * *dst + p.alpha * vv;
-                            }
+                        for (int x = 0; x < 16; ++x) {
+                            const int col = col0 + x, jl = col / NB, bo = col % NB;
+                            if (jl >= GJ) continue;
+                            const int32_t blk = __ldg(&p.cidx[((int64_t)tile * GI + si) * GJ + jl]);
+                            if (blk < 0) continue;
+                            double *dst = p.C + (int64_t)blk * p.c_stride + a * NB + bo;
+                            const double vv = ((double)__uint_as_float(h[x]) +
+                                               (double)__uint_as_float(m[x])) +
+                                              (double)lws[(col0 + x) * MT + arow];
+                            *dst = p.beta == 0.0 ? p.alpha * vv : p.beta * *dst + p.alpha * vv;
                         }
                     }
                 }

@@ -38,7 +38,7 @@
 #include <numeric>
 
 #include "cq_internal.cuh"
-#include "digits7.cuh"
+#include "emu_digits.cuh"
 #include "split3.cuh"
 
 namespace {
@@ -410,7 +410,7 @@ struct SplitArgs {
 #include "bsmm_emu_kernel.cuh"
 
 constexpr int SMEM = NS * STAGE + BAR_BYTES;     // pipeline stages + barriers
-constexpr int SMEM_E = NSE * E_STAGE + BAR_BYTES;
+constexpr int SMEM_E = NSE * E_STAGE + E_LWORDS + BAR_BYTES;
 
 // ---------------------------------------------------------------- emulated-FP64 packing
 
@@ -423,7 +423,7 @@ __device__ __forceinline__ uint32_t emu_off(int rows, int row, int col, int plan
                       (col & 1) * 128 + (row & 7) * 16);
 }
 
-// Largest exponent (digits7_exponent) of every scalar row of every A panel entry (one CTA
+// Largest exponent (emu_exponent) of every scalar row of every A panel entry (one CTA
 // of 128 threads per entry = (M group, K group)): row r = (slot r / NB, orbital r % NB).
 template <int NB>
 __global__ void __launch_bounds__(MT)
@@ -439,7 +439,7 @@ k_emu_rowexp_a(const int32_t *index, const double *__restrict__ A, int stride, i
         for (int a = 0; a < CA; ++a) {
             const int64_t b = __ldg(&blk[a]);
             if (b < 0) continue;
-            for (int k = 0; k < NB; ++k) m = max(m, digits7_exponent(A[b * stride + o * NB + k]));
+            for (int k = 0; k < NB; ++k) m = max(m, emu_exponent(A[b * stride + o * NB + k]));
         }
     }
     out[e * MT + r] = (int16_t)m;
@@ -461,7 +461,7 @@ k_emu_rowexp_b(const int32_t *index, const double *__restrict__ B, int stride, i
         for (int a = 0; a < CA; ++a) {
             const int64_t b = __ldg(&blk[a]);
             if (b < 0) continue;
-            for (int k = 0; k < NB; ++k) m = max(m, digits7_exponent(B[b * stride + k * NB + o]));
+            for (int k = 0; k < NB; ++k) m = max(m, emu_exponent(B[b * stride + k * NB + o]));
         }
     }
     out[e * NT + c] = (int16_t)m;
@@ -484,7 +484,7 @@ __global__ void k_emu_group_scale(int width, const int64_t *ptr, const int32_t *
     scale[e * width + r] = (int16_t)m;
 }
 
-// Seven digit planes of n (<= 8) values as seven 16-byte core-matrix rows (one per plane,
+// Eight digit planes of n (<= 8) values as eight 16-byte core-matrix rows (one per plane,
 // two BF16 per word, values beyond n zero).
 __device__ __forceinline__ void emu_rows(const double *x, int n, int E, uint4 (&w)[EMU_P])
 {
@@ -497,7 +497,7 @@ __device__ __forceinline__ void emu_rows(const double *x, int n, int E, uint4 (&
     for (int v = 0; v < 8; ++v) {
         if (v >= n) break;
         __nv_bfloat16 d[EMU_P];
-        digits7(x[v], E, d);
+        emu_digits(x[v], E, d);
 #pragma unroll
         for (int p = 0; p < EMU_P; ++p)
             u[p][v >> 1] |= (uint32_t)__bfloat16_as_ushort(d[p]) << (16 * (v & 1));
@@ -538,7 +538,7 @@ __device__ __forceinline__ void put_pair_emu(uint8_t *panel, int rows, int r, in
         *reinterpret_cast<uint4 *>(panel + emu_off(rows, r, KLayout<NB>::tail_col(a0), p)) = w[p];
 }
 
-// Emulated A panels of entries [e0, e0 + gridDim.x): as k_pack_a, seven digit planes per
+// Emulated A panels of entries [e0, e0 + gridDim.x): as k_pack_a, eight digit planes per
 // value against the (entry, row) group exponent.
 template <int NB>
 __global__ void __launch_bounds__(256)

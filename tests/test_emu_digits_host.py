@@ -1,10 +1,10 @@
 """The digit planes of the emulated-FP64 product, built for the host from the same header
 the packing kernels use, checked on the CPU against what the construction fixes.
 
-For a group exponent E with |x| < 2^E the planes f_p = d_p 2^(-8p) must hold integers
-|d_p| <= 128 (exact in BF16), and 2^(E - 7) sum_p f_p must equal x rounded to the grid
-2^(E - 55) -- checked exactly, in integers: round(x 2^(55 - E)) against
-sum_p d_p 2^(8 (6 - p)).  So |x - reconstruction| <= 2^(E - 56).  Zero gives zero planes;
+For a group exponent E with |x| < 2^E the eight planes f_p = d_p 2^(-8p) must hold
+integers |d_p| <= 128 (exact in BF16), and 2^(E - 7) sum_p f_p must equal x rounded to the
+grid 2^(E - 63) -- checked exactly, in integers: round(x 2^(63 - E)) against
+sum_p d_p 2^(8 (7 - p)).  So |x - reconstruction| <= 2^(E - 64).  Zero gives zero planes;
 infinities and NaNs give a NaN first plane (the group is poisoned); the exponent is the
 smallest E with |x| < 2^E, subnormals included.
 """
@@ -17,10 +17,11 @@ import numpy as np
 import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "digits7_host.cu")
-HDR = os.path.join(os.path.dirname(HERE), "paper_2205_08941_gb300", "csrc", "digits7.cuh")
-EXE = os.path.join(HERE, "_build", "digits7_host")
+SRC = os.path.join(HERE, "emu_digits_host.cu")
+HDR = os.path.join(os.path.dirname(HERE), "paper_2205_08941_gb300", "csrc", "emu_digits.cuh")
+EXE = os.path.join(HERE, "_build", "emu_digits_host")
 OWN = 99999
+P = 8
 
 
 @pytest.fixture(scope="module")
@@ -39,25 +40,25 @@ def digits():
         rec = np.zeros(len(x), dtype=[("x", "<f8"), ("E", "<i4")])
         rec["x"], rec["E"] = x, E
         out = subprocess.run([EXE], input=rec.tobytes(), capture_output=True, check=True).stdout
-        o = np.frombuffer(out, dtype=[("E", "<i4"), ("f", "<f4", (7,))])
+        o = np.frombuffer(out, dtype=[("E", "<i4"), ("f", "<f4", (P,))])
         return o["E"].astype(np.int64), o["f"].astype(np.float64)
 
     return run
 
 
 def _exact_check(x, E, f):
-    """Integers: d_p = f_p 2^(8p); sum_p d_p 2^(8(6-p)) == round(x 2^(55-E)) (ties away)."""
+    """Integers: d_p = f_p 2^(8p); sum_p d_p 2^(8(7-p)) == round(x 2^(63-E)) (ties away)."""
     for xi, Ei, fi in zip(x, E, f):
-        d = [int(Fraction(float(fi[p])) * 2 ** (8 * p)) for p in range(7)]
-        assert all(Fraction(float(fi[p])) * 2 ** (8 * p) == d[p] for p in range(7))
+        d = [int(Fraction(float(fi[p])) * 2 ** (8 * p)) for p in range(P)]
+        assert all(Fraction(float(fi[p])) * 2 ** (8 * p) == d[p] for p in range(P))
         assert all(abs(v) <= 128 for v in d), d
-        Y = sum(v * 2 ** (8 * (6 - p)) for p, v in enumerate(d))
-        t = Fraction(float(xi)) * Fraction(2) ** (55 - int(Ei))
+        Y = sum(v * 2 ** (8 * (P - 1 - p)) for p, v in enumerate(d))
+        t = Fraction(float(xi)) * Fraction(2) ** (63 - int(Ei))
         r = int(abs(t) + Fraction(1, 2))           # round half away from zero
         r = -r if t < 0 else r
         assert Y == r, (xi, Ei, Y, r)
-        err = abs(Fraction(float(xi)) - Fraction(2) ** (int(Ei) - 55) * Y)
-        assert err <= Fraction(2) ** (int(Ei) - 56)
+        err = abs(Fraction(float(xi)) - Fraction(2) ** (int(Ei) - 63) * Y)
+        assert err <= Fraction(2) ** (int(Ei) - 64)
 
 
 def test_exponent_is_the_smallest_bound(digits):

@@ -1,11 +1,13 @@
-"""Emulated-FP64 products (CQ_FP64_EMU: seven BF16 digit planes per value on the tensor
+"""Emulated-FP64 products (CQ_FP64_EMU: eight BF16 digit planes per value on the tensor
 cores, exact level sums, three-float drains) against the FP64 oracle, to the FP64 product
 bound of the other parity tests: per block
 ||dC_ij||_F <= 1e-12 max(||C_ij||_F, 1e-3 sum_k ||A_ik||_F ||B_kj||_F).
 
-The digits carry every value to 2^-56 of its scale group's largest magnitude and the
-dropped digit products are below 2^-56 of level 0, so the emulated product is FP64-class;
-the bound is the one FP64 FMAs are held to.  Cases: the 64-atom sp cell over several range
+The digits carry every value to 2^-64 of its scale group's largest magnitude, the merged
+high levels round near 2^-64 of it and the dropped digit products lie below that, so the
+emulated product is FP64-class even for values some 2^11 below their group's largest (the
+44-bohr S.X products reach such values at the edge of the lens); the bound is the one FP64
+FMAs are held to.  Cases: the 64-atom sp cell over several range
 triples with alpha and beta, the 512-atom SZP cell (long k-sums, sampled rows), blocks that
 no triplet reaches (exactly beta C), non-finite values (NaN where FP64 gives NaN, only in
 the same scalar row), and twenty LNV steps from the oracle's start (energies to 1e-10
