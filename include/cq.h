@@ -187,9 +187,13 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  * 2^(E-63) and cut into eight signed 8-bit digits, each exact in BF16; the 36 digit
  * products of levels p + q <= 7 run on the tensor cores, levels 0-4 summed exactly in FP32
  * within a scale period and levels 5-7 together, and every period drains into a three-float
- * (about 72-bit) sum.  Per block the error stays within the FP64 product bound
- * ||dC_ij|| <= 1e-12 max(||C_ij||, 1e-3 sum_k ||A_ik|| ||B_kj||) for products whose terms
- * lie between about 2^-70 and 2^120 in magnitude (FP32's range holds the drained sums).
+ * (about 72-bit) sum.  Every value is carried to 2^-64 of its group's largest magnitude,
+ * so the error of C_ij stays below about 1e-15 sum_k (Amax ||B_kj|| + ||A_ik|| Bmax) with
+ * Amax, Bmax the largest magnitudes of the scale groups the terms fall in.  While the
+ * magnitudes inside a group stay within about 2^14 of one another (the smooth decay of the
+ * method's matrices) that is the FP64 product bound
+ * ||dC_ij|| <= 1e-12 max(||C_ij||, 1e-3 sum_k ||A_ik|| ||B_kj||); terms must lie between
+ * about 2^-70 and 2^120 in magnitude (FP32's range holds the drained sums).
  * Same basis requirement as the split (4 or 9 orbitals); its panels take about 2.7x the
  * split's scratch (eight BF16 planes per value).  Infinities and NaNs poison their scale
  * group: they give NaN in every C value of the rows (of A) or columns (of B) that group
