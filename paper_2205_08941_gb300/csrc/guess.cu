@@ -339,14 +339,19 @@ k_gemm(int M, int N, const float *A, int lda, const BT *B, int ldb, float *C, in
         }
 }
 
-// Z += bias; H = silu(Z) (hidden) or H = Z (output)
-__global__ void k_bias_act(int64_t M, int N, const float *bias, float *Z, float *H, int act)
+#include "mlp_tc.cuh"
+
+// Z += bias; H = silu(Z) (hidden) or H = Z (output); Hb (if not null) = bf16(H)
+__global__ void k_bias_act(int64_t M, int N, const float *bias, float *Z, float *H, int act,
+                           __nv_bfloat16 *Hb)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= M * N) return;
     const float z = Z[e] + bias[e % N];
     Z[e] = z;
-    H[e] = act ? z / (1.f + __expf(-z)) : z;
+    const float h = act ? z / (1.f + __expf(-z)) : z;
+    H[e] = h;
+    if (Hb) Hb[e] = __float2bfloat16(h);
 }
 
 // dZ = dH * silu'(Z)
@@ -468,6 +473,10 @@ struct cq_guess {
     int64_t xin_rows = 0;
     DevBuf act;                       // Z and H per layer for a batch
     int64_t act_rows = 0;
+    // tensor-core path (BF16 weights): W^T per layer (BF16, N x K), and BF16 copies of the
+    // layer inputs, of dZ and the transposes H^T, dZ^T of the backward pass
+    DevBuf wt, actb;
+    int64_t actb_rows = 0;
 };
 
 namespace {
@@ -483,6 +492,61 @@ cq_status ensure_act(cq_guess *g, int64_t rows)
     CQ_TRY(cq_alloc(g->ctx, g->act, sizeof(float) * per * rows));
     g->act_rows = rows;
     return CQ_OK;
+}
+
+int64_t pad16(int64_t x) { return (x + 15) & ~(int64_t)15; }
+
+// BF16 buffers of the tensor-core path for `rows` samples: layer inputs Hb[0..L-1]
+// (rows x dims[l]), dZb (rows x 256), H^T and dZ^T (256 x pad16(rows) each)
+cq_status ensure_actb(cq_guess *g, int64_t rows)
+{
+    if (g->actb_rows >= rows) return CQ_OK;
+    int64_t per = 0;
+    for (int l = 0; l < g->n_layers; ++l) per += g->dims[l];
+    per += 256;
+    const int64_t elems = per * rows + 2 * 256 * pad16(rows);
+    CQ_TRY(cq_alloc(g->ctx, g->actb, sizeof(__nv_bfloat16) * elems));
+    g->actb_rows = rows;
+    return CQ_OK;
+}
+
+// W^T per layer in BF16 from the FP32 master weights (after every change of the weights)
+void refresh_wt(cq_guess *g, cudaStream_t s)
+{
+    for (int l = 0; l < g->n_layers; ++l) {
+        const int K = g->dims[l], N = g->dims[l + 1];
+        k_to_bf16_mat<<<blocks_for((int64_t)K * N), 256, 0, s>>>(
+            K, N, g->w.as<float>() + g->w_off[l], g->wt.as<__nv_bfloat16>() + g->w_off[l], 1, K);
+    }
+    cq_count_launch(g->n_layers);
+}
+
+cq_status tc_attr(cq_ctx *ctx)
+{
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cq_fail(ctx, CQ_ERR_INVALID, "guess: device index");
+    if (!done[dev]) {
+        CQ_TRY(cq_check_cuda(ctx, cudaFuncSetAttribute(k_gemm_tc,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       TC_SMEM), "mlp attribute"));
+        done[dev] = true;
+    }
+    return CQ_OK;
+}
+
+// C = A Bt^T on the tensor cores (see mlp_tc.cuh); parts > 1 splits K into that many
+// deterministic partial products c_stride_z apart
+void gemm_tc(cq_ctx *ctx, int M, int N, const __nv_bfloat16 *A, int64_t lda,
+             const __nv_bfloat16 *Bt, int64_t ldb, float *C, int64_t ldc, int64_t K, int parts,
+             int64_t c_stride_z)
+{
+    const int64_t chunk = parts > 1 ? pad16((K + parts - 1) / parts) : K;
+    dim3 grid((unsigned)((M + TC_MT - 1) / TC_MT), 1, (unsigned)parts);
+    k_gemm_tc<<<grid, 128, TC_SMEM, ctx->stream>>>(M, N, (int)pad16(N), A, lda, Bt, ldb, C, ldc,
+                                                   0, K, c_stride_z, chunk, ctx->flag.as<int32_t>());
+    cq_count_launch();
 }
 
 __global__ void k_norm_in(int64_t n, const float *x, const float *mean, const float *scale,
@@ -511,6 +575,21 @@ cq_status mlp_forward(cq_guess *g, const float *X, int64_t rows, std::vector<flo
     Z.assign(g->n_layers + 1, nullptr);
     H.assign(g->n_layers + 1, nullptr);
     H[0] = g->xin.as<float>();
+    const bool tc = !g->fp32_weights;
+    std::vector<__nv_bfloat16 *> Hb(g->n_layers, nullptr);
+    if (tc) {
+        // BF16 weights: the layers run on the tensor cores with BF16 inputs
+        CQ_TRY(ensure_actb(g, rows));
+        CQ_TRY(tc_attr(ctx));
+        int64_t ob = 0;
+        for (int l = 0; l < g->n_layers; ++l) {
+            Hb[l] = g->actb.as<__nv_bfloat16>() + ob;
+            ob += rows * g->dims[l];
+        }
+        k_to_bf16_mat<<<blocks_for(rows * NDESC), 256, 0, ctx->stream>>>(rows, NDESC, H[0],
+                                                                          Hb[0], 0, 0);
+        cq_count_launch();
+    }
     int64_t off = 0;
     for (int l = 1; l <= g->n_layers; ++l) {
         Z[l] = base + off;
@@ -518,18 +597,20 @@ cq_status mlp_forward(cq_guess *g, const float *X, int64_t rows, std::vector<flo
         H[l] = base + off;
         off += rows * g->dims[l];
         const int K = g->dims[l - 1], N = g->dims[l];
-        dim3 grid((N + 63) / 64, (unsigned)((rows + 63) / 64), 1);
-        if (g->fp32_weights)
+        if (tc) {
+            gemm_tc(ctx, (int)rows, N, Hb[l - 1], K, g->wt.as<__nv_bfloat16>() + g->w_off[l - 1], K,
+                    Z[l], N, K, 1, 0);
+        } else {
+            dim3 grid((N + 63) / 64, (unsigned)((rows + 63) / 64), 1);
             k_gemm<false, false, float><<<grid, 256, 0, ctx->stream>>>(
                 (int)rows, N, H[l - 1], K, g->w.as<float>() + g->w_off[l - 1], N, Z[l], N, 0, K, 0,
                 K);
-        else
-            k_gemm<false, false, __nv_bfloat16><<<grid, 256, 0, ctx->stream>>>(
-                (int)rows, N, H[l - 1], K, g->wb.as<__nv_bfloat16>() + g->w_off[l - 1], N, Z[l], N,
-                0, K, 0, K);
+            cq_count_launch();
+        }
         k_bias_act<<<blocks_for(rows * N), 256, 0, ctx->stream>>>(
-            rows, N, g->b.as<float>() + g->b_off[l - 1], Z[l], H[l], l < g->n_layers ? 1 : 0);
-        cq_count_launch(2);
+            rows, N, g->b.as<float>() + g->b_off[l - 1], Z[l], H[l], l < g->n_layers ? 1 : 0,
+            tc && l < g->n_layers ? Hb[l] : nullptr);
+        cq_count_launch();
     }
     return cq_check_cuda(ctx, cudaGetLastError(), "mlp forward");
 }
@@ -556,6 +637,7 @@ extern "C" cq_status cq_guess_create(cq_ctx *ctx, uint64_t seed, int32_t fp32_we
     for (DevBuf *b : {&g->b, &g->gb, &g->mb, &g->vb})
         CQ_TRY(cq_alloc(ctx, *b, sizeof(float) * g->n_b));
     CQ_TRY(cq_alloc(ctx, g->wb, sizeof(__nv_bfloat16) * g->n_w));
+    CQ_TRY(cq_alloc(ctx, g->wt, sizeof(__nv_bfloat16) * g->n_w));
     CQ_TRY(cq_alloc(ctx, g->mean, sizeof(float) * NOUT));
     CQ_TRY(cq_alloc(ctx, g->scale, sizeof(float) * NOUT));
     CQ_TRY(cq_alloc(ctx, g->in_mean, sizeof(float) * NDESC));
@@ -579,6 +661,7 @@ extern "C" cq_status cq_guess_create(cq_ctx *ctx, uint64_t seed, int32_t fp32_we
     cudaMemcpyAsync(g->in_scale.ptr, one.data(), sizeof(float) * NDESC, cudaMemcpyHostToDevice, s);
     k_to_bf16<<<blocks_for(g->n_w), 256, 0, s>>>(g->n_w, g->w.as<float>(), g->wb.as<__nv_bfloat16>());
     cq_count_launch();
+    refresh_wt(g.get(), s);
     CQ_TRY(cq_check_cuda(ctx, cudaStreamSynchronize(s), "guess create"));
     *out = g.release();
     return CQ_OK;
@@ -604,6 +687,7 @@ extern "C" cq_status cq_guess_params(cq_guess *g, float *w_host, float *b_host, 
         k_to_bf16<<<blocks_for(g->n_w), 256, 0, s>>>(g->n_w, g->w.as<float>(),
                                                       g->wb.as<__nv_bfloat16>());
         cq_count_launch();
+        refresh_wt(g, s);
     } else {
         if (w_host) cudaMemcpyAsync(w_host, g->w.ptr, 4 * g->n_w, cudaMemcpyDeviceToHost, s);
         if (b_host) cudaMemcpyAsync(b_host, g->b.ptr, 4 * g->n_b, cudaMemcpyDeviceToHost, s);
@@ -742,31 +826,55 @@ extern "C" cq_status cq_guess_train_step(cq_guess *g, const float *desc, const f
     cq_count_launch(2);
     // dY holds dLoss/dZ_L (output layer is linear)
     float *dZ = dY;
+    const bool tc = !g->fp32_weights;
+    __nv_bfloat16 *dZb = nullptr, *Ht = nullptr, *dZt = nullptr;
+    const int64_t rp = pad16(rows);
+    if (tc) {
+        int64_t ob = 0;
+        for (int l = 0; l < L; ++l) ob += rows * g->dims[l];
+        dZb = g->actb.as<__nv_bfloat16>() + ob;
+        Ht = dZb + rows * 256;
+        dZt = Ht + 256 * rp;
+    }
     for (int l = L; l >= 1; --l) {
         const int K = g->dims[l - 1], N = g->dims[l];
         // dW_l = H_{l-1}^T dZ  (K x N), reduction over rows in `parts` fixed chunks
         const int64_t chunk = ((rows + parts - 1) / parts + 15) / 16 * 16;
-        dim3 grid((N + 63) / 64, (K + 63) / 64, parts);
-        k_gemm<true, false, float><<<grid, 256, 0, s>>>(K, N, H[l - 1], K, dZ, N, (float *)vpart,
-                                                        N, 0, rows, (int64_t)K * N, chunk);
+        if (tc) {
+            // tensor cores: dW = (H^T)(dZ^T)^T from BF16 transposes (rows padded to 16)
+            k_to_bf16_mat<<<blocks_for(rows * K), 256, 0, s>>>(rows, K, H[l - 1], Ht, 1, rp);
+            k_to_bf16_mat<<<blocks_for(rows * N), 256, 0, s>>>(rows, N, dZ, dZt, 1, rp);
+            cq_count_launch(2);
+            gemm_tc(ctx, K, N, Ht, rp, dZt, rp, (float *)vpart, N, rows, parts, (int64_t)K * N);
+        } else {
+            dim3 grid((N + 63) / 64, (K + 63) / 64, parts);
+            k_gemm<true, false, float><<<grid, 256, 0, s>>>(K, N, H[l - 1], K, dZ, N,
+                                                            (float *)vpart, N, 0, rows,
+                                                            (int64_t)K * N, chunk);
+            cq_count_launch();
+        }
         k_sum_parts<<<blocks_for((int64_t)K * N), 256, 0, s>>>((int64_t)K * N, parts,
                                                              (int64_t)K * N, (float *)vpart,
                                                              g->gw.as<float>() + g->w_off[l - 1]);
         k_colsum<<<blocks_for(N), 256, 0, s>>>(rows, N, dZ, g->gb.as<float>() + g->b_off[l - 1]);
-        cq_count_launch(3);
+        cq_count_launch(2);
         if (l > 1) {
             // dH_{l-1} = dZ W_l^T (rows x K), then dZ_{l-1} = dH * silu'(Z_{l-1})
-            dim3 g2((K + 63) / 64, (unsigned)((rows + 63) / 64), 1);
-            if (g->fp32_weights)
+            if (tc) {
+                // W (K x N, row-major) is already the K-major second operand of dZ W^T
+                k_to_bf16_mat<<<blocks_for(rows * N), 256, 0, s>>>(rows, N, dZ, dZb, 0, 0);
+                cq_count_launch();
+                gemm_tc(ctx, (int)rows, K, dZb, N, g->wb.as<__nv_bfloat16>() + g->w_off[l - 1], N,
+                        dH, K, N, 1, 0);
+            } else {
+                dim3 g2((K + 63) / 64, (unsigned)((rows + 63) / 64), 1);
                 k_gemm<false, true, float><<<g2, 256, 0, s>>>(
                     (int)rows, K, dZ, N, g->w.as<float>() + g->w_off[l - 1], N, dH, K, 0, N, 0, N);
-            else
-                k_gemm<false, true, __nv_bfloat16><<<g2, 256, 0, s>>>(
-                    (int)rows, K, dZ, N, g->wb.as<__nv_bfloat16>() + g->w_off[l - 1], N, dH, K, 0,
-                    N, 0, N);
+                cq_count_launch();
+            }
             // dZ of layer l is no longer needed: the next layer's dZ reuses its buffer
             k_act_back<<<blocks_for(rows * K), 256, 0, s>>>(rows * K, Z[l - 1], dH, dY);
-            cq_count_launch(2);
+            cq_count_launch();
             dZ = dY;
         }
     }
@@ -782,6 +890,7 @@ extern "C" cq_status cq_guess_train_step(cq_guess *g, const float *desc, const f
                                                   g->mb.as<float>(), g->vb.as<float>(), nullptr, lr,
                                                   b1, b2, eps, c1, c2);
         cq_count_launch(2);
+        refresh_wt(g, s);
     }
     if (loss_host) {
         float part[256];

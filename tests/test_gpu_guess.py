@@ -88,10 +88,20 @@ def test_network_fp32_mode_matches_oracle(ctx):
 
 
 def test_network_bf16_mode_within_bf16_tolerance(ctx):
+    """BF16 weights: every contraction runs on the tensor cores (tcgen05, BF16 inputs, FP32
+    accumulation).  Outputs to 1e-2 of their scale; loss to 1e-2; weight and bias gradients
+    to 3e-2 of their largest entry (BF16 rounds the activations, dZ and the weights to 2^-9
+    relative before FP32 accumulation over the batch)."""
     g, X, T, (im, isc, om, osc), w, b = _net_case(ctx, False)
-    Y = g.forward(torch.tensor(X, device="cuda:0")).cpu().numpy()
+    Xg, Tg = torch.tensor(X, device="cuda:0"), torch.tensor(T, device="cuda:0")
+    Y = g.forward(Xg).cpu().numpy()
     Yo, _ = G.forward(w, b, X, im, isc)
     assert np.abs(Y - Yo).max() <= 1e-2 * max(1.0, np.abs(Yo).max())
+    loss, gw, gb = g.train_step(Xg, Tg, 0.0, grads=True)
+    lo, gwo, gbo = G.loss_and_grads(w, b, X, T, im, isc, om, osc)
+    assert loss == pytest.approx(lo, rel=1e-2)
+    assert np.abs(gw - gwo).max() <= 3e-2 * np.abs(gwo).max()
+    assert np.abs(gb - gbo).max() <= 3e-2 * np.abs(gbo).max()
     g.close()
 
 
