@@ -57,7 +57,7 @@ struct EmuArgs {
     int n_tiles;
     const int64_t *kstart;     // chunk range of each tile (n_tiles + 1)
     const int2 *chunks;        // (A panel entry, B panel entry) per chunk
-    const int32_t *kappa;      // K group of every chunk
+    const uint8_t *meta;       // per chunk: bit 0 starts a scale period, bit 1 ends one
     const int32_t *cidx;       // C block of each (M slot, N slot) pair of each tile
     const uint8_t *panel_a;    // A panels of entries [ea0, ...)
     int64_t ea0;
@@ -128,7 +128,23 @@ __device__ __forceinline__ void tm_st16(uint32_t addr, const uint32_t (&v)[16])
         : "memory");
 }
 
-__device__ __forceinline__ bool same_scale_group(int k0, int k1) { return (k0 >> 2) == (k1 >> 2); }
+constexpr uint8_t PERIOD_FIRST = 1, PERIOD_LAST = 2;
+
+__device__ __forceinline__ void tm_ld8(uint32_t addr, uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void tm_st8(uint32_t addr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(addr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                 "r"(v[7])
+                 : "memory");
+}
 
 template <int NB>
 __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
@@ -217,28 +233,28 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
         __syncwarp();
     } else if (warp == W_MMA) {
         // ------------------------------------------------------------ MMA issue
-        if (lane == 0) {
-            uint32_t sg = 0, pg = 0;
-            bool ok = true, issued = false;
-            const uint64_t da0 = emu_desc(sm0), db0 = emu_desc(sm0 + E_AKSTEP);
-            for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-                const int64_t c0 = p.kstart[tile];
-                const int nch = (int)(p.kstart[tile + 1] - c0);
-                int kprev = -1;
-                for (int c = 0; c < nch && ok; ++c) {
-                    const int kk = p.kappa[c0 + c];
-                    const bool first = (c == 0) || !same_scale_group(kprev, kk);
-                    const bool last_c = (c == nch - 1) || !same_scale_group(kk, p.kappa[c0 + c + 1]);
-                    kprev = kk;
+        // the warp walks the chunks (its lanes load the period flags 32 chunks at a time);
+        // lane 0 waits and issues
+        uint32_t sg = 0, pg = 0;
+        bool ok = true, issued = false;
+        const uint64_t da0 = emu_desc(sm0), db0 = emu_desc(sm0 + E_AKSTEP);
+        for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+            const int64_t c0 = p.kstart[tile];
+            const int nch = (int)(p.kstart[tile + 1] - c0);
+            uint32_t mine = 0;
+            for (int c = 0; c < nch && ok; ++c) {
+                if ((c & 31) == 0) mine = c + lane < nch ? p.meta[c0 + c + lane] : 0u;
+                const uint32_t meta = __shfl_sync(0xffffffffu, mine, c & 31);
+                const bool first = (meta & PERIOD_FIRST) != 0;
+                int go = 1;
+                if (lane == 0) {
                     if (first && pg > 0 &&
-                        !bar_wait(smem_u32(&bars->acc_empty), (pg - 1) & 1u, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    for (int ks = 0; ks < KSTEPS; ++ks, ++sg) {
+                        !bar_wait(smem_u32(&bars->acc_empty), (pg - 1) & 1u, abort_flag))
+                        go = 0;
+                    for (int ks = 0; ks < KSTEPS && go; ++ks, ++sg) {
                         const int s = (int)(sg % NSE);
                         if (!bar_wait(smem_u32(&bars->full[s]), (sg / NSE) & 1u, abort_flag)) {
-                            ok = false;
+                            go = 0;
                             break;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -264,20 +280,25 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
                         bar_commit(smem_u32(&bars->empty[s]));
                         issued = true;
                     }
-                    if (ok && last_c) {
-                        bar_commit(smem_u32(&bars->acc_full));
-                        ++pg;
-                    }
+                    if (go && (meta & PERIOD_LAST)) bar_commit(smem_u32(&bars->acc_full));
                 }
+                if (!__shfl_sync(0xffffffffu, go, 0)) {
+                    ok = false;
+                    break;
+                }
+                if (meta & PERIOD_LAST) ++pg;
             }
-            if (issued) {  // retire every MMA before the tensor memory is released
-                bar_commit(smem_u32(&bars->done));
-                if (!bar_wait_plain(smem_u32(&bars->done), 0u)) *abort_flag = 1;
-            }
+        }
+        if (lane == 0 && issued) {  // retire every MMA before the tensor memory is released
+            bar_commit(smem_u32(&bars->done));
+            if (!bar_wait_plain(smem_u32(&bars->done), 0u)) *abort_flag = 1;
         }
         __syncwarp();
     } else {
         // ------------------------------------------------------------ drain and epilogue
+        // the warp walks the chunks like the MMA warp (flags and panel entries 32 at a time);
+        // at every chunk that ends a period it drains the accumulators with the scales of
+        // that chunk's entries (all entries of one atom group in one scale group share them)
         const int quarter = warp & 3, half = (warp - 2) >> 2;
         const int arow = quarter * 32 + lane;
         const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
@@ -290,61 +311,72 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
 #pragma unroll
             for (int x = 0; x < 32; ++x) lws[(half * 32 + x) * MT + arow] = 0.f;
             bool first_period = true;
-            for (int c = 0; c < nch && ok;) {
-                // the period: chunks [c, c1) of one scale group
-                const int kk = p.kappa[c0 + c];
-                int c1 = c + 1;
-                while (c1 < nch && same_scale_group(kk, p.kappa[c0 + c1])) ++c1;
-                const int2 ent = p.chunks[c0 + c];
-                const int ea = p.scale_a[(int64_t)ent.x * MT + arow];
+            uint32_t mine = 0;
+            int2 ment = make_int2(0, 0);
+            for (int c = 0; c < nch && ok; ++c) {
+                if ((c & 31) == 0) {
+                    mine = c + lane < nch ? p.meta[c0 + c + lane] : 0u;
+                    ment = c + lane < nch ? p.chunks[c0 + c + lane] : make_int2(0, 0);
+                }
+                const uint32_t meta = __shfl_sync(0xffffffffu, mine, c & 31);
+                const int ea_ent = __shfl_sync(0xffffffffu, ment.x, c & 31);
+                const int eb_ent = __shfl_sync(0xffffffffu, ment.y, c & 31);
+                if (!(meta & PERIOD_LAST)) continue;
+                // scales first, so their loads overlap the wait for the accumulators
+                const int ea = p.scale_a[(int64_t)ea_ent * MT + arow];
+                const int4 *sb4 =
+                    reinterpret_cast<const int4 *>(p.scale_b + (int64_t)eb_ent * NT + half * 32);
+                const int4 s0 = __ldg(sb4), s1 = __ldg(sb4 + 1), s2 = __ldg(sb4 + 2),
+                           s3 = __ldg(sb4 + 3);
                 if (!bar_wait(smem_u32(&bars->acc_full), pg & 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const bool last_period = (c == nch - 1);
+#pragma unroll 1
+                for (int q = 0; q < 4; ++q) {  // eight columns at a time
+                    const int col0 = half * 32 + q * 8;
+                    const int4 sq = q == 0 ? s0 : q == 1 ? s1 : q == 2 ? s2 : s3;
+                    const uint32_t su[4] = {(uint32_t)sq.x, (uint32_t)sq.y, (uint32_t)sq.z,
+                                            (uint32_t)sq.w};
+                    uint32_t h[8], m[8], v[E_LEVELS][8];
+                    if (!first_period) {
+                        tm_ld8(lane_addr + E_COL_H + q * 8, h);
+                        tm_ld8(lane_addr + E_COL_M + q * 8, m);
+                    }
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int col0 = half * 32 + q * 16;
-                    uint32_t h[16], m[16];
+                    for (int lev = 0; lev < E_LEVELS; ++lev)
+                        tm_ld8(lane_addr + (uint32_t)(lev * NT) + q * 8, v[lev]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     if (first_period) {
 #pragma unroll
-                        for (int x = 0; x < 16; ++x) h[x] = m[x] = 0u;
-                    } else {
-                        tm_ld16(lane_addr + E_COL_H + q * 16, h);
-                        tm_ld16(lane_addr + E_COL_M + q * 16, m);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        for (int x = 0; x < 8; ++x) h[x] = m[x] = 0u;
                     }
-                    int eb[16];
 #pragma unroll
-                    for (int x = 0; x < 16; ++x)
-                        eb[x] = p.scale_b[(int64_t)ent.y * NT + col0 + x];
+                    for (int x = 0; x < 8; ++x) {
+                        const int ebx = (int)(int16_t)(su[x >> 1] >> (16 * (x & 1)));
+                        // a poisoned group's NaN digits made the accumulator NaN: pass it
+                        // on; groups without a nonzero value contribute nothing
+                        const bool poison = ea == EMU_POISON || ebx == EMU_POISON;
+                        if (!poison && (ea == EMU_NONE || ebx == EMU_NONE)) continue;
+                        const int e = poison ? 0 : ea + ebx - 14;
+                        float hh = __uint_as_float(h[x]), mm = __uint_as_float(m[x]);
+                        float &ll = lws[(col0 + x) * MT + arow];
 #pragma unroll
-                    for (int lev = 0; lev < E_LEVELS; ++lev) {
-                        uint32_t v[16];
-                        tm_ld16(lane_addr + (uint32_t)(lev * NT) + q * 16, v);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                        for (int x = 0; x < 16; ++x) {
-                            // a poisoned group's NaN digits made the accumulator NaN: pass it
-                            // on; groups without a nonzero value contribute nothing
-                            const bool poison = ea == EMU_POISON || eb[x] == EMU_POISON;
-                            if (!poison && (ea == EMU_NONE || eb[x] == EMU_NONE)) continue;
-                            const int e = poison ? 0 : ea + eb[x] - 14;
-                            float hh = __uint_as_float(h[x]), mm = __uint_as_float(m[x]);
-                            float &ll = lws[(col0 + x) * MT + arow];
-                            tf_add(hh, mm, ll, mul_pow2(__uint_as_float(v[x]), e));
-                            h[x] = __float_as_uint(hh);
-                            m[x] = __float_as_uint(mm);
-                        }
+                        for (int lev = 0; lev < E_LEVELS; ++lev)
+                            tf_add(hh, mm, ll, mul_pow2(__uint_as_float(v[lev][x]), e));
+                        h[x] = __float_as_uint(hh);
+                        m[x] = __float_as_uint(mm);
                     }
-                    tm_st16(lane_addr + E_COL_H + q * 16, h);
-                    tm_st16(lane_addr + E_COL_M + q * 16, m);
-                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                    if (c1 == nch && arow < GI * NB) {
+                    if (!last_period) {
+                        tm_st8(lane_addr + E_COL_H + q * 8, h);
+                        tm_st8(lane_addr + E_COL_M + q * 8, m);
+                    } else if (arow < GI * NB) {
                         // the tile's last period: C = beta C + alpha (h + m + l) in FP64
                         const int si = arow / NB, a = arow % NB;
 #pragma unroll
-                        for (int x = 0; x < 16; ++x) {
+                        for (int x = 0; x < 8; ++x) {
                             const int col = col0 + x, jl = col / NB, bo = col % NB;
                             if (jl >= GJ) continue;
                             const int32_t blk = __ldg(&p.cidx[((int64_t)tile * GI + si) * GJ + jl]);
@@ -357,11 +389,11 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
                         }
                     }
                 }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 bar_arrive(smem_u32(&bars->acc_empty));
                 ++pg;
                 first_period = false;
-                c = c1;
             }
             if (!ok) break;
             if (nch == 0 && arow < GI * NB) {

@@ -423,6 +423,21 @@ __device__ __forceinline__ uint32_t emu_off(int rows, int row, int col, int plan
                       (col & 1) * 128 + (row & 7) * 16);
 }
 
+// Scale-period flags of every chunk (one CTA per tile): a period is a run of a tile's
+// chunks whose K groups share a scale group (K group >> 2).
+__global__ void __launch_bounds__(256)
+k_emu_periods(const int64_t *kstart, const int32_t *kappa, uint8_t *meta)
+{
+    const int64_t c0 = kstart[blockIdx.x], c1 = kstart[blockIdx.x + 1];
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        const int sg = kappa[c] >> 2;
+        uint8_t f = 0;
+        if (c == c0 || (kappa[c - 1] >> 2) != sg) f |= 1;
+        if (c == c1 - 1 || (kappa[c + 1] >> 2) != sg) f |= 2;
+        meta[c] = f;
+    }
+}
+
 // Largest exponent (emu_exponent) of every scalar row of every A panel entry (one CTA
 // of 128 threads per entry = (M group, K group)): row r = (slot r / NB, orbital r % NB).
 template <int NB>
@@ -616,6 +631,7 @@ struct SplitPlan {
     DevBuf tiles, kstart, tile_kappa, chunks, cidx;
     DevBuf ga_ptr, ga_kappa, ga_group, hb_ptr, hb_kappa, hb_group;
     DevBuf ga_index, hb_index;  // block of every (slot, K-group atom) pair of every entry
+    DevBuf meta;                // emulated product: scale-period flags per chunk (on demand)
 };
 
 // Morton order of the atoms (positions quantised to 1024 per box edge).
@@ -996,7 +1012,7 @@ cq_status run_emu(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double alp
         a.n_tiles = b.tile1 - b.tile0;
         a.kstart = pl->kstart.as<int64_t>() + b.tile0;
         a.chunks = pl->chunks.as<int2>();
-        a.kappa = pl->tile_kappa.as<int32_t>();
+        a.meta = pl->meta.as<uint8_t>();
         a.cidx = pl->cidx.as<int32_t>() + (int64_t)b.tile0 * gr->gi * gr->gj;
         a.panel_a = (const uint8_t *)va;
         a.ea0 = b.e0;
@@ -1037,6 +1053,13 @@ cq_status cq_bsmm_emu(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pa
     if (st != CQ_OK) return st;
     if ((st = get_plan(ctx, pA, pB, pC, gr, &pl)) != CQ_OK) return st;
     if (pl->n_tiles == 0) return CQ_OK;
+    if (!pl->meta.ptr) {  // scale-period flags, built once per pattern triple
+        if ((st = cq_alloc(ctx, pl->meta, (size_t)pl->n_chunks + 16)) != CQ_OK) return st;
+        k_emu_periods<<<pl->n_tiles, 256, 0, ctx->stream>>>(
+            pl->kstart.as<int64_t>(), pl->tile_kappa.as<int32_t>(), pl->meta.as<uint8_t>());
+        cq_count_launch();
+        if ((st = cq_check_cuda(ctx, cudaGetLastError(), "emu periods")) != CQ_OK) return st;
+    }
     return nb == 9 ? run_emu<9>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops)
                    : run_emu<4>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops);
 }
