@@ -3,7 +3,7 @@
 //
 // Operands are eight BF16 digit planes per value (emu_digits.cuh): A_p, B_q with planes
 // pre-scaled by 2^(-8p), so the MMA of planes p and q lands at level p + q.  Per K step the
-// MMA thread issues the 36 products with p + q <= 7 into six FP32 accumulators in tensor
+// MMA thread issues the 36 products with p + q <= 7, level by level, into six FP32 accumulators in tensor
 // memory: levels 0 to 4 each alone -- over one scale period a level-l sum is an integer
 // times 2^(-8 l) of magnitude at most (l + 1) * 192 * 128^2 < 2^24 (192 K values per
 // period), hence exact -- and levels 5-7 together (rounded, but 2^-40 below level 0, so its
@@ -260,17 +260,20 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint64_t sa = da0 + (uint64_t)((s * E_STAGE) >> 4);
                         const uint64_t sb = db0 + (uint64_t)((s * E_STAGE) >> 4);
+                        // level by level (p + q ascending): back to back, the tensor cores
+                        // take these 36 products faster in this order than plane by plane
 #pragma unroll
-                        for (int pa = 0; pa < EMU_P; ++pa)
+                        for (int lv = 0; lv < EMU_P; ++lv)
 #pragma unroll
-                            for (int qb = 0; qb < EMU_P - pa; ++qb) {
-                                const int lev = pa + qb < E_LEVELS - 1 ? pa + qb : E_LEVELS - 1;
+                            for (int pa = 0; pa <= lv; ++pa) {
+                                const int qb = lv - pa;
+                                const int lev = lv < E_LEVELS - 1 ? lv : E_LEVELS - 1;
                                 const uint64_t ad = sa + (uint64_t)((pa * E_APLANE) >> 4);
                                 const uint64_t bd = sb + (uint64_t)((qb * E_BPLANE) >> 4);
                                 // the first product into each accumulator of a period
-                                // overwrites it: (0, q) for q < 6 in this order
+                                // overwrites it: (0, l) for l < 6 in this order
                                 const uint32_t acc =
-                                    (first && ks == 0 && pa == 0 && qb < E_LEVELS) ? 0u : 1u;
+                                    (first && ks == 0 && pa == 0 && lv < E_LEVELS) ? 0u : 1u;
                                 asm volatile(
                                     "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
@@ -361,11 +364,21 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
                         const bool poison = ea == EMU_POISON || ebx == EMU_POISON;
                         if (!poison && (ea == EMU_NONE || ebx == EMU_NONE)) continue;
                         const int e = poison ? 0 : ea + ebx - 14;
+                        // the three words in registers for the six additions (the smallest
+                        // one lives in shared memory between periods)
                         float hh = __uint_as_float(h[x]), mm = __uint_as_float(m[x]);
-                        float &ll = lws[(col0 + x) * MT + arow];
+                        float ll = lws[(col0 + x) * MT + arow];
+                        if (e >= -126 && e <= 127) {  // one exact scale factor for all levels
+                            const float sc = __uint_as_float((uint32_t)(e + 127) << 23);
 #pragma unroll
-                        for (int lev = 0; lev < E_LEVELS; ++lev)
-                            tf_add(hh, mm, ll, mul_pow2(__uint_as_float(v[lev][x]), e));
+                            for (int lev = 0; lev < E_LEVELS; ++lev)
+                                tf_add(hh, mm, ll, __uint_as_float(v[lev][x]) * sc);
+                        } else {
+#pragma unroll
+                            for (int lev = 0; lev < E_LEVELS; ++lev)
+                                tf_add(hh, mm, ll, mul_pow2(__uint_as_float(v[lev][x]), e));
+                        }
+                        lws[(col0 + x) * MT + arow] = ll;
                         h[x] = __float_as_uint(hh);
                         m[x] = __float_as_uint(mm);
                     }
