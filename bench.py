@@ -107,6 +107,10 @@ def parse():
                     help="with --converge: only the learned start and its split-BF16 phase on "
                          "the cell (no plain FP64 solve, no FP64 refinement), for cells whose "
                          "FP64 solve is too long for the bench")
+    ap.add_argument("--solvers", action="store_true",
+                    help="the solver options on the cell: Hotelling against the least-squares "
+                         "(CG) overlap inverse, and plain against T-preconditioned FP64 LNV to "
+                         "RMS gradient 1e-8 (steps and seconds)")
     ap.add_argument("--converge", action="store_true",
                     help="time full minimisations (plain FP64 vs learned guess + split-BF16 + "
                          "FP64 refinement) instead of the step benchmark")
@@ -844,6 +848,83 @@ def run_converge(args, dev):
     ctx.close()
 
 
+def run_solvers(args, dev):
+    """N4 and N2 at the benchmark's size.  Overlap inverse on P_L: 12 Hotelling steps against
+    the least-squares inverse by CG (from the same T_0, up to 40 steps), residual ||I - ST||_F
+    and seconds.  LNV from the same PM start (Hotelling T): plain against T-preconditioned
+    directions, FP64 products, to RMS gradient 1e-8; steps, seconds, energies."""
+    import torch
+
+    from paper_2205_08941_gb300 import build as B
+    B.build()
+    from paper_2205_08941_gb300 import cq
+    torch.cuda.set_device(dev)
+    cell, Spb, Hpb = make_inputs(args.ncell)
+    ctx = cq.Context(dev)
+    t = lambda a, dt: torch.tensor(a, dtype=dt, device=f"cuda:{dev}")
+    pos, nb = t(cell.pos, torch.float64), t(cell.nb, torch.int32)
+    pS = ctx.pattern(pos, cell.box, nb, WORKLOAD["r_S"])
+    pL = ctx.pattern(pos, cell.box, nb, WORKLOAD["r_L"])
+    up = lambda p, pb: ctx.scatter(p, t(pb.i, torch.int32), t(pb.j, torch.int32),
+                                   t(pb.off, torch.int64), t(pb.values, torch.float64))
+    S, H = up(pS, Spb), up(pS, Hpb)
+    n_e = 4.0 * cell.n_atoms
+    out = {"mode": "solvers", "workload": workload_name(cell.n_atoms)}
+    # overlap inverse: Hotelling against least-squares CG
+    T = ctx.zeros(pL)
+    ctx.hotelling_init(pS, S, pL, T)
+    ctx.hotelling_step(pS, S, pL, T)  # task lists and scratch before the clock
+    ctx.hotelling_init(pS, S, pL, T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hres = [ctx.hotelling_step(pS, S, pL, T) for _ in range(12)]
+    torch.cuda.synchronize()
+    t_h = time.perf_counter() - t0
+    Tc = ctx.zeros(pL)
+    ctx.hotelling_init(pS, S, pL, Tc)
+    ctx.overlap_inverse_cg(pS, S, pL, Tc, 1)
+    ctx.hotelling_init(pS, S, pL, Tc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cres, cg = ctx.overlap_inverse_cg(pS, S, pL, Tc, 40, 1e-6)
+    torch.cuda.synchronize()
+    t_c = time.perf_counter() - t0
+    # the Hotelling residual of the final T (one more step reports it)
+    Th = T.clone()
+    h_final = ctx.hotelling_step(pS, S, pL, Th)
+    Tc2 = Tc.clone()
+    c_final = ctx.hotelling_step(pS, S, pL, Tc2)
+    del Th, Tc2
+    out["overlap_inverse"] = {
+        "hotelling": {"steps": 12, "seconds": t_h, "resid_final": h_final,
+                      "resid_history": hres},
+        "least_squares_cg": {"steps": len(cres) - 1, "seconds": t_c, "resid_final": c_final,
+                             "resid_history": cres}}
+    # LNV: plain against preconditioned, from the same PM start
+    rows = {}
+    for name in ("plain", "preconditioned"):
+        L = ctx.zeros(pL)
+        torch.cuda.synchronize()
+        ctx.pm_guess(pS, S, H, pL, T, pL, L, n_e / 2.0)
+        lnv = ctx.lnv(pS, S, H, pL, L, n_e)
+        if name == "preconditioned":
+            lnv.set_preconditioner(pL, T)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, st = run_until(lnv, 1e-8, 80)
+        torch.cuda.synchronize()
+        rows[name] = {"steps": it, "seconds": time.perf_counter() - t0, "gnorm": st["gnorm"],
+                      "energy_per_atom": st["energy"] / cell.n_atoms,
+                      "flops_per_step": lnv.step_flops()}
+        lnv.close()
+        del L
+    rows["energy_diff_per_atom"] = abs(rows["plain"]["energy_per_atom"] -
+                                       rows["preconditioned"]["energy_per_atom"])
+    out["lnv_to_rms_1e-8"] = rows
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def run_sweep(args, dev):
     """Seconds per LNV step against the number of atoms, one GPU: for each cell size the
     patterns, Hotelling inverse and PM start are built (untimed), the LNV object takes two
@@ -880,6 +961,8 @@ def run_sweep(args, dev):
             L = ctx.zeros(pL)
             ctx.pm_guess(pS, S, H, pL, T, pL, L, n_e / 2.0)
             del T
+            if prec != cq.CQ_FP64:
+                ctx.release_cache()  # the set-up's FP64 task lists: tensor-core steps need none
             lnv = ctx.lnv(pS, S, H, pL, L, n_e, prec=prec)
             for _ in range(2):
                 lnv.step()
@@ -915,6 +998,9 @@ def main():
         return
     if args.converge:
         run_converge(args, int(os.environ.get("LOCAL_RANK", 0)))
+        return
+    if args.solvers:
+        run_solvers(args, int(os.environ.get("LOCAL_RANK", 0)))
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

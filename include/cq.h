@@ -82,6 +82,13 @@ cq_status cq_ctx_sync(cq_ctx *ctx);
 /* Cap the context's own device allocations at `bytes` (0 = no cap); an allocation beyond it
  * fails with CQ_ERR_NOMEM, as a real out-of-memory would.  Used to test that path. */
 cq_status cq_ctx_set_mem_limit(cq_ctx *ctx, int64_t bytes);
+/* Free everything the context caches to speed up later calls: (i, k, j) task lists, block
+ * maps, tensor-core tile plans and scratch buffers (patterns, values and LNV objects are
+ * untouched).  Later calls rebuild what they need, and LNV graph phases are captured anew.
+ * For working sets near the size of HBM: e.g. after the FP64 set-up of a large cell
+ * (Hotelling inverse, PM start), before tensor-core LNV steps that never use the FP64 task
+ * lists.  Synchronises; refused inside a graph capture. */
+cq_status cq_ctx_release_cache(cq_ctx *ctx);
 /* Bytes of device scratch the context currently holds. */
 int64_t cq_ctx_mem_used(const cq_ctx *ctx);
 /* Turn on (1) or off (0) CUDA-event timing of every block-product kernel launch on the

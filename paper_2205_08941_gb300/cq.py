@@ -106,6 +106,7 @@ SIGNATURES = {
     "cq_guess_forward": (_st, [_vp, _vp, _i64, _vp]),
     "cq_guess_apply": (_st, [_vp, _vp, _vp]),
     "cq_ctx_set_test_wait": (_st, [_vp, _i64]),
+    "cq_ctx_release_cache": (_st, [_vp]),
     "cq_trace_prod_static": (_st, [_vp, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.POINTER(ctypes.c_char_p)]),
 }
@@ -211,6 +212,10 @@ class Context:
 
     def set_autotune(self, on: bool):
         self._check(lib().cq_ctx_set_autotune(self.h, 1 if on else 0))
+
+    def release_cache(self):
+        """Free cached task lists, maps, tile plans and scratch (rebuilt on demand)."""
+        self._check(lib().cq_ctx_release_cache(self.h))
 
     def set_test_wait(self, cycles: int):
         """Test hook: split kernels make their first wait run out after `cycles` (0: off)."""

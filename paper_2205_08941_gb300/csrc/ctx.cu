@@ -653,6 +653,20 @@ extern "C" cq_status cq_ctx_set_graphs(cq_ctx *ctx, int on)
     return CQ_OK;
 }
 
+extern "C" cq_status cq_ctx_release_cache(cq_ctx *ctx)
+{
+    if (!ctx) return CQ_ERR_INVALID;
+    if (ctx->capturing) return cq_fail(ctx, CQ_ERR_INVALID, "release_cache inside a graph capture");
+    cq_status st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "release cache");
+    if (st != CQ_OK) return st;
+    ctx->tasks.clear();
+    ctx->maps.clear();
+    ctx->aux.clear();
+    ctx->scratch.clear();
+    ctx->scratch_gen++;  // captured graphs name the freed buffers: capture them again
+    return CQ_OK;
+}
+
 extern "C" cq_status cq_ctx_set_test_wait(cq_ctx *ctx, int64_t cycles)
 {
     if (!ctx || cycles < 0 || cycles > 100000000) return CQ_ERR_INVALID;

@@ -53,6 +53,8 @@ def guarded_start(ctx: cq.Context, guess: cq.Guess, pS, S, H, pT, T, pL, L, n_el
     Returns (lnv, used_learned, info)."""
     L_pm = ctx.zeros(pL)
     ctx.pm_guess(pS, S, H, pT, T, pL, L_pm, n_electrons / 2.0)
+    if prec != cq.CQ_FP64:
+        ctx.release_cache()  # the FP64 task lists of the set-up: tensor-core steps need none
     probe = ctx.lnv(pS, S, H, pL, L_pm, n_electrons, prec)
     s_pm = probe.state()
     probe.close()

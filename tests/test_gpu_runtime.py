@@ -82,3 +82,38 @@ def test_autotuner_picks_a_split_and_keeps_parity(built):
     assert_product_close(po[2], to_oracle(Cg, idx[2]), ref,
                          natural_scale(po[0], A, po[1], B, po[2], rows=rows), rows=rows)
     ctx.close()
+
+
+def test_release_cache_mid_run_changes_nothing(built):
+    """Dropping every cached task list, plan and scratch buffer between LNV steps (with graph
+    replay on) gives bitwise the same steps as a run that keeps them, and frees memory."""
+    def run(release):
+        c = cq.Context(0, stream=torch.cuda.Stream())
+        cell = I.diamond_cell(2, a=10.26, sigma=0.05, seed=1, norb=4)
+        Spb, Hpb = I.overlap_hamiltonian(cell, I.silicon_model(10.0))
+        pS, pL = gpu_pattern(c, cell, 10.0), gpu_pattern(c, cell, 12.0)
+        S, H = upload_pairs(c, pS, Spb), upload_pairs(c, pS, Hpb)
+        torch.cuda.synchronize()
+        T = c.zeros(pL)
+        torch.cuda.synchronize()
+        c.hotelling_init(pS, S, pL, T)
+        for _ in range(10):
+            c.hotelling_step(pS, S, pL, T)
+        L = c.zeros(pL)
+        torch.cuda.synchronize()
+        c.pm_guess(pS, S, H, pL, T, pL, L, 128.0)
+        c.set_graphs(True)
+        lnv = c.lnv(pS, S, H, pL, L, 256.0)
+        out = []
+        for k in range(6):
+            if release and k == 3:
+                before = c.mem_used()
+                c.release_cache()
+                assert c.mem_used() < before
+            r = lnv.step()
+            out.append((r["energy"], r["n_elec"], r["alpha"], r["n_corr"]))
+        lnv.close()
+        c.close()
+        return out
+
+    assert run(True) == run(False)
