@@ -334,14 +334,18 @@ cq_status run_phase(cq_lnv *s, int phase, const void *key, F body)
     if (!ctx->graphs) return body();
     cq_lnv::Graph &g = s->graphs[std::make_tuple(phase, key, (int)s->prec)];
     if (g.exec && g.gen != ctx->scratch_gen) {
-        // a scratch buffer the graph reads was reallocated since the capture: capture again
+        // a scratch buffer the graph reads was reallocated (or released) since the capture:
+        // run eagerly once more (rebuilding what was freed), then capture again
         cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
+        g.warm = false;
     }
     if (!g.exec) {
-        if (!g.warm) {
+        if (!g.warm || g.gen != ctx->scratch_gen) {
             g.warm = true;
-            return body();
+            const cq_status st = body();
+            g.gen = ctx->scratch_gen;  // the scratch this eager run left behind
+            return st;
         }
         const double f0 = s->flops;
         const int p0 = s->products;
