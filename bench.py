@@ -35,6 +35,10 @@ WORKLOAD = {"workload": "Si diamond 4096 atoms SZP (9 orb/atom, 36864 orbitals)"
             "ncell": 8, "a_bohr": 10.26, "sigma_bohr": 0.1, "seed": 2, "r_S": 14.0,
             "r_L": 16.0, "r_X": 30.0, "r_U": 44.0, "n_electrons": 16384}
 BF16_FALLBACK_TFLOPS = 1900.0
+# DRAM bytes per launch of the FP64 product kernel over the launches of one LNV step of the
+# 4096-atom cell, from one ncu capture of the current kernel
+# (profiles/bsmm_f64_traffic_si4096.md)
+FP64_TRAFFIC_PER_LAUNCH = 90.66e9
 
 
 METRIC = ("block-sparse GEMM GFLOP/s (useful FP64 flops) & s per LNV step, Si SZP; "
@@ -111,6 +115,12 @@ def parse():
                     help="the solver options on the cell: Hotelling against the least-squares "
                          "(CG) overlap inverse, and plain against T-preconditioned FP64 LNV to "
                          "RMS gradient 1e-8 (steps and seconds)")
+    ap.add_argument("--train-cells", type=int, default=6,
+                    help="with --converge: training cells for the learned start")
+    ap.add_argument("--train-ncell", type=int, default=3,
+                    help="with --converge: cells per edge of a training cell (3: 216 atoms)")
+    ap.add_argument("--train-split", action="store_true",
+                    help="with --converge: solve the training cells with split-BF16 steps")
     ap.add_argument("--converge", action="store_true",
                     help="time full minimisations (plain FP64 vs learned guess + split-BF16 + "
                          "FP64 refinement) instead of the step benchmark")
@@ -567,15 +577,17 @@ def run_cq(args, rank, world, local_rank):
         # FP64-accurate products on the tensor cores: the same K steps from the same L0
         L.copy_(L0)
         lnv.set_precision(cq.CQ_FP64_EMU)
-        res["emu"] = timed(args.steps, "emu")
+        k_emu = min(args.steps, 3)  # an extra leg: at most three steps keep the bench short
+        res["emu"] = timed(k_emu, "emu")
         r = res["emu"]
         n_launch, kern_ms, kern_flops, mma_flops = r["stats"]
         peaks = measured_peaks()
         bf16 = (peaks or {}).get("bf16_tflops")
+        fp64_step_ms = res["fp64"]["ms"] / args.steps if "fp64" in res else None
         emu = {"value": r["flops_all"] / (r["ms"] * 1e-3) / 1e9, "unit": "GFLOP/s",
-               "dtype": "f64 emulated: 7 bf16 digit planes, exact level sums",
-               "s_per_lnv_step": r["ms"] / args.steps / 1e3,
-               "speedup_vs_fp64_step": (res["fp64"]["ms"] / r["ms"]) if "fp64" in res else None,
+               "dtype": "f64 emulated: 8 bf16 digit planes, exact level sums", "steps": k_emu,
+               "s_per_lnv_step": r["ms"] / k_emu / 1e3,
+               "speedup_vs_fp64_step": (fp64_step_ms / (r["ms"] / k_emu)) if fp64_step_ms else None,
                "roofline": {"bound": "tensor", "kernel": "k_bsmm_emu",
                             "achieved": mma_flops / (kern_ms * 1e-3) / 1e12 if kern_ms else None,
                             "peak": bf16 or BF16_FALLBACK_TFLOPS, "unit": "TFLOP/s",
@@ -593,6 +605,10 @@ def run_cq(args, rank, world, local_rank):
             emu["same_step_decisions_as_fp64"] = all(
                 (a["restart"], a["fallback"], a["n_corr"]) == (b["restart"], b["fallback"], b["n_corr"])
                 for a, b in zip(r["reps"], res["fp64"]["reps"]))
+            # the FP64 trajectory after the same number of steps
+            E_k = res["fp64"]["reps"][k_emu - 1]["energy"]
+            emu["energy_diff_per_atom_vs_fp64"] = abs(r["reps"][-1]["energy"] - E_k) / cell.n_atoms
+            emu.pop("L_rel_diff_vs_fp64", None)
 
     batched = None
     if not args.no_batch:
@@ -627,7 +643,8 @@ def run_cq(args, rank, world, local_rank):
             "roofline": {"bound": "alu", "kernel": "k_bsmm_f64_uniform",
                          "achieved": achieved, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
                          "frac": (achieved / (peak_fp64 / 1e12)) if achieved else None,
-                         "traffic": None,
+                         "traffic": FP64_TRAFFIC_PER_LAUNCH if cell.n_atoms == 4096 else None,
+                         "traffic_source": "ncu dram bytes per launch, one LNV step of this cell",
                          "peak_source": "in-library FP64 probe (best of FMA and DMMA chains)",
                          "launches": n_launch, "kernel_ms": kern_ms,
                          "kernel_share": kern_ms / ms if ms > 0 else None},
@@ -734,28 +751,54 @@ def run_converge(args, dev):
     def run(lnv, gtol, cap, trace=None, t0=0.0, fp64=True, stall=None):
         return run_until(lnv, gtol, cap, trace, t0, fp64, stall)
 
-    # training set: converged L of small thermally displaced cells
+    # training set: converged L of small thermally displaced cells (seeds 1000 + k, jitter
+    # sigma ~ U[0.1, 0.3] bohr), solved in FP64 to RMS 1e-7 or, with --train-split, by
+    # split-BF16 steps to RMS 1e-6 (the targets only have to make a good start)
     t0 = time.perf_counter()
     rng = np.random.default_rng(1000)
     samples, keep = [], []
-    for k in range(6):
-        c = I.diamond_cell(3, a=WORKLOAD["a_bohr"], sigma=float(rng.uniform(0.1, 0.3)),
-                           seed=1000 + k, norb=9)
+    train_prec = cq.CQ_SPLIT_BF16X3 if args.train_split else cq.CQ_FP64
+    for k in range(args.train_cells):
+        c = I.diamond_cell(args.train_ncell, a=WORKLOAD["a_bohr"],
+                           sigma=float(rng.uniform(0.1, 0.3)), seed=1000 + k, norb=9)
         s_, h_ = I.overlap_hamiltonian(c, I.silicon_model(rS))
         pS, pL, S, H, T = setup(c, s_, h_)
         L = ctx.zeros(pL)
         ctx.pm_guess(pS, S, H, pL, T, pL, L, 2.0 * c.n_atoms)
-        lnv = ctx.lnv(pS, S, H, pL, L, 4.0 * c.n_atoms)
-        run(lnv, 1e-7, 80)
+        lnv = ctx.lnv(pS, S, H, pL, L, 4.0 * c.n_atoms, prec=train_prec)
+        if args.train_split:
+            run(lnv, 1e-6, 80, stall=0.9)
+        else:
+            run(lnv, 1e-7, 80)
         lnv.close()
         samples.append((pL, L))
-        keep.append((pS, S, H, T))
+        del pS, S, H, T
+        if (k + 1) % 16 == 0:
+            ctx.release_cache()  # every cell has its own patterns: drop their plans
+    t_data = time.perf_counter() - t0
     guess = cq.Guess(ctx, seed=11)
     desc, targ = learned.training_set(guess, samples)
-    hist = learned.train(guess, desc, targ, epochs=60, batch=4096, lr=2e-3, lr_decay=0.96)
     torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    epochs = 60
+    hist = learned.train(guess, desc, targ, epochs=epochs, batch=4096, lr=2e-3, lr_decay=0.96)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t1
     t_train = time.perf_counter() - t0
     n_samples = int(desc.shape[0])
+    # MLP work of the fit: forward 2 sum(d_l d_l+1) flops per sample, backward twice that
+    dims = (64, 256, 256, 256, 81)
+    fwd = 2.0 * sum(a * b for a, b in zip(dims, dims[1:]))
+    mlp_tflops = 3.0 * fwd * n_samples * epochs / t_fit / 1e12
+    peaks = measured_peaks()
+    bf16 = (peaks or {}).get("bf16_tflops")
+    training = {"cells": args.train_cells, "atoms_per_cell": 8 * args.train_ncell ** 3,
+                "solver": "split-BF16 to RMS 1e-6" if args.train_split else "FP64 to RMS 1e-7",
+                "samples": n_samples, "epochs": epochs, "seconds": t_train,
+                "data_seconds": t_data, "fit_seconds": t_fit,
+                "loss_first_last": [hist[0], hist[-1]],
+                "mlp_tflops": mlp_tflops,
+                "mlp_frac_of_bf16_peak": mlp_tflops / bf16 if bf16 else None}
     del samples, keep, desc, targ
 
     cell, Spb, Hpb = make_inputs(args.ncell)
@@ -781,8 +824,7 @@ def run_converge(args, dev):
             "start_seconds": t_start, "split_steps": it, "split_seconds": t_all - t_start,
             "gnorm": st["gnorm"], "energy_per_atom": st["energy"] / cell.n_atoms,
             "gnorm_trace": [x[2] for x in tr],
-            "training": {"cells": 6, "atoms_per_cell": 216, "samples": n_samples,
-                         "seconds": t_train}}), flush=True)
+            "training": training}), flush=True)
         guess.close()
         ctx.close()
         return
@@ -841,8 +883,7 @@ def run_converge(args, dev):
             "within_1e-6_per_atom": within,
             # intrinsic stopping rule for both: FP64 energy change per step < 1e-7 Ha/atom
             "stop_dE_1e-7_per_atom": stop_rule,
-            "training": {"cells": 6, "atoms_per_cell": 216, "samples": n_samples,
-                         "loss_first_last": [hist[0], hist[-1]], "seconds": t_train}}
+            "training": training}
     print(json.dumps(line), flush=True)
     guess.close()
     ctx.close()

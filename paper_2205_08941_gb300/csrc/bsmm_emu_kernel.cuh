@@ -368,22 +368,15 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
                         // one lives in shared memory between periods)
                         float hh = __uint_as_float(h[x]), mm = __uint_as_float(m[x]);
                         float ll = lws[(col0 + x) * MT + arow];
-                        const bool normal = e >= -126 && e <= 127;
-                        const float sc = normal ? __uint_as_float((uint32_t)(e + 127) << 23) : 1.f;
+                        if (e >= -126 && e <= 127) {  // one exact scale factor for all levels
+                            const float sc = __uint_as_float((uint32_t)(e + 127) << 23);
 #pragma unroll
-                        for (int lev = 0; lev < E_LEVELS; ++lev) {
-                            // one exact scale factor for all levels (rarely two steps)
-                            const float vs = normal ? __uint_as_float(v[lev][x]) * sc
-                                                    : mul_pow2(__uint_as_float(v[lev][x]), e);
-                            if (lev < 3) {
-                                tf_add(hh, mm, ll, vs);
-                            } else {
-                                // levels 3-5 lie 2^-24 and more below level 0: one
-                                // error-free sum into (m, l) carries them exactly
-                                const float sm = mm + vs, bp = sm - mm;
-                                ll += (mm - (sm - bp)) + (vs - bp);
-                                mm = sm;
-                            }
+                            for (int lev = 0; lev < E_LEVELS; ++lev)
+                                tf_add(hh, mm, ll, __uint_as_float(v[lev][x]) * sc);
+                        } else {
+#pragma unroll
+                            for (int lev = 0; lev < E_LEVELS; ++lev)
+                                tf_add(hh, mm, ll, mul_pow2(__uint_as_float(v[lev][x]), e));
                         }
                         lws[(col0 + x) * MT + arow] = ll;
                         h[x] = __float_as_uint(hh);
