@@ -9,28 +9,34 @@
 //
 // Local densification.  9x9 blocks do not fit MMA shapes, so atoms are grouped in space
 // (Morton order): an M group holds floor(128/nb) atoms (126 rows for nb = 9), an N group
-// floor(64/nb) atoms, a K group CA atoms (4 for nb = 9, 12 for nb = 4).  A work tile is a
-// pair (M group g, N group h) that holds at least one block of P_C; its chunks are the K
-// groups that contain an atom k with (i, k) in P_A for some i in g and (k, j) in P_B for
-// some j in h.  Absent blocks are zero.  Every C block belongs to exactly one tile, so
-// there are no atomics.
+// floor(64/nb) atoms.  A work tile is a pair (M group g, N group h) that holds at least one
+// block of P_C; its K atoms are the atoms k with (i, k) in P_A for some i in g and (k, j)
+// in P_B for some j in h.  Absent blocks are zero.  Every C block belongs to exactly one
+// tile, so there are no atomics.
 //
-// K layout.  Along K an atom's orbitals are split into a "main" piece of 8 values (one
-// 16-byte core-matrix row) and a "tail" of 4 values (half a core-matrix row; for nb = 9:
-// orbital 8 and three zeros, for nb = 4: all four orbitals).  A chunk of 48 K values (six
-// core-matrix columns, three MMA K steps) holds 4 atoms of 9 orbitals (mains in columns
-// 0-3, tails paired in columns 4-5) or 12 atoms of 4 orbitals (tails only), so 9-orbital
-// atoms cost 12 K values instead of 16.
+// K layout (one MMA K step = 16 values = two core-matrix columns of 8).  An atom's orbitals
+// are split into a main piece of 8 (orbitals 0-7, nb = 9 only) and a tail of nb - 8 (or
+// nb) values.  A main K step holds the main pieces of two K atoms of the tile, paired in
+// order, so a tile's main steps follow its own K atom set; a tail K step holds the tails
+// of one fixed tail group (16 consecutive atoms in Morton order for nb = 9, 4 for nb = 4),
+// taken when the tile has a K atom in the group.  A 9-orbital atom thus costs 8 K values
+// plus a sixteenth of a tail step.
 //
-// Panels.  Before each product the operands are split and packed into panels that are
-// byte-for-byte the shared-memory image of one chunk in the canonical no-swizzle K-major
-// layout (core matrix = 8 rows x 16 bytes; LBO = 128 B between K-adjacent core matrices,
-// SBO = 768 B between 8-row groups): an A panel per (M group, K group) pair that has a
-// block of P_A (3 planes x 128 rows x 48 K, 36 KB), a B panel per (N group, K group) pair
-// that has a block of P_B (3 planes x 64 rows, 18 KB).  The tile kernel then moves each
-// chunk with two TMA bulk copies; one thread issues the MMAs, eight warps drain the
-// accumulators (bsmm_split_kernel.cuh).  A panels are packed in batches of M groups so
-// that their scratch stays below A_PANEL_CAP bytes.
+// Pieces.  Before each product the operands are split and packed into pieces that are
+// byte-for-byte shared-memory images in the canonical no-swizzle K-major layout (core
+// matrix = 8 rows x 16 bytes; the 8-row groups of one core column adjacent, 128 B apart):
+// an A main piece per (M group, atom k) with a block of P_A (3 planes x 128 rows x 8 K,
+// 6 KB), an A tail piece per (M group, tail group) with a block (3 planes x 2 columns,
+// 12 KB), and B pieces per N group likewise (64 rows: 3 KB and 6 KB).  Shared memory holds
+// a K step in an 18 KB slot, so every step costs the same; the descriptors of a main step
+// reach its second atom's column through the leading byte offset, those of a tail step
+// its second column.  The tile kernel moves each piece with one TMA bulk copy; one thread
+// issues the MMAs, eight warps drain the accumulators (bsmm_split_kernel.cuh).  A pieces
+// are packed in batches of M groups so that their scratch stays below A_PANEL_CAP bytes.
+//
+// The emulated-FP64 product (bsmm_emu_kernel.cuh) keeps fixed K groups of CA atoms (4 for
+// nb = 9, 12 for nb = 4) packed into one panel per (atom group, K group) pair, because its
+// scale groups are runs of K groups.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -47,18 +53,30 @@ constexpr int ST = 320;                      // threads per CTA (10 warps)
 constexpr int MT = 128, NT = 64, KCH = 48;   // tile M, N and K chunk
 constexpr int KSTEPS = KCH / 16;             // MMA K steps per chunk
 constexpr int TAILW = 4;                     // values in an atom's tail piece
-constexpr int SBO = (KCH / 8) * 128;         // bytes between 8-row groups
-constexpr int A_PLANE = MT * KCH * 2;        // 12 KB
-constexpr int B_PLANE = NT * KCH * 2;        // 6 KB
-constexpr int A_CHUNK = 3 * A_PLANE;         // one packed A panel
-constexpr int B_CHUNK = 3 * B_PLANE;         // one packed B panel
-constexpr int STAGE = A_CHUNK + B_CHUNK;
+constexpr int A_CHUNK = 3 * MT * KCH * 2;   // 36 KB: three planes of 128 rows x 48 K
+constexpr int B_CHUNK = 3 * NT * KCH * 2;   // 18 KB
+constexpr int STAGE = A_CHUNK + B_CHUNK;    // one shared-memory stage of the split kernel
 constexpr int BAR_BYTES = 256;
 constexpr int DRAIN = 4;                     // chunks per FP32 accumulation period
 constexpr int NACC = 4;                      // FP32 accumulators in tensor memory
 constexpr int TMEM_COLS = NACC * NT;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 constexpr size_t A_PANEL_CAP = (size_t)12 << 30;  // scratch bound for one batch of A panels
+
+// Split-product pieces and the shared-memory slots of one stage (KSTEPS K steps).
+constexpr int COLB_A = MT * 16, COLB_B = NT * 16;  // one core column: 2 KB (A), 1 KB (B)
+constexpr int A_MAIN = 3 * COLB_A;                 // 6 KB: planes x one column
+constexpr int B_MAIN = 3 * COLB_B;                 // 3 KB
+constexpr int A_TAIL = 2 * A_MAIN;                 // 12 KB: planes x two columns
+constexpr int B_TAIL = 2 * B_MAIN;                 // 6 KB
+constexpr int A_SLOT = A_TAIL, B_SLOT = B_TAIL;    // a K step's room in a stage
+constexpr int B_SLOTS = KSTEPS * A_SLOT;           // stage offset of the B slots
+static_assert(KSTEPS * (A_SLOT + B_SLOT) == STAGE, "stage layout");
+
+// Main and tail widths of an atom's K values, and atoms per tail group.
+template <int NB> struct KPieces;
+template <> struct KPieces<9> { static constexpr int MAINW = 8, TW = 1, TG = 16; };
+template <> struct KPieces<4> { static constexpr int MAINW = 0, TW = 4, TG = 4; };
 
 // Atoms per chunk and core-matrix columns of an atom's pieces.
 template <int NB> struct KLayout;
@@ -78,19 +96,23 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// byte offset of (row, core-matrix column, byte) in the canonical no-swizzle K-major layout
-__host__ __device__ __forceinline__ uint32_t tile_off(int row, int col, int byte)
+// byte offset of (plane, core column, row) in a piece: planes plane_b apart, core columns
+// col_b apart, each column the 8-row groups of its rows 128 B apart
+__host__ __device__ __forceinline__ uint32_t piece_off(int plane, int plane_b, int col, int col_b,
+                                                       int row)
 {
-    return (uint32_t)((row >> 3) * SBO + col * 128 + (row & 7) * 16 + byte);
+    return (uint32_t)(plane * plane_b + col * col_b + (row >> 3) * 128 + (row & 7) * 16);
 }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+// shared-memory descriptor, no swizzle: lbo bytes between the two K-adjacent core columns
+// of a K step, 128 bytes between 8-row groups
+__device__ __forceinline__ uint64_t piece_desc(uint32_t saddr, uint32_t lbo)
 {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)(128 >> 4) << 16;    // leading (K) byte offset
-    d |= (uint64_t)(SBO >> 4) << 32;    // stride (M/N) byte offset
-    d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
-    return d;                           // base offset 0, no swizzle
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;  // leading (K) byte offset
+    d |= (uint64_t)(128 >> 4) << 32;             // stride (M/N) byte offset
+    d |= (uint64_t)1 << 46;                      // descriptor version for tcgen05
+    return d;                                    // base offset 0, no swizzle
 }
 
 // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N = 64, M = 128
@@ -248,6 +270,52 @@ k_tile_chunks(const int2 *tiles, const int64_t *kstart, const int32_t *tile_kapp
     }
 }
 
+// position of key in the ascending list lst[lo, hi) (the key is present)
+__device__ __forceinline__ int64_t list_pos(const int32_t *lst, int64_t lo, int64_t hi, int key)
+{
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (lst[mid] < key)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// K-step table of the split product (one CTA per tile): first the main steps, pairing the
+// tile's K atoms (Morton ranks, ascending) two by two -- (A main entry, second A main entry
+// or -1, B main entry, second B main entry or -1) -- then one tail step per tail group the
+// tile touches -- (A tail entry, -1, B tail entry, -1).  Entries index the M group's and
+// N group's piece lists.
+__global__ void __launch_bounds__(256)
+k_tile_steps(const int2 *tiles, const int64_t *ka_start, const int32_t *tile_rank,
+             const int64_t *kt_start, const int32_t *tile_tau, const int64_t *step_start,
+             const int64_t *gm_ptr, const int32_t *gm_key, const int64_t *hm_ptr,
+             const int32_t *hm_key, const int64_t *gt_ptr, const int32_t *gt_key,
+             const int64_t *ht_ptr, const int32_t *ht_key, int4 *steps)
+{
+    const int2 t = tiles[blockIdx.x];
+    const int64_t a0 = ka_start[blockIdx.x], na = ka_start[blockIdx.x + 1] - a0;
+    const int64_t t0 = kt_start[blockIdx.x], nt = kt_start[blockIdx.x + 1] - t0;
+    const int64_t nm = (na + 1) / 2, s0 = step_start[blockIdx.x];
+    for (int64_t q = threadIdx.x; q < nm; q += blockDim.x) {
+        const int k0 = tile_rank[a0 + 2 * q];
+        const int k1 = 2 * q + 1 < na ? tile_rank[a0 + 2 * q + 1] : -1;
+        int4 e;
+        e.x = (int)list_pos(gm_key, gm_ptr[t.x], gm_ptr[t.x + 1], k0);
+        e.y = k1 < 0 ? -1 : (int)list_pos(gm_key, gm_ptr[t.x], gm_ptr[t.x + 1], k1);
+        e.z = (int)list_pos(hm_key, hm_ptr[t.y], hm_ptr[t.y + 1], k0);
+        e.w = k1 < 0 ? -1 : (int)list_pos(hm_key, hm_ptr[t.y], hm_ptr[t.y + 1], k1);
+        steps[s0 + q] = e;
+    }
+    for (int64_t q = threadIdx.x; q < nt; q += blockDim.x) {
+        const int tau = tile_tau[t0 + q];
+        steps[s0 + nm + q] = make_int4((int)list_pos(gt_key, gt_ptr[t.x], gt_ptr[t.x + 1], tau), -1,
+                                       (int)list_pos(ht_key, ht_ptr[t.y], ht_ptr[t.y + 1], tau), -1);
+    }
+}
+
 // C block of every (M slot, N slot) pair of each tile: index into P_C or -1, so that the
 // epilogue needs one independent load per block instead of a binary search.
 __global__ void __launch_bounds__(256)
@@ -270,43 +338,22 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-// Writes one row of the K pieces of a pair of atoms (a0 even, a0 + 1) of a panel, three
-// planes: x0[m], x1[m] (m < MAINW + 4) split into BF16 terms.  Every store is a whole
-// 16-byte core-matrix row: the two main pieces and the column the two tails share.
-template <int NB>
-__device__ __forceinline__ void put_pair(uint8_t *panel, int plane_bytes, int r, int a0,
-                                         const double (&x0)[KLayout<NB>::MAINW + TAILW],
-                                         const double (&x1)[KLayout<NB>::MAINW + TAILW])
+// Three BF16 planes of eight values x[0..7] (split3), stored as one 16-byte core-matrix
+// row per plane at offsets off + plane * plane_b.
+__device__ __forceinline__ void put_row3(uint8_t *dst, uint32_t off, int plane_b,
+                                         const double (&x)[8])
 {
-    constexpr int MW = KLayout<NB>::MAINW, KA = MW + TAILW;
-    __nv_bfloat16 v0[3][KA], v1[3][KA];
+    __nv_bfloat16 v[3][8];
 #pragma unroll
-    for (int m = 0; m < KA; ++m) {
-        split3(x0[m], v0[0][m], v0[1][m], v0[2][m]);
-        split3(x1[m], v1[0][m], v1[1][m], v1[2][m]);
-    }
+    for (int m = 0; m < 8; ++m) split3(x[m], v[0][m], v[1][m], v[2][m]);
 #pragma unroll
     for (int pl = 0; pl < 3; ++pl) {
-        uint8_t *base = panel + pl * plane_bytes;
-        if (MW) {
-            uint4 w0, w1;
-            w0.x = pack_bf16x2(v0[pl][0], v0[pl][1]);
-            w0.y = pack_bf16x2(v0[pl][2], v0[pl][3]);
-            w0.z = pack_bf16x2(v0[pl][4], v0[pl][5]);
-            w0.w = pack_bf16x2(v0[pl][6], v0[pl][7]);
-            w1.x = pack_bf16x2(v1[pl][0], v1[pl][1]);
-            w1.y = pack_bf16x2(v1[pl][2], v1[pl][3]);
-            w1.z = pack_bf16x2(v1[pl][4], v1[pl][5]);
-            w1.w = pack_bf16x2(v1[pl][6], v1[pl][7]);
-            *reinterpret_cast<uint4 *>(base + tile_off(r, KLayout<NB>::main_col(a0), 0)) = w0;
-            *reinterpret_cast<uint4 *>(base + tile_off(r, KLayout<NB>::main_col(a0 + 1), 0)) = w1;
-        }
-        uint4 t;
-        t.x = pack_bf16x2(v0[pl][MW], v0[pl][MW + 1]);
-        t.y = pack_bf16x2(v0[pl][MW + 2], v0[pl][MW + 3]);
-        t.z = pack_bf16x2(v1[pl][MW], v1[pl][MW + 1]);
-        t.w = pack_bf16x2(v1[pl][MW + 2], v1[pl][MW + 3]);
-        *reinterpret_cast<uint4 *>(base + tile_off(r, KLayout<NB>::tail_col(a0), 0)) = t;
+        uint4 w;
+        w.x = pack_bf16x2(v[pl][0], v[pl][1]);
+        w.y = pack_bf16x2(v[pl][2], v[pl][3]);
+        w.z = pack_bf16x2(v[pl][4], v[pl][5]);
+        w.w = pack_bf16x2(v[pl][6], v[pl][7]);
+        *reinterpret_cast<uint4 *>(dst + off + pl * plane_b) = w;
     }
 }
 
@@ -330,55 +377,54 @@ k_panel_index(int gsize, int ca, const int32_t *ent_group, const int32_t *ent_ka
     }
 }
 
-// A panels of entries [e0, e0 + gridDim.x) (one CTA per entry = (M group g, K group kk)):
-// row r = (slot r / NB of g, orbital o = r % NB), K = (atom a of kk, orbital m): A_ik[o][m].
-template <int NB>
+// Main pieces of entries [e0, e0 + n) (one thread per (entry, row)), entry = (atom group,
+// K atom k), index = its block per slot (k_panel_index with one atom per K group).  A side
+// (LEFT): row r = (slot r / NB, orbital o), K = orbital m < 8 of k: A_ik[o][m]; B side: row
+// r = (slot, orbital o of j), K = m: B_kj[m][o].
+template <int NB, bool LEFT>
 __global__ void __launch_bounds__(256)
-k_pack_a(int64_t e0, const int32_t *index, const double *__restrict__ A, int stride,
-         uint8_t *panels)
+k_pack_main(int64_t e0, int64_t n, const int32_t *index, const double *__restrict__ X,
+            int stride, uint8_t *pieces)
 {
-    constexpr int GI = MT / NB, CA = KLayout<NB>::CA, KA = KLayout<NB>::MAINW + TAILW;
-    const int32_t *blk = index + (e0 + blockIdx.x) * (GI * CA);
-    uint8_t *panel = panels + (int64_t)blockIdx.x * A_CHUNK;
-    for (int q = threadIdx.x; q < MT * (CA / 2); q += blockDim.x) {
-        const int a0 = 2 * (q / MT), r = q % MT;
-        const bool row = r < GI * NB;
-        const int64_t b0 = row ? __ldg(&blk[(r / NB) * CA + a0]) : -1;
-        const int64_t b1 = row ? __ldg(&blk[(r / NB) * CA + a0 + 1]) : -1;
-        const int o = r % NB;
-        double x0[KA], x1[KA];
+    constexpr int ROWS = LEFT ? MT : NT, G = ROWS / NB, COLB = LEFT ? COLB_A : COLB_B;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n * ROWS) return;
+    const int64_t el = q / ROWS;
+    const int r = (int)(q % ROWS), o = r % NB;
+    const int64_t b = r < G * NB ? __ldg(&index[(e0 + el) * G + r / NB]) : -1;
+    double x[8];
 #pragma unroll
-        for (int m = 0; m < KA; ++m) {
-            x0[m] = (b0 >= 0 && m < NB) ? A[b0 * stride + o * NB + m] : 0.0;
-            x1[m] = (b1 >= 0 && m < NB) ? A[b1 * stride + o * NB + m] : 0.0;
-        }
-        put_pair<NB>(panel, A_PLANE, r, a0, x0, x1);
-    }
+    for (int m = 0; m < 8; ++m)
+        x[m] = b < 0 ? 0.0 : (LEFT ? X[b * stride + o * NB + m] : X[b * stride + m * NB + o]);
+    put_row3(pieces + el * (3 * COLB), piece_off(0, COLB, 0, 0, r), COLB, x);
 }
 
-// B panels (one CTA per entry = (N group h, K group kk)): row r = (slot r / NB of h,
-// orbital o of j), K = (atom a of kk, orbital m): B_kj[m][o].
-template <int NB>
+// Tail pieces of entries [e0, e0 + n) (one thread per (entry, row)), entry = (atom group,
+// tail group), index = its block per (slot, atom u of the tail group).  K position
+// u * TW + m (two core columns) = orbital MAINW + m of atom u.
+template <int NB, bool LEFT>
 __global__ void __launch_bounds__(256)
-k_pack_b(const int32_t *index, const double *__restrict__ B, int stride, uint8_t *panels)
+k_pack_tail(int64_t e0, int64_t n, const int32_t *index, const double *__restrict__ X,
+            int stride, uint8_t *pieces)
 {
-    constexpr int GJ = NT / NB, CA = KLayout<NB>::CA, KA = KLayout<NB>::MAINW + TAILW;
-    const int64_t e = blockIdx.x;
-    const int32_t *blk = index + e * (GJ * CA);
-    uint8_t *panel = panels + e * B_CHUNK;
-    for (int q = threadIdx.x; q < NT * (CA / 2); q += blockDim.x) {
-        const int a0 = 2 * (q / NT), r = q % NT;
-        const bool row = r < GJ * NB;
-        const int64_t b0 = row ? __ldg(&blk[(r / NB) * CA + a0]) : -1;
-        const int64_t b1 = row ? __ldg(&blk[(r / NB) * CA + a0 + 1]) : -1;
-        const int o = r % NB;
-        double x0[KA], x1[KA];
+    constexpr int ROWS = LEFT ? MT : NT, G = ROWS / NB, COLB = LEFT ? COLB_A : COLB_B;
+    constexpr int MW = KPieces<NB>::MAINW, TW = KPieces<NB>::TW, TG = KPieces<NB>::TG;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n * ROWS) return;
+    const int64_t el = q / ROWS;
+    const int r = (int)(q % ROWS), o = r % NB;
+    const int32_t *blk = index + ((e0 + el) * G + (r < G * NB ? r / NB : 0)) * TG;
+    uint8_t *piece = pieces + el * (6 * COLB);
 #pragma unroll
-        for (int m = 0; m < KA; ++m) {
-            x0[m] = (b0 >= 0 && m < NB) ? B[b0 * stride + m * NB + o] : 0.0;
-            x1[m] = (b1 >= 0 && m < NB) ? B[b1 * stride + m * NB + o] : 0.0;
+    for (int c = 0; c < 2; ++c) {
+        double x[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const int pos = 8 * c + v, u = pos / TW, m = MW + pos % TW;
+            const int64_t b = r < G * NB ? __ldg(&blk[u]) : -1;
+            x[v] = b < 0 ? 0.0 : (LEFT ? X[b * stride + o * NB + m] : X[b * stride + m * NB + o]);
         }
-        put_pair<NB>(panel, B_PLANE, r, a0, x0, x1);
+        put_row3(piece, piece_off(0, 2 * COLB, c, COLB, r), 2 * COLB, x);
     }
 }
 
@@ -393,12 +439,17 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x)
 
 struct SplitArgs {
     int n_tiles;              // tiles of this launch
-    const int64_t *kstart;    // chunk range of each tile (n_tiles + 1, into chunks)
-    const int2 *chunks;       // (A panel entry, B panel entry) per chunk
+    const int64_t *kstart;    // K-step range of each tile (n_tiles + 1, into steps)
+    const int32_t *nmain;     // main K steps of each tile (they come first)
+    const int4 *steps;        // piece entries of every K step (k_tile_steps)
     const int32_t *cidx;      // C block of each (M slot, N slot) pair of each tile
-    const uint8_t *panel_a;   // A panels of entries [ea0, ...)
-    int64_t ea0;
-    const uint8_t *panel_b;   // all B panels
+    const uint8_t *a_main;    // A main pieces of entries [am0, ...)
+    int64_t am0;
+    const uint8_t *a_tail;    // A tail pieces of entries [at0, ...)
+    int64_t at0;
+    const uint8_t *b_main;    // all B main pieces
+    const uint8_t *b_tail;    // all B tail pieces
+    const uint8_t *zero;      // an all-zero A main piece (stands for a missing second atom)
     double *C;
     int c_stride;
     double alpha, beta;
@@ -615,6 +666,9 @@ struct Groups {
     int gi = 0, gj = 0, ca = 0;      // atoms per M, N and K group
     int n_g = 0, n_h = 0, n_kappa = 0;
     DevBuf g_atoms, h_atoms, kg_atoms, g_of, h_of, kg_of;
+    // split product: K atoms by Morton rank, tail groups of tg consecutive ranks
+    int tg = 0, n_tau = 0;
+    DevBuf rank_atoms, rank_of, tg_atoms, tg_of;
 };
 
 struct Batch {
@@ -632,6 +686,31 @@ struct SplitPlan {
     DevBuf ga_ptr, ga_kappa, ga_group, hb_ptr, hb_kappa, hb_group;
     DevBuf ga_index, hb_index;  // block of every (slot, K-group atom) pair of every entry
     DevBuf meta;                // emulated product: scale-period flags per chunk (on demand)
+};
+
+// Piece entries of one operand kind (A or B, main or tail): per atom group, ascending keys
+// (Morton ranks or tail groups); index = block of every (slot, atom of the key) pair.
+struct PieceList {
+    DevBuf ptr, key, group, index;
+    std::vector<int64_t> ptr_host;
+    int64_t n() const { return ptr_host.empty() ? 0 : ptr_host.back(); }
+};
+
+struct PieceBatch {
+    int tile0, tile1;        // tiles [tile0, tile1)
+    int64_t am0, am1;        // A main entries [am0, am1)
+    int64_t at0, at1;        // A tail entries [at0, at1)
+};
+
+// Plan of one split product (pattern triple): tiles, K-step table, piece lists.
+struct PiecePlan {
+    int n_tiles = 0;
+    int64_t n_steps = 0;
+    double mma_flops = 0.0;  // tensor-core flops of one product over these tiles
+    std::vector<PieceBatch> batches;
+    std::vector<int64_t> batch_steps;
+    DevBuf tiles, kstart, nmain, steps, cidx, zero;
+    PieceList am, at, bm, bt;
 };
 
 // Morton order of the atoms (positions quantised to 1024 per box edge).
@@ -692,12 +771,18 @@ cq_status get_groups(cq_ctx *ctx, const cq_pattern *p, Groups **out)
     std::vector<int32_t> order = spatial_order(g);
     std::vector<int32_t> ga((size_t)gr->n_g * gr->gi, -1), ha((size_t)gr->n_h * gr->gj, -1),
         ka((size_t)gr->n_kappa * gr->ca, -1);
-    std::vector<int32_t> gof(g.n_atoms), hof(g.n_atoms), kof(g.n_atoms);
+    gr->tg = nb == 9 ? KPieces<9>::TG : KPieces<4>::TG;
+    gr->n_tau = (g.n_atoms + gr->tg - 1) / gr->tg;
+    std::vector<int32_t> ta((size_t)gr->n_tau * gr->tg, -1);
+    std::vector<int32_t> gof(g.n_atoms), hof(g.n_atoms), kof(g.n_atoms), rof(g.n_atoms),
+        tof(g.n_atoms);
     for (int r = 0; r < g.n_atoms; ++r) {
-        ga[r] = ha[r] = ka[r] = order[r];
+        ga[r] = ha[r] = ka[r] = ta[r] = order[r];
         gof[order[r]] = r / gr->gi;
         hof[order[r]] = r / gr->gj;
         kof[order[r]] = r / gr->ca;
+        rof[order[r]] = r;
+        tof[order[r]] = r / gr->tg;
     }
     cq_status st;
     if ((st = upload(ctx, gr->g_atoms, ga.data(), 4 * ga.size())) != CQ_OK ||
@@ -705,7 +790,11 @@ cq_status get_groups(cq_ctx *ctx, const cq_pattern *p, Groups **out)
         (st = upload(ctx, gr->kg_atoms, ka.data(), 4 * ka.size())) != CQ_OK ||
         (st = upload(ctx, gr->g_of, gof.data(), 4 * gof.size())) != CQ_OK ||
         (st = upload(ctx, gr->h_of, hof.data(), 4 * hof.size())) != CQ_OK ||
-        (st = upload(ctx, gr->kg_of, kof.data(), 4 * kof.size())) != CQ_OK)
+        (st = upload(ctx, gr->kg_of, kof.data(), 4 * kof.size())) != CQ_OK ||
+        (st = upload(ctx, gr->rank_atoms, order.data(), 4 * order.size())) != CQ_OK ||
+        (st = upload(ctx, gr->rank_of, rof.data(), 4 * rof.size())) != CQ_OK ||
+        (st = upload(ctx, gr->tg_atoms, ta.data(), 4 * ta.size())) != CQ_OK ||
+        (st = upload(ctx, gr->tg_of, tof.data(), 4 * tof.size())) != CQ_OK)
         return st;
     if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "groups")) != CQ_OK) return st;
     *out = gr.get();
@@ -713,23 +802,25 @@ cq_status get_groups(cq_ctx *ctx, const cq_pattern *p, Groups **out)
     return CQ_OK;
 }
 
-// K-group lists of n_groups atom groups in a pattern: ptr (n_groups + 1), kappa (ascending
-// per group), group (entry -> group); ptr_host receives ptr.
-cq_status group_lists(cq_ctx *ctx, const Groups *gr, int n_groups, int gsize,
-                      const int32_t *atoms, const cq_pattern *p, DevBuf &ptr, DevBuf &kappa,
-                      DevBuf &group, std::vector<int64_t> &ptr_host)
+// Key lists of n_groups atom groups in a pattern, key_of mapping an atom to one of n_keys
+// keys (its K group, Morton rank or tail group): every key of a column of a row of the
+// group's atoms.  ptr (n_groups + 1), kappa (ascending per group), group (entry -> group);
+// ptr_host receives ptr.
+cq_status group_lists(cq_ctx *ctx, int n_groups, int gsize, const int32_t *atoms,
+                      const cq_pattern *p, const int32_t *key_of, int n_keys, DevBuf &ptr,
+                      DevBuf &kappa, DevBuf &group, std::vector<int64_t> &ptr_host)
 {
     cudaStream_t s = ctx->stream;
     cq_status st;
     void *vc;
     if ((st = cq_scratch(ctx, "split_cnt", 8 * ((size_t)n_groups + 1), &vc)) != CQ_OK) return st;
     if ((st = cq_alloc(ctx, ptr, 8 * ((size_t)n_groups + 1))) != CQ_OK) return st;
-    const size_t shm = 4 * (size_t)((gr->n_kappa + 31) / 32);
+    const size_t shm = 4 * (size_t)((n_keys + 31) / 32);
     cudaFuncSetAttribute(k_group_kappa<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     cudaFuncSetAttribute(k_group_kappa<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     k_group_kappa<false><<<n_groups, 256, shm, s>>>(gsize, atoms, p->row_ptr.as<int64_t>(),
-                                                    p->col.as<int32_t>(), gr->kg_of.as<int32_t>(),
-                                                    gr->n_kappa, (int64_t *)vc, nullptr, nullptr);
+                                                    p->col.as<int32_t>(), key_of, n_keys,
+                                                    (int64_t *)vc, nullptr, nullptr);
     cq_count_launch();
     if ((st = cq_scan_i64(ctx, (int64_t *)vc, ptr.as<int64_t>(), n_groups)) != CQ_OK) return st;
     ptr_host.assign((size_t)n_groups + 1, 0);
@@ -738,9 +829,8 @@ cq_status group_lists(cq_ctx *ctx, const Groups *gr, int n_groups, int gsize,
     const int64_t n = ptr_host[n_groups];
     if ((st = cq_alloc(ctx, kappa, 4 * (size_t)(n + 1))) != CQ_OK) return st;
     k_group_kappa<true><<<n_groups, 256, shm, s>>>(gsize, atoms, p->row_ptr.as<int64_t>(),
-                                                   p->col.as<int32_t>(), gr->kg_of.as<int32_t>(),
-                                                   gr->n_kappa, nullptr, ptr.as<int64_t>(),
-                                                   kappa.as<int32_t>());
+                                                   p->col.as<int32_t>(), key_of, n_keys, nullptr,
+                                                   ptr.as<int64_t>(), kappa.as<int32_t>());
     cq_count_launch();
     std::vector<int32_t> grp((size_t)n);
     for (int q = 0; q < n_groups; ++q)
@@ -749,19 +839,12 @@ cq_status group_lists(cq_ctx *ctx, const Groups *gr, int n_groups, int gsize,
     return cq_check_cuda(ctx, cudaStreamSynchronize(s), "group lists");
 }
 
-cq_status get_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
-                   const cq_pattern *pC, const Groups *gr, SplitPlan **out)
+// Work tiles of a product, sorted by (g, h): the (M group, N group) pairs that hold a
+// block of P_C.
+cq_status tile_list(cq_ctx *ctx, const cq_pattern *pC, const Groups *gr, std::vector<int2> &tiles)
 {
-    auto key = std::make_tuple(2, pA->id, pB->id, pC->id);
-    auto it = ctx->aux.find(key);
-    if (it != ctx->aux.end()) {
-        *out = static_cast<SplitPlan *>(it->second.get());
-        return CQ_OK;
-    }
     cudaStream_t s = ctx->stream;
-    auto pl = std::make_shared<SplitPlan>();
     cq_status st;
-    // tiles, sorted by (g, h)
     const int64_t nbits = (int64_t)gr->n_g * gr->n_h;
     const int64_t nwords = (nbits + 31) / 32;
     void *vb;
@@ -776,17 +859,36 @@ cq_status get_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
     std::vector<uint32_t> bits(nwords);
     cudaMemcpyAsync(bits.data(), vb, 4 * nwords, cudaMemcpyDeviceToHost, s);
     if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "tile mark")) != CQ_OK) return st;
-    std::vector<int2> tiles;
+    tiles.clear();
     for (int64_t b = 0; b < nbits; ++b)
         if (bits[b >> 5] & (1u << (b & 31)))
             tiles.push_back(make_int2((int)(b / gr->n_h), (int)(b % gr->n_h)));
+    return CQ_OK;
+}
+
+cq_status get_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
+                   const cq_pattern *pC, const Groups *gr, SplitPlan **out)
+{
+    auto key = std::make_tuple(2, pA->id, pB->id, pC->id);
+    auto it = ctx->aux.find(key);
+    if (it != ctx->aux.end()) {
+        *out = static_cast<SplitPlan *>(it->second.get());
+        return CQ_OK;
+    }
+    cudaStream_t s = ctx->stream;
+    auto pl = std::make_shared<SplitPlan>();
+    cq_status st;
+    std::vector<int2> tiles;
+    if ((st = tile_list(ctx, pC, gr, tiles)) != CQ_OK) return st;
     pl->n_tiles = (int)tiles.size();
     // K-group lists of the M groups (rows of P_A) and of the N groups (rows of P_B)
     std::vector<int64_t> ga_host, hb_host;
-    if ((st = group_lists(ctx, gr, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA, pl->ga_ptr,
-                          pl->ga_kappa, pl->ga_group, ga_host)) != CQ_OK ||
-        (st = group_lists(ctx, gr, gr->n_h, gr->gj, gr->h_atoms.as<int32_t>(), pB, pl->hb_ptr,
-                          pl->hb_kappa, pl->hb_group, hb_host)) != CQ_OK)
+    if ((st = group_lists(ctx, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA,
+                          gr->kg_of.as<int32_t>(), gr->n_kappa, pl->ga_ptr, pl->ga_kappa,
+                          pl->ga_group, ga_host)) != CQ_OK ||
+        (st = group_lists(ctx, gr->n_h, gr->gj, gr->h_atoms.as<int32_t>(), pB,
+                          gr->kg_of.as<int32_t>(), gr->n_kappa, pl->hb_ptr, pl->hb_kappa,
+                          pl->hb_group, hb_host)) != CQ_OK)
         return st;
     // batches of whole M groups (tiles are sorted by g) whose A panels fit A_PANEL_CAP
     {
@@ -880,18 +982,201 @@ cq_status get_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
     return CQ_OK;
 }
 
+// Piece list of one operand kind: the keys of every atom group (group_lists) and the block
+// of every (slot, key atom) pair (k_panel_index); ca atoms per key, key_atoms listing them.
+template <bool LEFT>
+cq_status piece_list(cq_ctx *ctx, int n_groups, int gsize, const int32_t *atoms,
+                     const cq_pattern *p, const int32_t *key_of, int n_keys, int ca,
+                     const int32_t *key_atoms, PieceList &pl)
+{
+    cq_status st = group_lists(ctx, n_groups, gsize, atoms, p, key_of, n_keys, pl.ptr, pl.key,
+                               pl.group, pl.ptr_host);
+    if (st != CQ_OK) return st;
+    const int64_t n = pl.n();
+    if ((st = cq_alloc(ctx, pl.index, 4 * ((size_t)n * gsize * ca + 1))) != CQ_OK) return st;
+    if (n > 0) {
+        k_panel_index<LEFT><<<(unsigned)n, 256, 0, ctx->stream>>>(
+            gsize, ca, pl.group.as<int32_t>(), pl.key.as<int32_t>(), atoms, key_atoms,
+            p->row_ptr.as<int64_t>(), p->col.as<int32_t>(),
+            LEFT ? nullptr : p->transpose.as<int64_t>(), pl.index.as<int32_t>());
+        cq_count_launch();
+    }
+    return cq_check_cuda(ctx, cudaGetLastError(), "piece index");
+}
+
+// Keys of every tile (k_tile_kappa with key_of: Morton ranks or tail groups): start
+// (n_tiles + 1) on the device and the host, keys ascending per tile.
+cq_status tile_keys(cq_ctx *ctx, const DevBuf &tiles, int n_tiles, const Groups *gr,
+                    const cq_pattern *pA, const cq_pattern *pB, const int32_t *key_of, int n_keys,
+                    DevBuf &start, DevBuf &keys, std::vector<int64_t> &start_host)
+{
+    cudaStream_t s = ctx->stream;
+    const int n_atoms = pA->geo->n_atoms;
+    const size_t shm = 4 * (size_t)(2 * ((n_atoms + 31) / 32) + (n_keys + 31) / 32);
+    if (shm > 200 * 1024) return cq_fail(ctx, CQ_ERR_INVALID, "split product: too many atoms");
+    cq_status st;
+    void *vc;
+    if ((st = cq_scratch(ctx, "split_cnt", 8 * ((size_t)n_tiles + 1), &vc)) != CQ_OK) return st;
+    if ((st = cq_alloc(ctx, start, 8 * ((size_t)n_tiles + 1))) != CQ_OK) return st;
+    cudaFuncSetAttribute(k_tile_kappa<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(k_tile_kappa<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k_tile_kappa<false><<<n_tiles, 256, shm, s>>>(
+        n_atoms, tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
+        gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
+        pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), key_of, n_keys, (int64_t *)vc, nullptr,
+        nullptr);
+    cq_count_launch();
+    if ((st = cq_scan_i64(ctx, (int64_t *)vc, start.as<int64_t>(), n_tiles)) != CQ_OK) return st;
+    start_host.assign((size_t)n_tiles + 1, 0);
+    cudaMemcpyAsync(start_host.data(), start.ptr, 8 * start_host.size(), cudaMemcpyDeviceToHost, s);
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "tile keys")) != CQ_OK) return st;
+    if ((st = cq_alloc(ctx, keys, 4 * (size_t)(start_host[n_tiles] + 1))) != CQ_OK) return st;
+    k_tile_kappa<true><<<n_tiles, 256, shm, s>>>(
+        n_atoms, tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
+        gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
+        pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), key_of, n_keys, nullptr,
+        start.as<int64_t>(), keys.as<int32_t>());
+    cq_count_launch();
+    return cq_check_cuda(ctx, cudaGetLastError(), "tile keys");
+}
+
+cq_status get_piece_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
+                         const cq_pattern *pC, const Groups *gr, PiecePlan **out)
+{
+    auto key = std::make_tuple(3, pA->id, pB->id, pC->id);
+    auto it = ctx->aux.find(key);
+    if (it != ctx->aux.end()) {
+        *out = static_cast<PiecePlan *>(it->second.get());
+        return CQ_OK;
+    }
+    cudaStream_t s = ctx->stream;
+    auto pl = std::make_shared<PiecePlan>();
+    const bool mains = pC->geo->uniform_nb == 9;
+    const int n_atoms = pA->geo->n_atoms;
+    cq_status st;
+    // piece lists: main pieces per (atom group, K atom), tail pieces per (atom group, tail group)
+    if (mains &&
+        ((st = piece_list<true>(ctx, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA,
+                                gr->rank_of.as<int32_t>(), n_atoms, 1,
+                                gr->rank_atoms.as<int32_t>(), pl->am)) != CQ_OK ||
+         (st = piece_list<false>(ctx, gr->n_h, gr->gj, gr->h_atoms.as<int32_t>(), pB,
+                                 gr->rank_of.as<int32_t>(), n_atoms, 1,
+                                 gr->rank_atoms.as<int32_t>(), pl->bm)) != CQ_OK))
+        return st;
+    if ((st = piece_list<true>(ctx, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA,
+                               gr->tg_of.as<int32_t>(), gr->n_tau, gr->tg,
+                               gr->tg_atoms.as<int32_t>(), pl->at)) != CQ_OK ||
+        (st = piece_list<false>(ctx, gr->n_h, gr->gj, gr->h_atoms.as<int32_t>(), pB,
+                                gr->tg_of.as<int32_t>(), gr->n_tau, gr->tg,
+                                gr->tg_atoms.as<int32_t>(), pl->bt)) != CQ_OK)
+        return st;
+    if ((st = cq_alloc(ctx, pl->zero, A_MAIN)) != CQ_OK) return st;
+    cudaMemsetAsync(pl->zero.ptr, 0, A_MAIN, s);
+    std::vector<int2> tiles;
+    if ((st = tile_list(ctx, pC, gr, tiles)) != CQ_OK) return st;
+    pl->n_tiles = (int)tiles.size();
+    if (tiles.empty()) {
+        if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "split plan")) != CQ_OK) return st;
+        *out = pl.get();
+        ctx->aux[key] = pl;
+        return CQ_OK;
+    }
+    // bytes of the A pieces of M groups [g0, g1]
+    auto nm_of = [&](int g) { return mains ? pl->am.ptr_host[g] : (int64_t)0; };
+    auto a_bytes = [&](int g0, int g1) {
+        return (nm_of(g1 + 1) - nm_of(g0)) * (int64_t)A_MAIN +
+               (pl->at.ptr_host[g1 + 1] - pl->at.ptr_host[g0]) * (int64_t)A_TAIL;
+    };
+    // batches of whole M groups (tiles are sorted by g) whose A pieces fit A_PANEL_CAP
+    {
+        int t0 = 0;
+        while (t0 < pl->n_tiles) {
+            const int g0 = tiles[t0].x;
+            int t1 = t0, g1 = g0;
+            while (t1 < pl->n_tiles) {
+                const int g = tiles[t1].x;
+                if (g != g1) {  // the next M group starts; keep it only if its pieces still fit
+                    if (a_bytes(g0, g) > (int64_t)A_PANEL_CAP) break;
+                    g1 = g;
+                }
+                ++t1;
+            }
+            pl->batches.push_back({t0, t1, nm_of(g0), nm_of(g1 + 1), pl->at.ptr_host[g0],
+                                   pl->at.ptr_host[g1 + 1]});
+            t0 = t1;
+        }
+    }
+    if ((st = upload(ctx, pl->tiles, tiles.data(), sizeof(int2) * tiles.size())) != CQ_OK) return st;
+    // K atoms and tail groups of every tile (temporaries), then the K-step table
+    DevBuf ka_start, tile_rank, kt_start, tile_tau;
+    std::vector<int64_t> ka, kt;
+    if (mains) {
+        if ((st = tile_keys(ctx, pl->tiles, pl->n_tiles, gr, pA, pB, gr->rank_of.as<int32_t>(),
+                            n_atoms, ka_start, tile_rank, ka)) != CQ_OK)
+            return st;
+    } else {
+        ka.assign((size_t)pl->n_tiles + 1, 0);
+        if ((st = upload(ctx, ka_start, ka.data(), 8 * ka.size())) != CQ_OK ||
+            (st = cq_alloc(ctx, tile_rank, 4)) != CQ_OK)
+            return st;
+    }
+    if ((st = tile_keys(ctx, pl->tiles, pl->n_tiles, gr, pA, pB, gr->tg_of.as<int32_t>(),
+                        gr->n_tau, kt_start, tile_tau, kt)) != CQ_OK)
+        return st;
+    std::vector<int64_t> step_start((size_t)pl->n_tiles + 1, 0);
+    std::vector<int32_t> nmain((size_t)pl->n_tiles);
+    for (int b = 0; b < pl->n_tiles; ++b) {
+        const int64_t nm = (ka[b + 1] - ka[b] + 1) / 2, nt = kt[b + 1] - kt[b];
+        nmain[b] = (int32_t)nm;
+        step_start[b + 1] = step_start[b] + nm + nt;
+    }
+    pl->n_steps = step_start[pl->n_tiles];
+    pl->mma_flops = (double)pl->n_steps * 6.0 * 2.0 * MT * NT * 16;
+    for (const PieceBatch &bt : pl->batches)
+        pl->batch_steps.push_back(step_start[bt.tile1] - step_start[bt.tile0]);
+    if ((st = upload(ctx, pl->kstart, step_start.data(), 8 * step_start.size())) != CQ_OK ||
+        (st = upload(ctx, pl->nmain, nmain.data(), 4 * nmain.size())) != CQ_OK ||
+        (st = cq_alloc(ctx, pl->steps, sizeof(int4) * (size_t)(pl->n_steps + 1))) != CQ_OK ||
+        (st = cq_alloc(ctx, pl->cidx, 4 * ((size_t)pl->n_tiles * gr->gi * gr->gj + 1))) != CQ_OK)
+        return st;
+    k_tile_steps<<<pl->n_tiles, 256, 0, s>>>(
+        pl->tiles.as<int2>(), ka_start.as<int64_t>(), tile_rank.as<int32_t>(),
+        kt_start.as<int64_t>(), tile_tau.as<int32_t>(), pl->kstart.as<int64_t>(),
+        pl->am.ptr.as<int64_t>(), pl->am.key.as<int32_t>(), pl->bm.ptr.as<int64_t>(),
+        pl->bm.key.as<int32_t>(), pl->at.ptr.as<int64_t>(), pl->at.key.as<int32_t>(),
+        pl->bt.ptr.as<int64_t>(), pl->bt.key.as<int32_t>(), pl->steps.as<int4>());
+    k_tile_cidx<<<pl->n_tiles, 256, 0, s>>>(
+        pl->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
+        gr->h_atoms.as<int32_t>(), pC->row_ptr.as<int64_t>(), pC->col.as<int32_t>(),
+        pl->cidx.as<int32_t>());
+    cq_count_launch(2);
+    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "split plan")) != CQ_OK) return st;
+    // the temporaries are freed on return: let the kernels that read them finish
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "split plan")) != CQ_OK) return st;
+    *out = pl.get();
+    ctx->aux[key] = pl;
+    return CQ_OK;
+}
+
 template <int NB>
-cq_status run_split(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double alpha,
+cq_status run_split(cq_ctx *ctx, const PiecePlan *pl, const Groups *gr, double alpha,
                     const cq_pattern *pA, const double *A, const cq_pattern *pB,
                     const double *B, double beta, const cq_pattern *pC, double *C, double flops)
 {
     cudaStream_t s = ctx->stream;
     cq_status st;
-    size_t a_bytes = 0;
-    for (const Batch &b : pl->batches) a_bytes = std::max(a_bytes, (size_t)(b.e1 - b.e0) * A_CHUNK);
-    void *va, *vb;
-    if ((st = cq_scratch(ctx, "split_A", a_bytes, &va)) != CQ_OK) return st;
-    if ((st = cq_scratch(ctx, "split_B", (size_t)pl->n_hb * B_CHUNK, &vb)) != CQ_OK) return st;
+    size_t am_bytes = 0, at_bytes = 0;
+    for (const PieceBatch &b : pl->batches) {
+        am_bytes = std::max(am_bytes, (size_t)(b.am1 - b.am0) * A_MAIN);
+        at_bytes = std::max(at_bytes, (size_t)(b.at1 - b.at0) * A_TAIL);
+    }
+    // one spare piece of room at the end of each piece array
+    void *vam, *vat, *vbm, *vbt;
+    if ((st = cq_scratch(ctx, "split_Am", am_bytes + A_TAIL, &vam)) != CQ_OK ||
+        (st = cq_scratch(ctx, "split_At", at_bytes + A_TAIL, &vat)) != CQ_OK ||
+        (st = cq_scratch(ctx, "split_Bm", (size_t)pl->bm.n() * B_MAIN + A_TAIL, &vbm)) != CQ_OK ||
+        (st = cq_scratch(ctx, "split_Bt", (size_t)pl->bt.n() * B_TAIL + A_TAIL, &vbt)) != CQ_OK)
+        return st;
     // the shared-memory limit is a per-device attribute: set it once per device, on the
     // first split product there (which runs eagerly: building its plan synchronises)
     static bool attr_set[64] = {};
@@ -908,26 +1193,42 @@ cq_status run_split(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double a
             return st;
         attr_set[dev] = true;
     }
-    if (pl->n_hb > 0) {
-        k_pack_b<NB><<<(unsigned)pl->n_hb, 256, 0, s>>>(pl->hb_index.as<int32_t>(), B,
-                                                         pB->uniform, (uint8_t *)vb);
+    auto blocks = [](int64_t n, int rows) { return (unsigned)((n * rows + 255) / 256); };
+    if (pl->bm.n() > 0) {
+        k_pack_main<NB, false><<<blocks(pl->bm.n(), NT), 256, 0, s>>>(
+            0, pl->bm.n(), pl->bm.index.as<int32_t>(), B, pB->uniform, (uint8_t *)vbm);
+        cq_count_launch();
+    }
+    if (pl->bt.n() > 0) {
+        k_pack_tail<NB, false><<<blocks(pl->bt.n(), NT), 256, 0, s>>>(
+            0, pl->bt.n(), pl->bt.index.as<int32_t>(), B, pB->uniform, (uint8_t *)vbt);
         cq_count_launch();
     }
     for (size_t q = 0; q < pl->batches.size(); ++q) {
-        const Batch &b = pl->batches[q];
-        if (b.e1 > b.e0) {
-            k_pack_a<NB><<<(unsigned)(b.e1 - b.e0), 256, 0, s>>>(
-                b.e0, pl->ga_index.as<int32_t>(), A, pA->uniform, (uint8_t *)va);
+        const PieceBatch &b = pl->batches[q];
+        if (b.am1 > b.am0) {
+            k_pack_main<NB, true><<<blocks(b.am1 - b.am0, MT), 256, 0, s>>>(
+                b.am0, b.am1 - b.am0, pl->am.index.as<int32_t>(), A, pA->uniform, (uint8_t *)vam);
+            cq_count_launch();
+        }
+        if (b.at1 > b.at0) {
+            k_pack_tail<NB, true><<<blocks(b.at1 - b.at0, MT), 256, 0, s>>>(
+                b.at0, b.at1 - b.at0, pl->at.index.as<int32_t>(), A, pA->uniform, (uint8_t *)vat);
             cq_count_launch();
         }
         SplitArgs a;
         a.n_tiles = b.tile1 - b.tile0;
         a.kstart = pl->kstart.as<int64_t>() + b.tile0;
-        a.chunks = pl->chunks.as<int2>();
+        a.nmain = pl->nmain.as<int32_t>() + b.tile0;
+        a.steps = pl->steps.as<int4>();
         a.cidx = pl->cidx.as<int32_t>() + (int64_t)b.tile0 * gr->gi * gr->gj;
-        a.panel_a = (const uint8_t *)va;
-        a.ea0 = b.e0;
-        a.panel_b = (const uint8_t *)vb;
+        a.a_main = (const uint8_t *)vam;
+        a.am0 = b.am0;
+        a.a_tail = (const uint8_t *)vat;
+        a.at0 = b.at0;
+        a.b_main = (const uint8_t *)vbm;
+        a.b_tail = (const uint8_t *)vbt;
+        a.zero = pl->zero.as<uint8_t>();
         a.C = C;
         a.c_stride = pC->uniform;
         a.alpha = alpha;
@@ -936,7 +1237,7 @@ cq_status run_split(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double a
         a.test_wait_cycles = ctx->test_wait_cycles;
         // this launch's share of the product's useful and tensor-core flops
         const double share =
-            pl->n_chunks > 0 ? (double)pl->batch_chunks[q] / (double)pl->n_chunks : 0.0;
+            pl->n_steps > 0 ? (double)pl->batch_steps[q] / (double)pl->n_steps : 0.0;
         const int grid = std::min(a.n_tiles, ctx->num_sms);
         cq_timing_begin(ctx, flops * share, pl->mma_flops * share);
         k_bsmm_split<NB><<<grid, ST, SMEM, s>>>(a);
@@ -1074,10 +1375,10 @@ cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_
                        "split-BF16 product: needs a uniform basis of 4 or 9 orbitals per atom");
     if (pC->n_blocks == 0) return CQ_OK;
     Groups *gr;
-    SplitPlan *pl;
+    PiecePlan *pl;
     cq_status st = get_groups(ctx, pC, &gr);
     if (st != CQ_OK) return st;
-    if ((st = get_plan(ctx, pA, pB, pC, gr, &pl)) != CQ_OK) return st;
+    if ((st = get_piece_plan(ctx, pA, pB, pC, gr, &pl)) != CQ_OK) return st;
     if (pl->n_tiles == 0) return CQ_OK;
     return nb == 9 ? run_split<9>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops)
                    : run_split<4>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops);

@@ -1,10 +1,12 @@
 // The tile kernel of the split-BF16 product (included by bsmm_split.cu).
 //
 // Warp roles (10 warps, one CTA per SM):
-//   warp 0      producer: lane 0 copies each chunk's A panel (36 KB) and B panel (18 KB)
-//               into a free stage with two TMA bulk copies that complete on the stage's
-//               "full" barrier; the warp's lanes load the chunk table 32 entries at a time;
-//   warp 1      lane 0 issues the 18 MMAs of a chunk (3 K steps x 6 split products) into
+//   warp 0      producer: a chunk is up to three consecutive K steps of a tile; lane 0
+//               copies each K step's pieces (main step: two A and two B main pieces; tail
+//               step: one A and one B tail piece; 18 KB either way) into the step's slot of
+//               a free stage with TMA bulk copies that complete on the stage's "full"
+//               barrier; the warp's lanes load the K-step table 32 entries at a time;
+//   warp 1      lane 0 issues the MMAs of a chunk (6 split products per K step) into
 //               one of NACC TMEM accumulators (one per drain period, in rotation) and
 //               commits them to the stage's "empty" barrier, and at the end of a drain
 //               period to the accumulator's "full" barrier;
@@ -184,34 +186,56 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
         for (int s = 0; s < NS; ++s) last[s] = -1;
         bool ok = true;
         for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-            const int64_t c0 = p.kstart[tile];
-            const int nch = (int)(p.kstart[tile + 1] - c0);
-            int2 ent = make_int2(0, 0);
+            const int64_t s0 = p.kstart[tile];
+            const int nks = (int)(p.kstart[tile + 1] - s0);
+            const int nm = p.nmain[tile];
+            const int nch = (nks + KSTEPS - 1) / KSTEPS;
+            int4 ent = make_int4(0, 0, 0, 0);
             for (int c = 0; c < nch; ++c, ++cg) {
-                if ((c & 31) == 0) ent = c + lane < nch ? p.chunks[c0 + c + lane] : make_int2(0, 0);
-                const int ea = __shfl_sync(0xffffffffu, ent.x, c & 31);
-                const int eb = __shfl_sync(0xffffffffu, ent.y, c & 31);
+                const int s = (int)(cg % NS);
+                const int nv = min(KSTEPS, nks - KSTEPS * c);  // K steps of this chunk
                 int go = 1;
                 if (lane == 0) {
-                    const int s = (int)(cg % NS);
                     if (cg >= (uint32_t)NS &&
                         !bar_wait(smem_u32(&bars->empty[s]), ((cg / NS) + 1) & 1u, abort_flag)) {
                         go = 0;
                     } else {
-                        const uint32_t fb = smem_u32(&bars->full[s]);
-                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                                     "r"((uint32_t)STAGE)
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                         smem_u32(&bars->full[s])),
+                                     "r"((uint32_t)(nv * (A_SLOT + B_SLOT)))
                                      : "memory");
-                        bulk_copy(sm0 + s * STAGE, p.panel_a + (int64_t)(ea - p.ea0) * A_CHUNK,
-                                  A_CHUNK, fb);
-                        bulk_copy(sm0 + s * STAGE + A_CHUNK, p.panel_b + (int64_t)eb * B_CHUNK,
-                                  B_CHUNK, fb);
                         last[s] = (int)cg;
                     }
                 }
                 if (!__shfl_sync(0xffffffffu, go, 0)) {
                     ok = false;
                     break;
+                }
+                for (int x = 0; x < nv; ++x) {
+                    const int q = KSTEPS * c + x;
+                    if ((q & 31) == 0)
+                        ent = q + lane < nks ? p.steps[s0 + q + lane] : make_int4(0, 0, 0, 0);
+                    const int ea = __shfl_sync(0xffffffffu, ent.x, q & 31);
+                    const int ea2 = __shfl_sync(0xffffffffu, ent.y, q & 31);
+                    const int eb = __shfl_sync(0xffffffffu, ent.z, q & 31);
+                    const int eb2 = __shfl_sync(0xffffffffu, ent.w, q & 31);
+                    if (lane == 0) {
+                        const uint32_t fb = smem_u32(&bars->full[s]);
+                        const uint32_t da = sm0 + s * STAGE + x * A_SLOT;
+                        const uint32_t db = sm0 + s * STAGE + B_SLOTS + x * B_SLOT;
+                        if (q < nm) {
+                            bulk_copy(da, p.a_main + (int64_t)(ea - p.am0) * A_MAIN, A_MAIN, fb);
+                            bulk_copy(da + A_MAIN,
+                                      ea2 < 0 ? p.zero : p.a_main + (int64_t)(ea2 - p.am0) * A_MAIN,
+                                      A_MAIN, fb);
+                            bulk_copy(db, p.b_main + (int64_t)eb * B_MAIN, B_MAIN, fb);
+                            bulk_copy(db + B_MAIN, eb2 < 0 ? p.zero : p.b_main + (int64_t)eb2 * B_MAIN,
+                                      B_MAIN, fb);
+                        } else {
+                            bulk_copy(da, p.a_tail + (int64_t)(ea - p.at0) * A_TAIL, A_TAIL, fb);
+                            bulk_copy(db, p.b_tail + (int64_t)eb * B_TAIL, B_TAIL, fb);
+                        }
+                    }
                 }
             }
         }
@@ -232,11 +256,17 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
                 ok = false;
             }
             const int pq[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
-            // descriptors of stage 0; a stage, plane or K step only moves the 14-bit start
-            // address field (shared addresses stay below 256 KB, so no carry leaves it)
-            const uint64_t da0 = smem_desc(sm0), db0 = smem_desc(sm0 + A_CHUNK);
+            // descriptors of slot 0 of stage 0 for both kinds of K step (main: the second
+            // column is the second atom's piece, A_MAIN / B_MAIN further; tail: the piece's
+            // second column); a stage, slot or plane only moves the 14-bit start address
+            // field (shared addresses stay below 256 KB, so no carry leaves it)
+            const uint64_t dam = piece_desc(sm0, A_MAIN), dat = piece_desc(sm0, COLB_A);
+            const uint64_t dbm = piece_desc(sm0 + B_SLOTS, B_MAIN);
+            const uint64_t dbt = piece_desc(sm0 + B_SLOTS, COLB_B);
             for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-                const int nch = (int)(p.kstart[tile + 1] - p.kstart[tile]);
+                const int nks = (int)(p.kstart[tile + 1] - p.kstart[tile]);
+                const int nm = p.nmain[tile];
+                const int nch = (nks + KSTEPS - 1) / KSTEPS;
                 for (int c = 0; c < nch; ++c, ++cg) {
                     const uint32_t b = pg % NACC;
                     if (c % DRAIN == 0 && pg >= (uint32_t)NACC &&
@@ -251,15 +281,22 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint64_t sa = da0 + (uint64_t)((s * STAGE) >> 4);
-                    const uint64_t sb = db0 + (uint64_t)((s * STAGE) >> 4);
                     const uint32_t acc_addr = tmem + b * NT;
-#pragma unroll
-                    for (int ks = 0; ks < KSTEPS; ++ks)
+                    const int nv = min(KSTEPS, nks - KSTEPS * c);
+                    for (int ks = 0; ks < nv; ++ks) {
+                        const bool main_step = KSTEPS * c + ks < nm;
+                        // plane strides in 16-byte units: main pieces hold one column per
+                        // plane, tail pieces two
+                        const uint32_t pa = main_step ? COLB_A >> 4 : (2 * COLB_A) >> 4;
+                        const uint32_t pb = main_step ? COLB_B >> 4 : (2 * COLB_B) >> 4;
+                        const uint64_t sa = (main_step ? dam : dat) +
+                                            (uint64_t)((s * STAGE + ks * A_SLOT) >> 4);
+                        const uint64_t sb = (main_step ? dbm : dbt) +
+                                            (uint64_t)((s * STAGE + ks * B_SLOT) >> 4);
 #pragma unroll
                         for (int x = 0; x < 6; ++x) {
-                            const uint64_t ad = sa + (uint64_t)((pq[x][0] * A_PLANE + ks * 256) >> 4);
-                            const uint64_t bd = sb + (uint64_t)((pq[x][1] * B_PLANE + ks * 256) >> 4);
+                            const uint64_t ad = sa + (uint64_t)(pq[x][0] * pa);
+                            const uint64_t bd = sb + (uint64_t)(pq[x][1] * pb);
                             const uint32_t acc = (c % DRAIN == 0 && ks == 0 && x == 0) ? 0u : 1u;
                             asm volatile(
                                 "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -267,6 +304,7 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
                                     acc_addr),
                                 "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
                         }
+                    }
                     bar_commit(smem_u32(&bars->empty[s]));
                     issued = true;
                     if (c % DRAIN == DRAIN - 1 || c == nch - 1) {
@@ -289,7 +327,8 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
         uint32_t pg = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-            const int nch = (int)(p.kstart[tile + 1] - p.kstart[tile]);
+            const int nks = (int)(p.kstart[tile + 1] - p.kstart[tile]);
+            const int nch = (nks + KSTEPS - 1) / KSTEPS;
             const int np = (nch + DRAIN - 1) / DRAIN;
             // this row's C blocks, loaded now and used after the tile's last period
             constexpr int NJ = epi_slots<NB>();
