@@ -180,7 +180,7 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  * triple is built on the device on first use and cached in the context.  C must not alias
  * A or B.  prec selects FP64 FMAs or the split-BF16 tensor-core product.  The split product
  * needs a uniform basis of 4 or 9 orbitals per atom (else CQ_ERR_INVALID); it packs both
- * operands into context-owned scratch panels before every call (about 2x the FP64 size of
+ * operands into context-owned scratch before every call (up to about 2x the FP64 size of
  * the operands, the A side in batches of at most 12 GB), and its accuracy is FP32-class:
  * about 1e-7 relative per block, with FP32 partial sums drained to double-float.  Each value
  * is split to about 2^-27 relative for 2^-74 <= |x| < (2 - 2^-8) 2^127 (coarser below,
@@ -189,8 +189,9 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  *
  * CQ_FP64_EMU gives FP64-class products on the BF16 tensor cores (Ozaki-style slicing; the
  * paper's priorities of GPU products and solver accuracy together, on a GPU whose FP64 pipe
- * is narrow): per scalar row of A and scalar column of B over every sixteen atoms of K (four
- * K groups) a power-of-two scale 2^E with |x| < 2^E; every value is rounded to the grid
+ * is narrow): per scalar row of A and scalar column of B over every sixteen consecutive atoms
+ * of K in the spatial (Morton) order (four for a 4-orbital basis) a power-of-two scale 2^E
+ * with |x| < 2^E; every value is rounded to the grid
  * 2^(E-63) and cut into eight signed 8-bit digits, each exact in BF16; the 36 digit
  * products of levels p + q <= 7 run on the tensor cores, levels 0-4 summed exactly in FP32
  * within a scale period and levels 5-7 together, and every period drains into a three-float
@@ -201,8 +202,8 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  * method's matrices) that is the FP64 product bound
  * ||dC_ij|| <= 1e-12 max(||C_ij||, 1e-3 sum_k ||A_ik|| ||B_kj||); terms must lie between
  * about 2^-70 and 2^120 in magnitude (FP32's range holds the drained sums).
- * Same basis requirement as the split (4 or 9 orbitals); its panels take about 2.7x the
- * split's scratch (eight BF16 planes per value).  Infinities and NaNs poison their scale
+ * Same basis requirement as the split (4 or 9 orbitals); its packed operands take about
+ * 2.7x the split's scratch (eight BF16 planes per value).  Infinities and NaNs poison their scale
  * group: they give NaN in every C value of the rows (of A) or columns (of B) that group
  * reaches.
  *

@@ -3,22 +3,24 @@
 //
 // Operands are eight BF16 digit planes per value (emu_digits.cuh): A_p, B_q with planes
 // pre-scaled by 2^(-8p), so the MMA of planes p and q lands at level p + q.  Per K step the
-// MMA thread issues the 36 products with p + q <= 7, level by level, into six FP32 accumulators in tensor
-// memory: levels 0 to 4 each alone -- over one scale period a level-l sum is an integer
-// times 2^(-8 l) of magnitude at most (l + 1) * 192 * 128^2 < 2^24 (192 K values per
-// period), hence exact -- and levels 5-7 together (rounded, but 2^-40 below level 0, so its
-// rounding stays near 2^-64 of the group's scale, as does the digit split itself).  A scale
-// period is a run of chunks whose K groups share a scale group (four K groups, sixteen
-// 9-orbital atoms).  At its end the drain warps scale every level by
+// MMA thread issues the 36 products with p + q <= 7, level by level, into six FP32
+// accumulators in tensor memory: levels 0 to 4 each alone -- over one scale period a
+// level-l sum is an integer times 2^(-8 l) of magnitude at most (l + 1) * 144 * 128^2 < 2^24
+// (at most 144 K values per period), hence exact -- and levels 5-7 together (rounded, but
+// 2^-40 below level 0, so its rounding stays near 2^-64 of the group's scale, as does the
+// digit split itself).  A scale period is one tail group of K (16 consecutive atoms in Morton
+// order for 9 orbitals, 4 for 4): the main K steps pairing the tile's K atoms of the group,
+// then the group's tail step.  At its end the drain warps scale every level by
 // 2^(E_A(row) + E_B(column) - 14) and add it into a three-float sum (h, m, l): h and m in
 // tensor memory beside the accumulators, l (the smallest word) in shared memory (column-
 // major, so the lanes of a warp, which own consecutive rows, hit distinct banks).  After a
 // tile's last period C = beta C + alpha (h + m + l) is written in FP64.
 //
 // Warp roles (10 warps, one CTA per SM):
-//   warp 0      producer: lane 0 copies every K step of every chunk (A: 8 planes x 128 rows
-//               x 16 K, 32 KB; B: 8 planes x 64 rows, 16 KB) into a free stage with two TMA
-//               bulk copies completing on the stage's "full" barrier;
+//   warp 0      producer: lane 0 copies the pieces of every K step (main step: two A main
+//               pieces of 8 planes x 128 rows x 8 K, 16 KB each, and two B main pieces of
+//               8 KB; tail step: one A tail piece, 32 KB, and one B tail piece, 16 KB) into a
+//               free stage with TMA bulk copies completing on the stage's "full" barrier;
 //   warp 1      lane 0 issues the 36 MMAs of each K step and commits the stage to its
 //               "empty" barrier; at a period's end it commits the accumulators to
 //               "acc_full" and, before the next period, waits on "acc_empty";
@@ -30,14 +32,11 @@
 // Every wait is bounded as in the split kernel; a CTA that gives up retires its copies and
 // MMAs, frees its tensor memory and sets bit 16 of the context flag.
 constexpr int NSE = 4;                       // shared-memory stages (one K step each)
-constexpr int E_APLANE = MT * 16 * 2;        // 4 KB: one A digit plane of one K step
-constexpr int E_BPLANE = NT * 16 * 2;        // 2 KB
-constexpr int E_AKSTEP = EMU_P * E_APLANE;   // 32 KB
-constexpr int E_BKSTEP = EMU_P * E_BPLANE;   // 16 KB
-constexpr int E_APANEL = KSTEPS * E_AKSTEP;  // 96 KB: one packed A panel
-constexpr int E_BPANEL = KSTEPS * E_BKSTEP;  // 48 KB
-constexpr int E_STAGE = E_AKSTEP + E_BKSTEP;
-constexpr int E_SBO = 256;                   // bytes between 8-row groups (2 core columns)
+constexpr int E_AMAIN = EMU_P * COLB_A;      // 16 KB: an A main piece (planes x one column)
+constexpr int E_BMAIN = EMU_P * COLB_B;      // 8 KB
+constexpr int E_ATAIL = 2 * E_AMAIN;         // 32 KB: an A tail piece (planes x two columns)
+constexpr int E_BTAIL = 2 * E_BMAIN;         // 16 KB
+constexpr int E_STAGE = E_ATAIL + E_BTAIL;   // one K step: A at 0, B at E_ATAIL
 constexpr int E_LEVELS = 6;                  // accumulators: levels 0-4, then 5-7 merged
 constexpr int E_COL_H = E_LEVELS * NT, E_COL_M = E_COL_H + NT;
 constexpr int E_TMEM_COLS = 512;
@@ -55,29 +54,25 @@ static_assert(E_COL_M + NT <= E_TMEM_COLS, "tensor memory columns");
 
 struct EmuArgs {
     int n_tiles;
-    const int64_t *kstart;     // chunk range of each tile (n_tiles + 1)
-    const int2 *chunks;        // (A panel entry, B panel entry) per chunk
-    const uint8_t *meta;       // per chunk: bit 0 starts a scale period, bit 1 ends one
+    const int64_t *kstart;     // K-step range of each tile (n_tiles + 1)
+    const int4 *steps;         // piece entries of every K step
+    const uint8_t *meta;       // per K step: bit 0 starts a scale period, bit 1 ends one
+                               // (the period's tail step)
     const int32_t *cidx;       // C block of each (M slot, N slot) pair of each tile
-    const uint8_t *panel_a;    // A panels of entries [ea0, ...)
-    int64_t ea0;
-    const uint8_t *panel_b;    // all B panels
-    const int16_t *scale_a;    // group exponent of every (A entry, row): n_ga x 128
-    const int16_t *scale_b;    // group exponent of every (B entry, column): n_hb x 64
+    const uint8_t *a_main;     // A main pieces of entries [am0, ...)
+    int64_t am0;
+    const uint8_t *a_tail;     // A tail pieces of entries [at0, ...)
+    int64_t at0;
+    const uint8_t *b_main;     // all B main pieces
+    const uint8_t *b_tail;     // all B tail pieces
+    const uint8_t *zero;       // an all-zero A main piece
+    const int16_t *scale_a;    // group exponent of every (A tail entry, row): n_at x 128
+    const int16_t *scale_b;    // group exponent of every (B tail entry, column): n_bt x 64
     double *C;
     int c_stride;
     double alpha, beta;
     int32_t *flag;
 };
-
-__device__ __forceinline__ uint64_t emu_desc(uint32_t saddr)
-{
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)(128 >> 4) << 16;     // leading (K) byte offset: adjacent core matrices
-    d |= (uint64_t)(E_SBO >> 4) << 32;   // stride (M/N) byte offset between 8-row groups
-    d |= (uint64_t)1 << 46;
-    return d;
-}
 
 // x 2^e for an FP32 x, exact while the result stays a normal FP32 number
 __device__ __forceinline__ float mul_pow2(float x, int e)
@@ -192,37 +187,50 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
         for (int s = 0; s < NSE; ++s) last[s] = -1;
         bool ok = true;
         for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-            const int64_t c0 = p.kstart[tile];
-            const int nch = (int)(p.kstart[tile + 1] - c0);
-            int2 ent = make_int2(0, 0);
-            for (int c = 0; c < nch && ok; ++c) {
-                if ((c & 31) == 0) ent = c + lane < nch ? p.chunks[c0 + c + lane] : make_int2(0, 0);
-                const int ea = __shfl_sync(0xffffffffu, ent.x, c & 31);
-                const int eb = __shfl_sync(0xffffffffu, ent.y, c & 31);
-                for (int ks = 0; ks < KSTEPS; ++ks, ++sg) {
-                    int go = 1;
-                    if (lane == 0) {
-                        const int s = (int)(sg % NSE);
-                        if (sg >= (uint32_t)NSE &&
-                            !bar_wait(smem_u32(&bars->empty[s]), ((sg / NSE) + 1) & 1u, abort_flag)) {
-                            go = 0;
+            const int64_t s0 = p.kstart[tile];
+            const int nks = (int)(p.kstart[tile + 1] - s0);
+            int4 ent = make_int4(0, 0, 0, 0);
+            uint32_t mine = 0;
+            for (int q = 0; q < nks; ++q, ++sg) {
+                if ((q & 31) == 0) {
+                    ent = q + lane < nks ? p.steps[s0 + q + lane] : make_int4(0, 0, 0, 0);
+                    mine = q + lane < nks ? p.meta[s0 + q + lane] : 0u;
+                }
+                const int ea = __shfl_sync(0xffffffffu, ent.x, q & 31);
+                const int ea2 = __shfl_sync(0xffffffffu, ent.y, q & 31);
+                const int eb = __shfl_sync(0xffffffffu, ent.z, q & 31);
+                const int eb2 = __shfl_sync(0xffffffffu, ent.w, q & 31);
+                const uint32_t meta = __shfl_sync(0xffffffffu, mine, q & 31);
+                int go = 1;
+                if (lane == 0) {
+                    const int s = (int)(sg % NSE);
+                    if (sg >= (uint32_t)NSE &&
+                        !bar_wait(smem_u32(&bars->empty[s]), ((sg / NSE) + 1) & 1u, abort_flag)) {
+                        go = 0;
+                    } else {
+                        const uint32_t fb = smem_u32(&bars->full[s]);
+                        const uint32_t da = sm0 + s * E_STAGE, db = da + E_ATAIL;
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                     "r"((uint32_t)E_STAGE)
+                                     : "memory");
+                        if (meta & PERIOD_LAST) {  // tail step
+                            bulk_copy(da, p.a_tail + (int64_t)(ea - p.at0) * E_ATAIL, E_ATAIL, fb);
+                            bulk_copy(db, p.b_tail + (int64_t)eb * E_BTAIL, E_BTAIL, fb);
                         } else {
-                            const uint32_t fb = smem_u32(&bars->full[s]);
-                            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                                         "r"((uint32_t)E_STAGE)
-                                         : "memory");
-                            bulk_copy(sm0 + s * E_STAGE,
-                                      p.panel_a + (int64_t)(ea - p.ea0) * E_APANEL + ks * E_AKSTEP,
-                                      E_AKSTEP, fb);
-                            bulk_copy(sm0 + s * E_STAGE + E_AKSTEP,
-                                      p.panel_b + (int64_t)eb * E_BPANEL + ks * E_BKSTEP, E_BKSTEP, fb);
-                            last[s] = (int)sg;
+                            bulk_copy(da, p.a_main + (int64_t)(ea - p.am0) * E_AMAIN, E_AMAIN, fb);
+                            bulk_copy(da + E_AMAIN,
+                                      ea2 < 0 ? p.zero : p.a_main + (int64_t)(ea2 - p.am0) * E_AMAIN,
+                                      E_AMAIN, fb);
+                            bulk_copy(db, p.b_main + (int64_t)eb * E_BMAIN, E_BMAIN, fb);
+                            bulk_copy(db + E_BMAIN, eb2 < 0 ? p.zero : p.b_main + (int64_t)eb2 * E_BMAIN,
+                                      E_BMAIN, fb);
                         }
+                        last[s] = (int)sg;
                     }
-                    if (!__shfl_sync(0xffffffffu, go, 0)) {
-                        ok = false;
-                        break;
-                    }
+                }
+                if (!__shfl_sync(0xffffffffu, go, 0)) {
+                    ok = false;
+                    break;
                 }
             }
         }
@@ -233,33 +241,39 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
         __syncwarp();
     } else if (warp == W_MMA) {
         // ------------------------------------------------------------ MMA issue
-        // the warp walks the chunks (its lanes load the period flags 32 chunks at a time);
+        // the warp walks the K steps (its lanes load the period flags 32 steps at a time);
         // lane 0 waits and issues
         uint32_t sg = 0, pg = 0;
         bool ok = true, issued = false;
-        const uint64_t da0 = emu_desc(sm0), db0 = emu_desc(sm0 + E_AKSTEP);
+        // descriptors of stage 0 for both kinds of K step (main: the second column is the
+        // second atom's piece; tail: the piece's second column); a stage or plane only moves
+        // the 14-bit start address field
+        const uint64_t dam = piece_desc(sm0, E_AMAIN), dat = piece_desc(sm0, COLB_A);
+        const uint64_t dbm = piece_desc(sm0 + E_ATAIL, E_BMAIN), dbt = piece_desc(sm0 + E_ATAIL, COLB_B);
         for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-            const int64_t c0 = p.kstart[tile];
-            const int nch = (int)(p.kstart[tile + 1] - c0);
+            const int64_t s0 = p.kstart[tile];
+            const int nks = (int)(p.kstart[tile + 1] - s0);
             uint32_t mine = 0;
-            for (int c = 0; c < nch && ok; ++c) {
-                if ((c & 31) == 0) mine = c + lane < nch ? p.meta[c0 + c + lane] : 0u;
-                const uint32_t meta = __shfl_sync(0xffffffffu, mine, c & 31);
-                const bool first = (meta & PERIOD_FIRST) != 0;
+            for (int q = 0; q < nks && ok; ++q, ++sg) {
+                if ((q & 31) == 0) mine = q + lane < nks ? p.meta[s0 + q + lane] : 0u;
+                const uint32_t meta = __shfl_sync(0xffffffffu, mine, q & 31);
+                const bool first = (meta & PERIOD_FIRST) != 0, tail = (meta & PERIOD_LAST) != 0;
                 int go = 1;
                 if (lane == 0) {
+                    const int s = (int)(sg % NSE);
                     if (first && pg > 0 &&
                         !bar_wait(smem_u32(&bars->acc_empty), (pg - 1) & 1u, abort_flag))
                         go = 0;
-                    for (int ks = 0; ks < KSTEPS && go; ++ks, ++sg) {
-                        const int s = (int)(sg % NSE);
-                        if (!bar_wait(smem_u32(&bars->full[s]), (sg / NSE) & 1u, abort_flag)) {
-                            go = 0;
-                            break;
-                        }
+                    else if (!bar_wait(smem_u32(&bars->full[s]), (sg / NSE) & 1u, abort_flag))
+                        go = 0;
+                    if (go) {
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint64_t sa = da0 + (uint64_t)((s * E_STAGE) >> 4);
-                        const uint64_t sb = db0 + (uint64_t)((s * E_STAGE) >> 4);
+                        // plane strides in 16-byte units: main pieces hold one column per
+                        // plane, tail pieces two
+                        const uint32_t pla = tail ? (2 * COLB_A) >> 4 : COLB_A >> 4;
+                        const uint32_t plb = tail ? (2 * COLB_B) >> 4 : COLB_B >> 4;
+                        const uint64_t sa = (tail ? dat : dam) + (uint64_t)((s * E_STAGE) >> 4);
+                        const uint64_t sb = (tail ? dbt : dbm) + (uint64_t)((s * E_STAGE) >> 4);
                         // level by level (p + q ascending): back to back, the tensor cores
                         // take these 36 products faster in this order than plane by plane
 #pragma unroll
@@ -268,12 +282,11 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
                             for (int pa = 0; pa <= lv; ++pa) {
                                 const int qb = lv - pa;
                                 const int lev = lv < E_LEVELS - 1 ? lv : E_LEVELS - 1;
-                                const uint64_t ad = sa + (uint64_t)((pa * E_APLANE) >> 4);
-                                const uint64_t bd = sb + (uint64_t)((qb * E_BPLANE) >> 4);
+                                const uint64_t ad = sa + (uint64_t)(pa * pla);
+                                const uint64_t bd = sb + (uint64_t)(qb * plb);
                                 // the first product into each accumulator of a period
                                 // overwrites it: (0, l) for l < 6 in this order
-                                const uint32_t acc =
-                                    (first && ks == 0 && pa == 0 && lv < E_LEVELS) ? 0u : 1u;
+                                const uint32_t acc = (first && pa == 0 && lv < E_LEVELS) ? 0u : 1u;
                                 asm volatile(
                                     "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
@@ -282,14 +295,14 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
                             }
                         bar_commit(smem_u32(&bars->empty[s]));
                         issued = true;
+                        if (tail) bar_commit(smem_u32(&bars->acc_full));
                     }
-                    if (go && (meta & PERIOD_LAST)) bar_commit(smem_u32(&bars->acc_full));
                 }
                 if (!__shfl_sync(0xffffffffu, go, 0)) {
                     ok = false;
                     break;
                 }
-                if (meta & PERIOD_LAST) ++pg;
+                if (tail) ++pg;
             }
         }
         if (lane == 0 && issued) {  // retire every MMA before the tensor memory is released
@@ -299,31 +312,31 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
         __syncwarp();
     } else {
         // ------------------------------------------------------------ drain and epilogue
-        // the warp walks the chunks like the MMA warp (flags and panel entries 32 at a time);
-        // at every chunk that ends a period it drains the accumulators with the scales of
-        // that chunk's entries (all entries of one atom group in one scale group share them)
+        // the warp walks the K steps like the MMA warp (flags and entries 32 at a time); at
+        // every tail step it drains the accumulators with the scales of the step's tail
+        // pieces (the period's group exponents)
         const int quarter = warp & 3, half = (warp - 2) >> 2;
         const int arow = quarter * 32 + lane;
         const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
         uint32_t pg = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-            const int64_t c0 = p.kstart[tile];
-            const int nch = (int)(p.kstart[tile + 1] - c0);
+            const int64_t s0 = p.kstart[tile];
+            const int nks = (int)(p.kstart[tile + 1] - s0);
             // the smallest words of this thread's row and 32 columns start at zero per tile
 #pragma unroll
             for (int x = 0; x < 32; ++x) lws[(half * 32 + x) * MT + arow] = 0.f;
             bool first_period = true;
             uint32_t mine = 0;
-            int2 ment = make_int2(0, 0);
-            for (int c = 0; c < nch && ok; ++c) {
-                if ((c & 31) == 0) {
-                    mine = c + lane < nch ? p.meta[c0 + c + lane] : 0u;
-                    ment = c + lane < nch ? p.chunks[c0 + c + lane] : make_int2(0, 0);
+            int4 ment = make_int4(0, 0, 0, 0);
+            for (int q = 0; q < nks && ok; ++q) {
+                if ((q & 31) == 0) {
+                    mine = q + lane < nks ? p.meta[s0 + q + lane] : 0u;
+                    ment = q + lane < nks ? p.steps[s0 + q + lane] : make_int4(0, 0, 0, 0);
                 }
-                const uint32_t meta = __shfl_sync(0xffffffffu, mine, c & 31);
-                const int ea_ent = __shfl_sync(0xffffffffu, ment.x, c & 31);
-                const int eb_ent = __shfl_sync(0xffffffffu, ment.y, c & 31);
+                const uint32_t meta = __shfl_sync(0xffffffffu, mine, q & 31);
+                const int ea_ent = __shfl_sync(0xffffffffu, ment.x, q & 31);
+                const int eb_ent = __shfl_sync(0xffffffffu, ment.z, q & 31);
                 if (!(meta & PERIOD_LAST)) continue;
                 // scales first, so their loads overlap the wait for the accumulators
                 const int ea = p.scale_a[(int64_t)ea_ent * MT + arow];
@@ -336,7 +349,7 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const bool last_period = (c == nch - 1);
+                const bool last_period = (q == nks - 1);
 #pragma unroll 1
                 for (int q = 0; q < 4; ++q) {  // eight columns at a time
                     const int col0 = half * 32 + q * 8;
@@ -409,8 +422,8 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_emu(const EmuArgs p)
                 first_period = false;
             }
             if (!ok) break;
-            if (nch == 0 && arow < GI * NB) {
-                // a tile without chunks: its C blocks get beta C
+            if (nks == 0 && arow < GI * NB) {
+                // a tile without K steps: its C blocks get beta C
                 const int si = arow / NB, a = arow % NB;
                 for (int x = 0; x < 32; ++x) {
                     const int col = half * 32 + x, jl = col / NB, bo = col % NB;

@@ -3,9 +3,9 @@
 // C <- beta C + alpha mask_{P_C}(A.B) with every FP64 operand value split into three BF16
 // terms x ~ x0 + x1 + x2 (about 26 bits; see split3) and the product formed as the six
 // cross products A_p B_q with p + q <= 2, accumulated in FP32 in tensor memory.  Every
-// DRAIN chunks the FP32 accumulator is drained into a per-thread double-float (hi, lo)
-// sum, so FP32 rounding only acts within a drain period; the result is written back in
-// FP64.
+// DRAIN chunks (of KSTEPS K steps) the FP32 accumulator is drained into a per-thread
+// double-float (hi, lo) sum, so FP32 rounding only acts within a drain period; the result is
+// written back in FP64.
 //
 // Local densification.  9x9 blocks do not fit MMA shapes, so atoms are grouped in space
 // (Morton order): an M group holds floor(128/nb) atoms (126 rows for nb = 9), an N group
@@ -32,11 +32,11 @@
 // reach its second atom's column through the leading byte offset, those of a tail step
 // its second column.  The tile kernel moves each piece with one TMA bulk copy; one thread
 // issues the MMAs, eight warps drain the accumulators (bsmm_split_kernel.cuh).  A pieces
-// are packed in batches of M groups so that their scratch stays below A_PANEL_CAP bytes.
+// are packed in batches of M groups so that their scratch stays below A_PIECE_CAP bytes.
 //
-// The emulated-FP64 product (bsmm_emu_kernel.cuh) keeps fixed K groups of CA atoms (4 for
-// nb = 9, 12 for nb = 4) packed into one panel per (atom group, K group) pair, because its
-// scale groups are runs of K groups.
+// The emulated-FP64 product (bsmm_emu_kernel.cuh) uses the same pieces with eight digit
+// planes instead of three BF16 terms; its K steps come grouped by tail group, which is its
+// scale group.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -52,7 +52,6 @@ namespace {
 constexpr int ST = 320;                      // threads per CTA (10 warps)
 constexpr int MT = 128, NT = 64, KCH = 48;   // tile M, N and K chunk
 constexpr int KSTEPS = KCH / 16;             // MMA K steps per chunk
-constexpr int TAILW = 4;                     // values in an atom's tail piece
 constexpr int A_CHUNK = 3 * MT * KCH * 2;   // 36 KB: three planes of 128 rows x 48 K
 constexpr int B_CHUNK = 3 * NT * KCH * 2;   // 18 KB
 constexpr int STAGE = A_CHUNK + B_CHUNK;    // one shared-memory stage of the split kernel
@@ -61,7 +60,7 @@ constexpr int DRAIN = 4;                     // chunks per FP32 accumulation per
 constexpr int NACC = 4;                      // FP32 accumulators in tensor memory
 constexpr int TMEM_COLS = NACC * NT;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
-constexpr size_t A_PANEL_CAP = (size_t)12 << 30;  // scratch bound for one batch of A panels
+constexpr size_t A_PIECE_CAP = (size_t)12 << 30;  // scratch bound for one batch of A pieces
 
 // Split-product pieces and the shared-memory slots of one stage (KSTEPS K steps).
 constexpr int COLB_A = MT * 16, COLB_B = NT * 16;  // one core column: 2 KB (A), 1 KB (B)
@@ -77,19 +76,6 @@ static_assert(KSTEPS * (A_SLOT + B_SLOT) == STAGE, "stage layout");
 template <int NB> struct KPieces;
 template <> struct KPieces<9> { static constexpr int MAINW = 8, TW = 1, TG = 16; };
 template <> struct KPieces<4> { static constexpr int MAINW = 0, TW = 4, TG = 4; };
-
-// Atoms per chunk and core-matrix columns of an atom's pieces.
-template <int NB> struct KLayout;
-template <> struct KLayout<9> {
-    static constexpr int CA = 4, MAINW = 8;
-    __host__ __device__ static constexpr int main_col(int a) { return a; }
-    __host__ __device__ static constexpr int tail_col(int a) { return 4 + (a >> 1); }
-};
-template <> struct KLayout<4> {
-    static constexpr int CA = 12, MAINW = 0;
-    __host__ __device__ static constexpr int main_col(int) { return 0; }
-    __host__ __device__ static constexpr int tail_col(int a) { return a >> 1; }
-};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -179,23 +165,23 @@ __device__ void bitmap_emit(const uint32_t *bits, int words, int64_t *count, int
     }
 }
 
-// K groups of each atom group (one CTA per group): every K group holding a column of a row
-// of the group's atoms in pattern (rp, col).
+// Keys of each atom group (one CTA per group): the key (key_of: Morton rank or tail group)
+// of every column of a row of the group's atoms in pattern (rp, col).
 template <bool FILL>
 __global__ void __launch_bounds__(256)
-k_group_kappa(int gsize, const int32_t *atoms, const int64_t *rp, const int32_t *col,
-              const int32_t *kg_of, int n_kappa, int64_t *count, const int64_t *start,
+k_group_keys(int gsize, const int32_t *atoms, const int64_t *rp, const int32_t *col,
+              const int32_t *key_of, int n_keys, int64_t *count, const int64_t *start,
               int32_t *out)
 {
     extern __shared__ uint32_t bits[];
-    const int words = (n_kappa + 31) >> 5;
+    const int words = (n_keys + 31) >> 5;
     for (int w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
     __syncthreads();
     for (int s = 0; s < gsize; ++s) {
         const int i = atoms[(int64_t)blockIdx.x * gsize + s];
         if (i < 0) continue;
         for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) {
-            const int kk = kg_of[col[e]];
+            const int kk = key_of[col[e]];
             atomicOr(&bits[kk >> 5], 1u << (kk & 31));
         }
     }
@@ -203,18 +189,17 @@ k_group_kappa(int gsize, const int32_t *atoms, const int64_t *rp, const int32_t 
     bitmap_emit<FILL>(bits, words, count + blockIdx.x, FILL ? start[blockIdx.x] : 0, out);
 }
 
-// K groups of each tile (one CTA per tile): the groups of the atoms k reachable from the M
-// group through P_A and from the N group through P_B (P_B symmetric: (k, j) in P_B <=> k in
-// row j).
+// Keys of each tile (one CTA per tile): the keys of the atoms k reachable from the M group
+// through P_A and from the N group through P_B (P_B symmetric: (k, j) in P_B <=> k in row j).
 template <bool FILL>
 __global__ void __launch_bounds__(256)
-k_tile_kappa(int n_atoms, const int2 *tiles, int gi, int gj, const int32_t *g_atoms,
+k_tile_keys(int n_atoms, const int2 *tiles, int gi, int gj, const int32_t *g_atoms,
              const int32_t *h_atoms, const int64_t *a_rp, const int32_t *a_col,
-             const int64_t *b_rp, const int32_t *b_col, const int32_t *kg_of, int n_kappa,
+             const int64_t *b_rp, const int32_t *b_col, const int32_t *key_of, int n_keys,
              int64_t *count, const int64_t *start, int32_t *out)
 {
     extern __shared__ uint32_t bm[];
-    const int words = (n_atoms + 31) >> 5, kwords = (n_kappa + 31) >> 5;
+    const int words = (n_atoms + 31) >> 5, kwords = (n_keys + 31) >> 5;
     uint32_t *ba = bm, *bb = bm + words, *bk = bm + 2 * words;
     for (int w = threadIdx.x; w < 2 * words + kwords; w += blockDim.x) bm[w] = 0u;
     __syncthreads();
@@ -237,37 +222,12 @@ k_tile_kappa(int n_atoms, const int2 *tiles, int gi, int gj, const int32_t *g_at
         while (v) {
             const int bit = __ffs(v) - 1;
             v &= v - 1;
-            const int kk = kg_of[w * 32 + bit];
+            const int kk = key_of[w * 32 + bit];
             atomicOr(&bk[kk >> 5], 1u << (kk & 31));
         }
     }
     __syncthreads();
     bitmap_emit<FILL>(bk, kwords, count + blockIdx.x, FILL ? start[blockIdx.x] : 0, out);
-}
-
-// Chunk table: for every K group of every tile, the A panel (entry of the M group's list)
-// and the B panel (entry of the N group's list).
-__global__ void __launch_bounds__(256)
-k_tile_chunks(const int2 *tiles, const int64_t *kstart, const int32_t *tile_kappa,
-              const int64_t *ga_ptr, const int32_t *ga_kappa, const int64_t *hb_ptr,
-              const int32_t *hb_kappa, int2 *chunks)
-{
-    const int2 t = tiles[blockIdx.x];
-    auto pos = [](const int32_t *lst, int64_t lo, int64_t hi, int key) {
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (lst[mid] < key)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        return lo;
-    };
-    for (int64_t c = kstart[blockIdx.x] + threadIdx.x; c < kstart[blockIdx.x + 1]; c += blockDim.x) {
-        const int kk = tile_kappa[c];
-        chunks[c] = make_int2((int)pos(ga_kappa, ga_ptr[t.x], ga_ptr[t.x + 1], kk),
-                              (int)pos(hb_kappa, hb_ptr[t.y], hb_ptr[t.y + 1], kk));
-    }
 }
 
 // position of key in the ascending list lst[lo, hi) (the key is present)
@@ -331,7 +291,7 @@ k_tile_cidx(const int2 *tiles, int gi, int gj, const int32_t *g_atoms, const int
     }
 }
 
-// ---------------------------------------------------------------- panel packing
+// ---------------------------------------------------------------- piece packing
 
 __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi)
 {
@@ -357,20 +317,20 @@ __device__ __forceinline__ void put_row3(uint8_t *dst, uint32_t off, int plane_b
     }
 }
 
-// Block index of every (slot, K-group atom) pair of every panel entry (one CTA per entry):
+// Block index of every (slot, key atom) pair of every piece entry (one CTA per entry):
 // A side (LEFT): block (i_slot, k) of P_A; B side: block (k, j_slot) of P_B, found as
 // block (j, k) of row j and its transpose.  -1 where the pattern has no block.  Patterns
 // do not change between products, so the table is built once per pattern triple.
 template <bool LEFT>
 __global__ void __launch_bounds__(256)
-k_panel_index(int gsize, int ca, const int32_t *ent_group, const int32_t *ent_kappa,
-              const int32_t *atoms, const int32_t *kg_atoms, const int64_t *rp,
+k_piece_index(int gsize, int ca, const int32_t *ent_group, const int32_t *ent_key,
+              const int32_t *atoms, const int32_t *key_atoms, const int64_t *rp,
               const int32_t *col, const int64_t *tr, int32_t *index)
 {
     const int64_t e = blockIdx.x;
-    const int grp = ent_group[e], kk = ent_kappa[e];
+    const int grp = ent_group[e], kk = ent_key[e];
     for (int q = threadIdx.x; q < gsize * ca; q += blockDim.x) {
-        const int x = atoms[(int64_t)grp * gsize + q / ca], k = kg_atoms[(int64_t)kk * ca + q % ca];
+        const int x = atoms[(int64_t)grp * gsize + q / ca], k = key_atoms[(int64_t)kk * ca + q % ca];
         int64_t b = (x >= 0 && k >= 0) ? find_block(rp, col, x, k) : -1;
         if (!LEFT && b >= 0) b = tr[b];
         index[e * gsize * ca + q] = (int32_t)b;
@@ -378,7 +338,7 @@ k_panel_index(int gsize, int ca, const int32_t *ent_group, const int32_t *ent_ka
 }
 
 // Main pieces of entries [e0, e0 + n) (one thread per (entry, row)), entry = (atom group,
-// K atom k), index = its block per slot (k_panel_index with one atom per K group).  A side
+// K atom k), index = its block per slot (k_piece_index with one atom per key).  A side
 // (LEFT): row r = (slot r / NB, orbital o), K = orbital m < 8 of k: A_ik[o][m]; B side: row
 // r = (slot, orbital o of j), K = m: B_kj[m][o].
 template <int NB, bool LEFT>
@@ -463,91 +423,89 @@ struct SplitArgs {
 constexpr int SMEM = NS * STAGE + BAR_BYTES;     // pipeline stages + barriers
 constexpr int SMEM_E = NSE * E_STAGE + E_LWORDS + BAR_BYTES;
 
-// ---------------------------------------------------------------- emulated-FP64 packing
+// ---------------------------------------------------------------- emulated-FP64 plan and packing
 
-// Byte offset of (row, core-matrix column col of the chunk's K layout, digit plane) in an
-// emulated-FP64 panel: K step col / 2, then the plane, then the canonical no-swizzle
-// K-major image of rows x 16 K (core matrices adjacent along K, 8-row groups 256 B apart).
-__device__ __forceinline__ uint32_t emu_off(int rows, int row, int col, int plane)
+// K-step table of the emulated product (one thread per tile; COUNT writes the number of
+// steps of each tile, FILL the steps): per tail group the tile touches (ascending), main
+// steps pairing the tile's K atoms of that group (Morton ranks, ascending), then the group's
+// tail step; meta flags the first and the last (tail) step of each such scale period.
+template <bool FILL>
+__global__ void __launch_bounds__(128)
+k_emu_steps(int n_tiles, int tg, const int2 *tiles, const int64_t *ka_start,
+            const int32_t *tile_rank, const int64_t *kt_start, const int32_t *tile_tau,
+            const int64_t *gm_ptr, const int32_t *gm_key, const int64_t *hm_ptr,
+            const int32_t *hm_key, const int64_t *gt_ptr, const int32_t *gt_key,
+            const int64_t *ht_ptr, const int32_t *ht_key, const int64_t *step_start,
+            int64_t *count, int4 *steps, uint8_t *meta)
 {
-    return (uint32_t)((col >> 1) * EMU_P * rows * 32 + plane * rows * 32 + (row >> 3) * E_SBO +
-                      (col & 1) * 128 + (row & 7) * 16);
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_tiles) return;
+    const int2 t = tiles[b];
+    const int64_t a0 = ka_start[b], na = ka_start[b + 1] - a0;
+    const int64_t t0 = kt_start[b], nt = kt_start[b + 1] - t0;
+    int64_t s = FILL ? step_start[b] : 0, p = 0;
+    for (int64_t i = 0; i < nt; ++i) {
+        const int tau = tile_tau[t0 + i];
+        int64_t p2 = p;
+        while (p2 < na && tile_rank[a0 + p2] / tg == tau) ++p2;
+        for (int64_t q = p; q < p2; q += 2, ++s) {
+            if (!FILL) continue;
+            const int k0 = tile_rank[a0 + q], k1 = q + 1 < p2 ? tile_rank[a0 + q + 1] : -1;
+            int4 e;
+            e.x = (int)list_pos(gm_key, gm_ptr[t.x], gm_ptr[t.x + 1], k0);
+            e.y = k1 < 0 ? -1 : (int)list_pos(gm_key, gm_ptr[t.x], gm_ptr[t.x + 1], k1);
+            e.z = (int)list_pos(hm_key, hm_ptr[t.y], hm_ptr[t.y + 1], k0);
+            e.w = k1 < 0 ? -1 : (int)list_pos(hm_key, hm_ptr[t.y], hm_ptr[t.y + 1], k1);
+            steps[s] = e;
+            meta[s] = q == p ? PERIOD_FIRST : 0;
+        }
+        if (FILL) {
+            steps[s] = make_int4((int)list_pos(gt_key, gt_ptr[t.x], gt_ptr[t.x + 1], tau), -1,
+                                 (int)list_pos(ht_key, ht_ptr[t.y], ht_ptr[t.y + 1], tau), -1);
+            meta[s] = PERIOD_LAST | (p2 == p ? PERIOD_FIRST : 0);
+        }
+        ++s;
+        p = p2;
+    }
+    if (!FILL) count[b] = s;
 }
 
-// Scale-period flags of every chunk (one CTA per tile): a period is a run of a tile's
-// chunks whose K groups share a scale group (K group >> 2).
+// Group exponent of every row of every tail entry (one thread per (entry, row)): the
+// largest emu_exponent of the row's values over the blocks of the entry's tail group (all
+// orbitals of its atoms).  A side (LEFT): row r = (slot, orbital o), values A_ik[o][m]; B
+// side: column r = (slot, orbital o of j), values B_kj[m][o].
+template <int NB, bool LEFT>
 __global__ void __launch_bounds__(256)
-k_emu_periods(const int64_t *kstart, const int32_t *kappa, uint8_t *meta)
+k_emu_rowexp(int64_t n, const int32_t *index, const double *__restrict__ X, int stride,
+             int16_t *out)
 {
-    const int64_t c0 = kstart[blockIdx.x], c1 = kstart[blockIdx.x + 1];
-    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-        const int sg = kappa[c] >> 2;
-        uint8_t f = 0;
-        if (c == c0 || (kappa[c - 1] >> 2) != sg) f |= 1;
-        if (c == c1 - 1 || (kappa[c + 1] >> 2) != sg) f |= 2;
-        meta[c] = f;
-    }
-}
-
-// Largest exponent (emu_exponent) of every scalar row of every A panel entry (one CTA
-// of 128 threads per entry = (M group, K group)): row r = (slot r / NB, orbital r % NB).
-template <int NB>
-__global__ void __launch_bounds__(MT)
-k_emu_rowexp_a(const int32_t *index, const double *__restrict__ A, int stride, int16_t *out)
-{
-    constexpr int GI = MT / NB, CA = KLayout<NB>::CA;
-    const int64_t e = blockIdx.x;
-    const int r = threadIdx.x;
+    constexpr int ROWS = LEFT ? MT : NT, G = ROWS / NB, TG = KPieces<NB>::TG;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n * ROWS) return;
+    const int64_t e = q / ROWS;
+    const int r = (int)(q % ROWS), o = r % NB;
     int m = EMU_NONE;
-    if (r < GI * NB) {
-        const int32_t *blk = index + e * (GI * CA) + (r / NB) * CA;
-        const int o = r % NB;
-        for (int a = 0; a < CA; ++a) {
-            const int64_t b = __ldg(&blk[a]);
+    if (r < G * NB) {
+        const int32_t *blk = index + (e * G + r / NB) * TG;
+        for (int u = 0; u < TG; ++u) {
+            const int64_t b = __ldg(&blk[u]);
             if (b < 0) continue;
-            for (int k = 0; k < NB; ++k) m = max(m, emu_exponent(A[b * stride + o * NB + k]));
+            for (int k = 0; k < NB; ++k)
+                m = max(m, emu_exponent(LEFT ? X[b * stride + o * NB + k] : X[b * stride + k * NB + o]));
         }
     }
-    out[e * MT + r] = (int16_t)m;
+    out[q] = (int16_t)m;
 }
 
-// The same for every scalar column of every B panel entry (one CTA of 64 threads per entry
-// = (N group, K group)): column c = (slot c / NB, orbital o); values B_kj[m][o].
-template <int NB>
-__global__ void __launch_bounds__(NT)
-k_emu_rowexp_b(const int32_t *index, const double *__restrict__ B, int stride, int16_t *out)
+// Tail entry of the tail group of every main entry (one thread per main entry): the scale of
+// a main piece is its group's.
+__global__ void k_emu_main_tail(int64_t n, int tg, const int32_t *group, const int32_t *rank,
+                                const int64_t *t_ptr, const int32_t *t_key, int32_t *out)
 {
-    constexpr int GJ = NT / NB, CA = KLayout<NB>::CA;
-    const int64_t e = blockIdx.x;
-    const int c = threadIdx.x;
-    int m = EMU_NONE;
-    if (c < GJ * NB) {
-        const int32_t *blk = index + e * (GJ * CA) + (c / NB) * CA;
-        const int o = c % NB;
-        for (int a = 0; a < CA; ++a) {
-            const int64_t b = __ldg(&blk[a]);
-            if (b < 0) continue;
-            for (int k = 0; k < NB; ++k) m = max(m, emu_exponent(B[b * stride + k * NB + o]));
-        }
-    }
-    out[e * NT + c] = (int16_t)m;
-}
-
-// Group exponent of every (entry, row): the largest row exponent over the entries of the
-// same atom group whose K groups share a scale group (K group >> 2).  The entries of a
-// group are sorted by K group, so those entries are adjacent.
-__global__ void k_emu_group_scale(int width, const int64_t *ptr, const int32_t *kappa,
-                                  const int32_t *group, const int16_t *rowexp, int16_t *scale)
-{
-    const int64_t e = blockIdx.x;
-    const int r = threadIdx.x;
-    const int g = group[e], sg = kappa[e] >> 2;
-    int64_t lo = e, hi = e + 1;
-    while (lo > ptr[g] && (kappa[lo - 1] >> 2) == sg) --lo;
-    while (hi < ptr[g + 1] && (kappa[hi] >> 2) == sg) ++hi;
-    int m = EMU_NONE;
-    for (int64_t f = lo; f < hi; ++f) m = max(m, (int)rowexp[f * width + r]);
-    scale[e * width + r] = (int16_t)m;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int g = group[e];
+    out[e] = (int32_t)list_pos(t_key, t_ptr[g], t_ptr[g + 1], rank[e] / tg);
 }
 
 // Eight digit planes of n (<= 8) values as eight 16-byte core-matrix rows (one per plane,
@@ -572,120 +530,76 @@ __device__ __forceinline__ void emu_rows(const double *x, int n, int E, uint4 (&
     for (int p = 0; p < EMU_P; ++p) w[p] = make_uint4(u[p][0], u[p][1], u[p][2], u[p][3]);
 }
 
-// One row of the K pieces of a pair of atoms (a0 even, a0 + 1) of an emulated panel: the
-// two main pieces (8 values each) and the core column the two tails (4 values each) share.
-template <int NB>
-__device__ __forceinline__ void put_pair_emu(uint8_t *panel, int rows, int r, int a0, int E,
-                                             const double (&x0)[KLayout<NB>::MAINW + TAILW],
-                                             const double (&x1)[KLayout<NB>::MAINW + TAILW])
+// Emulated main pieces of entries [e0, e0 + n) (one thread per (entry, row)): as
+// k_pack_main, eight digit planes of orbitals 0-7 against the row's group exponent.
+template <int NB, bool LEFT>
+__global__ void __launch_bounds__(256)
+k_pack_main_emu(int64_t e0, int64_t n, const int32_t *index, const int32_t *main_tail,
+                const int16_t *scale, const double *__restrict__ X, int stride, uint8_t *pieces)
 {
-    constexpr int MW = KLayout<NB>::MAINW;
+    constexpr int ROWS = LEFT ? MT : NT, G = ROWS / NB, COLB = LEFT ? COLB_A : COLB_B;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n * ROWS) return;
+    const int64_t el = q / ROWS, e = e0 + el;
+    const int r = (int)(q % ROWS), o = r % NB;
+    const bool row = r < G * NB;
+    const int64_t b = row ? __ldg(&index[e * G + r / NB]) : -1;
+    const int E = row ? (int)scale[(int64_t)main_tail[e] * ROWS + r] : EMU_NONE;
+    double x[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+        x[m] = b < 0 ? 0.0 : (LEFT ? X[b * stride + o * NB + m] : X[b * stride + m * NB + o]);
     uint4 w[EMU_P];
-    if (MW) {
-        emu_rows(x0, MW, E, w);
+    emu_rows(x, 8, E, w);
+    uint8_t *piece = pieces + el * (EMU_P * COLB);
 #pragma unroll
-        for (int p = 0; p < EMU_P; ++p)
-            *reinterpret_cast<uint4 *>(panel + emu_off(rows, r, KLayout<NB>::main_col(a0), p)) = w[p];
-        emu_rows(x1, MW, E, w);
-#pragma unroll
-        for (int p = 0; p < EMU_P; ++p)
-            *reinterpret_cast<uint4 *>(panel + emu_off(rows, r, KLayout<NB>::main_col(a0 + 1), p)) =
-                w[p];
-    }
-    double t[8];
-#pragma unroll
-    for (int m = 0; m < TAILW; ++m) {
-        t[m] = x0[MW + m];
-        t[TAILW + m] = x1[MW + m];
-    }
-    emu_rows(t, 8, E, w);
-#pragma unroll
-    for (int p = 0; p < EMU_P; ++p)
-        *reinterpret_cast<uint4 *>(panel + emu_off(rows, r, KLayout<NB>::tail_col(a0), p)) = w[p];
+    for (int pl = 0; pl < EMU_P; ++pl)
+        *reinterpret_cast<uint4 *>(piece + piece_off(pl, COLB, 0, 0, r)) = w[pl];
 }
 
-// Emulated A panels of entries [e0, e0 + gridDim.x): as k_pack_a, eight digit planes per
-// value against the (entry, row) group exponent.
-template <int NB>
+// Emulated tail pieces of entries [e0, e0 + n) (one thread per (entry, row)): as
+// k_pack_tail, eight digit planes against the row's group exponent.
+template <int NB, bool LEFT>
 __global__ void __launch_bounds__(256)
-k_pack_a_emu(int64_t e0, const int32_t *index, const int16_t *scale, const double *__restrict__ A,
-             int stride, uint8_t *panels)
+k_pack_tail_emu(int64_t e0, int64_t n, const int32_t *index, const int16_t *scale,
+                const double *__restrict__ X, int stride, uint8_t *pieces)
 {
-    constexpr int GI = MT / NB, CA = KLayout<NB>::CA, KA = KLayout<NB>::MAINW + TAILW;
-    const int64_t e = e0 + blockIdx.x;
-    const int32_t *blk = index + e * (GI * CA);
-    uint8_t *panel = panels + (int64_t)blockIdx.x * E_APANEL;
-    for (int q = threadIdx.x; q < MT * (CA / 2); q += blockDim.x) {
-        const int a0 = 2 * (q / MT), r = q % MT;
-        const bool row = r < GI * NB;
-        const int64_t b0 = row ? __ldg(&blk[(r / NB) * CA + a0]) : -1;
-        const int64_t b1 = row ? __ldg(&blk[(r / NB) * CA + a0 + 1]) : -1;
-        const int E = row ? (int)scale[e * MT + r] : EMU_NONE;
-        const int o = r % NB;
-        double x0[KA], x1[KA];
+    constexpr int ROWS = LEFT ? MT : NT, G = ROWS / NB, COLB = LEFT ? COLB_A : COLB_B;
+    constexpr int MW = KPieces<NB>::MAINW, TW = KPieces<NB>::TW, TG = KPieces<NB>::TG;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n * ROWS) return;
+    const int64_t el = q / ROWS, e = e0 + el;
+    const int r = (int)(q % ROWS), o = r % NB;
+    const bool row = r < G * NB;
+    const int32_t *blk = index + (e * G + (row ? r / NB : 0)) * TG;
+    const int E = row ? (int)scale[e * ROWS + r] : EMU_NONE;
+    uint8_t *piece = pieces + el * (2 * EMU_P * COLB);
 #pragma unroll
-        for (int m = 0; m < KA; ++m) {
-            x0[m] = (b0 >= 0 && m < NB) ? A[b0 * stride + o * NB + m] : 0.0;
-            x1[m] = (b1 >= 0 && m < NB) ? A[b1 * stride + o * NB + m] : 0.0;
-        }
-        put_pair_emu<NB>(panel, MT, r, a0, E, x0, x1);
-    }
-}
-
-// Emulated B panels (one CTA per entry): row r of the panel = column of C; K = (atom,
-// orbital m): B_kj[m][o], against the (entry, column) group exponent.
-template <int NB>
-__global__ void __launch_bounds__(256)
-k_pack_b_emu(const int32_t *index, const int16_t *scale, const double *__restrict__ B, int stride,
-             uint8_t *panels)
-{
-    constexpr int GJ = NT / NB, CA = KLayout<NB>::CA, KA = KLayout<NB>::MAINW + TAILW;
-    const int64_t e = blockIdx.x;
-    const int32_t *blk = index + e * (GJ * CA);
-    uint8_t *panel = panels + e * E_BPANEL;
-    for (int q = threadIdx.x; q < NT * (CA / 2); q += blockDim.x) {
-        const int a0 = 2 * (q / NT), r = q % NT;
-        const bool row = r < GJ * NB;
-        const int64_t b0 = row ? __ldg(&blk[(r / NB) * CA + a0]) : -1;
-        const int64_t b1 = row ? __ldg(&blk[(r / NB) * CA + a0 + 1]) : -1;
-        const int E = row ? (int)scale[e * NT + r] : EMU_NONE;
-        const int o = r % NB;
-        double x0[KA], x1[KA];
+    for (int c = 0; c < 2; ++c) {
+        double x[8];
 #pragma unroll
-        for (int m = 0; m < KA; ++m) {
-            x0[m] = (b0 >= 0 && m < NB) ? B[b0 * stride + m * NB + o] : 0.0;
-            x1[m] = (b1 >= 0 && m < NB) ? B[b1 * stride + m * NB + o] : 0.0;
+        for (int v = 0; v < 8; ++v) {
+            const int pos = 8 * c + v, u = pos / TW, m = MW + pos % TW;
+            const int64_t b = row ? __ldg(&blk[u]) : -1;
+            x[v] = b < 0 ? 0.0 : (LEFT ? X[b * stride + o * NB + m] : X[b * stride + m * NB + o]);
         }
-        put_pair_emu<NB>(panel, NT, r, a0, E, x0, x1);
+        uint4 w[EMU_P];
+        emu_rows(x, 8, E, w);
+#pragma unroll
+        for (int pl = 0; pl < EMU_P; ++pl)
+            *reinterpret_cast<uint4 *>(piece + piece_off(pl, 2 * COLB, c, COLB, r)) = w[pl];
     }
 }
 
 // ---------------------------------------------------------------- host side
 
 struct Groups {
-    int gi = 0, gj = 0, ca = 0;      // atoms per M, N and K group
-    int n_g = 0, n_h = 0, n_kappa = 0;
-    DevBuf g_atoms, h_atoms, kg_atoms, g_of, h_of, kg_of;
-    // split product: K atoms by Morton rank, tail groups of tg consecutive ranks
+    int gi = 0, gj = 0;              // atoms per M and N group
+    int n_g = 0, n_h = 0;
+    DevBuf g_atoms, h_atoms, g_of, h_of;
+    // K atoms by Morton rank, tail groups of tg consecutive ranks
     int tg = 0, n_tau = 0;
     DevBuf rank_atoms, rank_of, tg_atoms, tg_of;
-};
-
-struct Batch {
-    int tile0, tile1;   // tiles [tile0, tile1)
-    int64_t e0, e1;     // A panel entries [e0, e1)
-};
-
-struct SplitPlan {
-    int n_tiles = 0;
-    int64_t n_chunks = 0, n_ga = 0, n_hb = 0;
-    double mma_flops = 0.0;  // tensor-core flops of one product over these tiles
-    std::vector<Batch> batches;
-    std::vector<int64_t> batch_chunks;
-    DevBuf tiles, kstart, tile_kappa, chunks, cidx;
-    DevBuf ga_ptr, ga_kappa, ga_group, hb_ptr, hb_kappa, hb_group;
-    DevBuf ga_index, hb_index;  // block of every (slot, K-group atom) pair of every entry
-    DevBuf meta;                // emulated product: scale-period flags per chunk (on demand)
 };
 
 // Piece entries of one operand kind (A or B, main or tail): per atom group, ascending keys
@@ -702,15 +616,25 @@ struct PieceBatch {
     int64_t at0, at1;        // A tail entries [at0, at1)
 };
 
-// Plan of one split product (pattern triple): tiles, K-step table, piece lists.
+// Piece lists of one product (pattern triple), shared by its split and emulated plans.
+struct PieceSet {
+    PieceList am, at, bm, bt;  // A main, A tail, B main, B tail
+    DevBuf zero;               // an all-zero main piece (stands for a missing second atom)
+    DevBuf am_tail, bm_tail;   // emulated product: the tail entry of every main entry's group
+};
+
+// Plan of one tensor-core product (pattern triple): tiles, K-step table, batches.  Split
+// plans take the main steps of a tile first, then its tail steps; emulated plans take the
+// steps of one tail group (its scale period) together, its tail step last, and flag the
+// first and last step of every period in meta.
 struct PiecePlan {
     int n_tiles = 0;
     int64_t n_steps = 0;
     double mma_flops = 0.0;  // tensor-core flops of one product over these tiles
     std::vector<PieceBatch> batches;
     std::vector<int64_t> batch_steps;
-    DevBuf tiles, kstart, nmain, steps, cidx, zero;
-    PieceList am, at, bm, bt;
+    DevBuf tiles, kstart, nmain, steps, meta, cidx;
+    std::shared_ptr<PieceSet> ps;
 };
 
 // Morton order of the atoms (positions quantised to 1024 per box edge).
@@ -764,33 +688,26 @@ cq_status get_groups(cq_ctx *ctx, const cq_pattern *p, Groups **out)
     const int nb = g.uniform_nb;
     gr->gi = MT / nb;
     gr->gj = NT / nb;
-    gr->ca = nb == 9 ? KLayout<9>::CA : KLayout<4>::CA;
     gr->n_g = (g.n_atoms + gr->gi - 1) / gr->gi;
     gr->n_h = (g.n_atoms + gr->gj - 1) / gr->gj;
-    gr->n_kappa = (g.n_atoms + gr->ca - 1) / gr->ca;
-    std::vector<int32_t> order = spatial_order(g);
-    std::vector<int32_t> ga((size_t)gr->n_g * gr->gi, -1), ha((size_t)gr->n_h * gr->gj, -1),
-        ka((size_t)gr->n_kappa * gr->ca, -1);
     gr->tg = nb == 9 ? KPieces<9>::TG : KPieces<4>::TG;
     gr->n_tau = (g.n_atoms + gr->tg - 1) / gr->tg;
-    std::vector<int32_t> ta((size_t)gr->n_tau * gr->tg, -1);
-    std::vector<int32_t> gof(g.n_atoms), hof(g.n_atoms), kof(g.n_atoms), rof(g.n_atoms),
-        tof(g.n_atoms);
+    std::vector<int32_t> order = spatial_order(g);
+    std::vector<int32_t> ga((size_t)gr->n_g * gr->gi, -1), ha((size_t)gr->n_h * gr->gj, -1),
+        ta((size_t)gr->n_tau * gr->tg, -1);
+    std::vector<int32_t> gof(g.n_atoms), hof(g.n_atoms), rof(g.n_atoms), tof(g.n_atoms);
     for (int r = 0; r < g.n_atoms; ++r) {
-        ga[r] = ha[r] = ka[r] = ta[r] = order[r];
+        ga[r] = ha[r] = ta[r] = order[r];
         gof[order[r]] = r / gr->gi;
         hof[order[r]] = r / gr->gj;
-        kof[order[r]] = r / gr->ca;
         rof[order[r]] = r;
         tof[order[r]] = r / gr->tg;
     }
     cq_status st;
     if ((st = upload(ctx, gr->g_atoms, ga.data(), 4 * ga.size())) != CQ_OK ||
         (st = upload(ctx, gr->h_atoms, ha.data(), 4 * ha.size())) != CQ_OK ||
-        (st = upload(ctx, gr->kg_atoms, ka.data(), 4 * ka.size())) != CQ_OK ||
         (st = upload(ctx, gr->g_of, gof.data(), 4 * gof.size())) != CQ_OK ||
         (st = upload(ctx, gr->h_of, hof.data(), 4 * hof.size())) != CQ_OK ||
-        (st = upload(ctx, gr->kg_of, kof.data(), 4 * kof.size())) != CQ_OK ||
         (st = upload(ctx, gr->rank_atoms, order.data(), 4 * order.size())) != CQ_OK ||
         (st = upload(ctx, gr->rank_of, rof.data(), 4 * rof.size())) != CQ_OK ||
         (st = upload(ctx, gr->tg_atoms, ta.data(), 4 * ta.size())) != CQ_OK ||
@@ -803,12 +720,12 @@ cq_status get_groups(cq_ctx *ctx, const cq_pattern *p, Groups **out)
 }
 
 // Key lists of n_groups atom groups in a pattern, key_of mapping an atom to one of n_keys
-// keys (its K group, Morton rank or tail group): every key of a column of a row of the
-// group's atoms.  ptr (n_groups + 1), kappa (ascending per group), group (entry -> group);
+// keys (its Morton rank or tail group): every key of a column of a row of the
+// group's atoms.  ptr (n_groups + 1), keys (ascending per group), group (entry -> group);
 // ptr_host receives ptr.
 cq_status group_lists(cq_ctx *ctx, int n_groups, int gsize, const int32_t *atoms,
                       const cq_pattern *p, const int32_t *key_of, int n_keys, DevBuf &ptr,
-                      DevBuf &kappa, DevBuf &group, std::vector<int64_t> &ptr_host)
+                      DevBuf &keys, DevBuf &group, std::vector<int64_t> &ptr_host)
 {
     cudaStream_t s = ctx->stream;
     cq_status st;
@@ -816,9 +733,9 @@ cq_status group_lists(cq_ctx *ctx, int n_groups, int gsize, const int32_t *atoms
     if ((st = cq_scratch(ctx, "split_cnt", 8 * ((size_t)n_groups + 1), &vc)) != CQ_OK) return st;
     if ((st = cq_alloc(ctx, ptr, 8 * ((size_t)n_groups + 1))) != CQ_OK) return st;
     const size_t shm = 4 * (size_t)((n_keys + 31) / 32);
-    cudaFuncSetAttribute(k_group_kappa<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    cudaFuncSetAttribute(k_group_kappa<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k_group_kappa<false><<<n_groups, 256, shm, s>>>(gsize, atoms, p->row_ptr.as<int64_t>(),
+    cudaFuncSetAttribute(k_group_keys<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(k_group_keys<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k_group_keys<false><<<n_groups, 256, shm, s>>>(gsize, atoms, p->row_ptr.as<int64_t>(),
                                                     p->col.as<int32_t>(), key_of, n_keys,
                                                     (int64_t *)vc, nullptr, nullptr);
     cq_count_launch();
@@ -827,10 +744,10 @@ cq_status group_lists(cq_ctx *ctx, int n_groups, int gsize, const int32_t *atoms
     cudaMemcpyAsync(ptr_host.data(), ptr.ptr, 8 * ptr_host.size(), cudaMemcpyDeviceToHost, s);
     if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "group lists")) != CQ_OK) return st;
     const int64_t n = ptr_host[n_groups];
-    if ((st = cq_alloc(ctx, kappa, 4 * (size_t)(n + 1))) != CQ_OK) return st;
-    k_group_kappa<true><<<n_groups, 256, shm, s>>>(gsize, atoms, p->row_ptr.as<int64_t>(),
+    if ((st = cq_alloc(ctx, keys, 4 * (size_t)(n + 1))) != CQ_OK) return st;
+    k_group_keys<true><<<n_groups, 256, shm, s>>>(gsize, atoms, p->row_ptr.as<int64_t>(),
                                                    p->col.as<int32_t>(), key_of, n_keys, nullptr,
-                                                   ptr.as<int64_t>(), kappa.as<int32_t>());
+                                                   ptr.as<int64_t>(), keys.as<int32_t>());
     cq_count_launch();
     std::vector<int32_t> grp((size_t)n);
     for (int q = 0; q < n_groups; ++q)
@@ -866,124 +783,8 @@ cq_status tile_list(cq_ctx *ctx, const cq_pattern *pC, const Groups *gr, std::ve
     return CQ_OK;
 }
 
-cq_status get_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
-                   const cq_pattern *pC, const Groups *gr, SplitPlan **out)
-{
-    auto key = std::make_tuple(2, pA->id, pB->id, pC->id);
-    auto it = ctx->aux.find(key);
-    if (it != ctx->aux.end()) {
-        *out = static_cast<SplitPlan *>(it->second.get());
-        return CQ_OK;
-    }
-    cudaStream_t s = ctx->stream;
-    auto pl = std::make_shared<SplitPlan>();
-    cq_status st;
-    std::vector<int2> tiles;
-    if ((st = tile_list(ctx, pC, gr, tiles)) != CQ_OK) return st;
-    pl->n_tiles = (int)tiles.size();
-    // K-group lists of the M groups (rows of P_A) and of the N groups (rows of P_B)
-    std::vector<int64_t> ga_host, hb_host;
-    if ((st = group_lists(ctx, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA,
-                          gr->kg_of.as<int32_t>(), gr->n_kappa, pl->ga_ptr, pl->ga_kappa,
-                          pl->ga_group, ga_host)) != CQ_OK ||
-        (st = group_lists(ctx, gr->n_h, gr->gj, gr->h_atoms.as<int32_t>(), pB,
-                          gr->kg_of.as<int32_t>(), gr->n_kappa, pl->hb_ptr, pl->hb_kappa,
-                          pl->hb_group, hb_host)) != CQ_OK)
-        return st;
-    // batches of whole M groups (tiles are sorted by g) whose A panels fit A_PANEL_CAP
-    {
-        const int64_t cap = std::max<int64_t>(1, (int64_t)(A_PANEL_CAP / A_CHUNK));
-        int t0 = 0;
-        while (t0 < pl->n_tiles) {
-            const int g0 = tiles[t0].x;
-            int t1 = t0, g1 = g0;
-            while (t1 < pl->n_tiles) {
-                const int g = tiles[t1].x;
-                if (g != g1) {  // the next M group starts; keep it only if its panels still fit
-                    if (ga_host[g + 1] - ga_host[g0] > cap) break;
-                    g1 = g;
-                }
-                ++t1;
-            }
-            pl->batches.push_back({t0, t1, ga_host[g0], ga_host[g1 + 1]});
-            t0 = t1;
-        }
-    }
-    if ((st = upload(ctx, pl->tiles, tiles.data(), sizeof(int2) * tiles.size())) != CQ_OK) return st;
-    pl->n_ga = ga_host[gr->n_g];
-    pl->n_hb = hb_host[gr->n_h];
-    if ((st = cq_alloc(ctx, pl->ga_index, 4 * ((size_t)pl->n_ga * gr->gi * gr->ca + 1))) != CQ_OK ||
-        (st = cq_alloc(ctx, pl->hb_index, 4 * ((size_t)pl->n_hb * gr->gj * gr->ca + 1))) != CQ_OK)
-        return st;
-    if (pl->n_ga > 0) {
-        k_panel_index<true><<<(unsigned)pl->n_ga, 256, 0, s>>>(
-            gr->gi, gr->ca, pl->ga_group.as<int32_t>(), pl->ga_kappa.as<int32_t>(),
-            gr->g_atoms.as<int32_t>(), gr->kg_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(),
-            pA->col.as<int32_t>(), nullptr, pl->ga_index.as<int32_t>());
-        cq_count_launch();
-    }
-    if (pl->n_hb > 0) {
-        k_panel_index<false><<<(unsigned)pl->n_hb, 256, 0, s>>>(
-            gr->gj, gr->ca, pl->hb_group.as<int32_t>(), pl->hb_kappa.as<int32_t>(),
-            gr->h_atoms.as<int32_t>(), gr->kg_atoms.as<int32_t>(), pB->row_ptr.as<int64_t>(),
-            pB->col.as<int32_t>(), pB->transpose.as<int64_t>(), pl->hb_index.as<int32_t>());
-        cq_count_launch();
-    }
-    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "panel index")) != CQ_OK) return st;
-    if (tiles.empty()) {
-        *out = pl.get();
-        ctx->aux[key] = pl;
-        return CQ_OK;
-    }
-    // K groups and chunk table of every tile
-    const int n_atoms = pA->geo->n_atoms;
-    const size_t shm = 4 * (size_t)(2 * ((n_atoms + 31) / 32) + (gr->n_kappa + 31) / 32);
-    if (shm > 200 * 1024) return cq_fail(ctx, CQ_ERR_INVALID, "split product: too many atoms");
-    void *vc;
-    if ((st = cq_scratch(ctx, "split_cnt", 8 * (tiles.size() + 1), &vc)) != CQ_OK) return st;
-    if ((st = cq_alloc(ctx, pl->kstart, 8 * (tiles.size() + 1))) != CQ_OK) return st;
-    cudaFuncSetAttribute(k_tile_kappa<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    cudaFuncSetAttribute(k_tile_kappa<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k_tile_kappa<false><<<pl->n_tiles, 256, shm, s>>>(
-        n_atoms, pl->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
-        gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
-        pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), gr->kg_of.as<int32_t>(), gr->n_kappa,
-        (int64_t *)vc, nullptr, nullptr);
-    cq_count_launch();
-    if ((st = cq_scan_i64(ctx, (int64_t *)vc, pl->kstart.as<int64_t>(), pl->n_tiles)) != CQ_OK)
-        return st;
-    std::vector<int64_t> ks(pl->n_tiles + 1);
-    cudaMemcpyAsync(ks.data(), pl->kstart.ptr, 8 * ks.size(), cudaMemcpyDeviceToHost, s);
-    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "tile chunks")) != CQ_OK) return st;
-    pl->n_chunks = ks[pl->n_tiles];
-    pl->mma_flops = (double)pl->n_chunks * 6.0 * KSTEPS * 2.0 * MT * NT * 16;
-    if ((st = cq_alloc(ctx, pl->tile_kappa, 4 * (size_t)(pl->n_chunks + 1))) != CQ_OK ||
-        (st = cq_alloc(ctx, pl->chunks, sizeof(int2) * (size_t)(pl->n_chunks + 1))) != CQ_OK ||
-        (st = cq_alloc(ctx, pl->cidx, 4 * ((size_t)pl->n_tiles * gr->gi * gr->gj + 1))) != CQ_OK)
-        return st;
-    k_tile_kappa<true><<<pl->n_tiles, 256, shm, s>>>(
-        n_atoms, pl->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
-        gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
-        pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), gr->kg_of.as<int32_t>(), gr->n_kappa,
-        nullptr, pl->kstart.as<int64_t>(), pl->tile_kappa.as<int32_t>());
-    k_tile_chunks<<<pl->n_tiles, 256, 0, s>>>(
-        pl->tiles.as<int2>(), pl->kstart.as<int64_t>(), pl->tile_kappa.as<int32_t>(),
-        pl->ga_ptr.as<int64_t>(), pl->ga_kappa.as<int32_t>(), pl->hb_ptr.as<int64_t>(),
-        pl->hb_kappa.as<int32_t>(), pl->chunks.as<int2>());
-    k_tile_cidx<<<pl->n_tiles, 256, 0, s>>>(
-        pl->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
-        gr->h_atoms.as<int32_t>(), pC->row_ptr.as<int64_t>(), pC->col.as<int32_t>(),
-        pl->cidx.as<int32_t>());
-    cq_count_launch(3);
-    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "split plan")) != CQ_OK) return st;
-    for (const Batch &bt : pl->batches) pl->batch_chunks.push_back(ks[bt.tile1] - ks[bt.tile0]);
-    *out = pl.get();
-    ctx->aux[key] = pl;
-    return CQ_OK;
-}
-
 // Piece list of one operand kind: the keys of every atom group (group_lists) and the block
-// of every (slot, key atom) pair (k_panel_index); ca atoms per key, key_atoms listing them.
+// of every (slot, key atom) pair (k_piece_index); ca atoms per key, key_atoms listing them.
 template <bool LEFT>
 cq_status piece_list(cq_ctx *ctx, int n_groups, int gsize, const int32_t *atoms,
                      const cq_pattern *p, const int32_t *key_of, int n_keys, int ca,
@@ -995,7 +796,7 @@ cq_status piece_list(cq_ctx *ctx, int n_groups, int gsize, const int32_t *atoms,
     const int64_t n = pl.n();
     if ((st = cq_alloc(ctx, pl.index, 4 * ((size_t)n * gsize * ca + 1))) != CQ_OK) return st;
     if (n > 0) {
-        k_panel_index<LEFT><<<(unsigned)n, 256, 0, ctx->stream>>>(
+        k_piece_index<LEFT><<<(unsigned)n, 256, 0, ctx->stream>>>(
             gsize, ca, pl.group.as<int32_t>(), pl.key.as<int32_t>(), atoms, key_atoms,
             p->row_ptr.as<int64_t>(), p->col.as<int32_t>(),
             LEFT ? nullptr : p->transpose.as<int64_t>(), pl.index.as<int32_t>());
@@ -1004,7 +805,7 @@ cq_status piece_list(cq_ctx *ctx, int n_groups, int gsize, const int32_t *atoms,
     return cq_check_cuda(ctx, cudaGetLastError(), "piece index");
 }
 
-// Keys of every tile (k_tile_kappa with key_of: Morton ranks or tail groups): start
+// Keys of every tile (k_tile_keys with key_of: Morton ranks or tail groups): start
 // (n_tiles + 1) on the device and the host, keys ascending per tile.
 cq_status tile_keys(cq_ctx *ctx, const DevBuf &tiles, int n_tiles, const Groups *gr,
                     const cq_pattern *pA, const cq_pattern *pB, const int32_t *key_of, int n_keys,
@@ -1018,9 +819,9 @@ cq_status tile_keys(cq_ctx *ctx, const DevBuf &tiles, int n_tiles, const Groups 
     void *vc;
     if ((st = cq_scratch(ctx, "split_cnt", 8 * ((size_t)n_tiles + 1), &vc)) != CQ_OK) return st;
     if ((st = cq_alloc(ctx, start, 8 * ((size_t)n_tiles + 1))) != CQ_OK) return st;
-    cudaFuncSetAttribute(k_tile_kappa<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    cudaFuncSetAttribute(k_tile_kappa<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k_tile_kappa<false><<<n_tiles, 256, shm, s>>>(
+    cudaFuncSetAttribute(k_tile_keys<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(k_tile_keys<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k_tile_keys<false><<<n_tiles, 256, shm, s>>>(
         n_atoms, tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
         gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
         pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), key_of, n_keys, (int64_t *)vc, nullptr,
@@ -1031,7 +832,7 @@ cq_status tile_keys(cq_ctx *ctx, const DevBuf &tiles, int n_tiles, const Groups 
     cudaMemcpyAsync(start_host.data(), start.ptr, 8 * start_host.size(), cudaMemcpyDeviceToHost, s);
     if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "tile keys")) != CQ_OK) return st;
     if ((st = cq_alloc(ctx, keys, 4 * (size_t)(start_host[n_tiles] + 1))) != CQ_OK) return st;
-    k_tile_kappa<true><<<n_tiles, 256, shm, s>>>(
+    k_tile_keys<true><<<n_tiles, 256, shm, s>>>(
         n_atoms, tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
         gr->h_atoms.as<int32_t>(), pA->row_ptr.as<int64_t>(), pA->col.as<int32_t>(),
         pB->row_ptr.as<int64_t>(), pB->col.as<int32_t>(), key_of, n_keys, nullptr,
@@ -1040,10 +841,51 @@ cq_status tile_keys(cq_ctx *ctx, const DevBuf &tiles, int n_tiles, const Groups 
     return cq_check_cuda(ctx, cudaGetLastError(), "tile keys");
 }
 
-cq_status get_piece_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
+cq_status get_pieces(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
+                     const cq_pattern *pC, const Groups *gr, std::shared_ptr<PieceSet> *out)
+{
+    auto key = std::make_tuple(5, pA->id, pB->id, pC->id);
+    auto it = ctx->aux.find(key);
+    if (it != ctx->aux.end()) {
+        *out = std::static_pointer_cast<PieceSet>(it->second);
+        return CQ_OK;
+    }
+    auto ps = std::make_shared<PieceSet>();
+    const int n_atoms = pA->geo->n_atoms;
+    cq_status st;
+    // main pieces per (atom group, K atom) for 9-orbital atoms, tail pieces per (atom
+    // group, tail group)
+    if (pC->geo->uniform_nb == 9 &&
+        ((st = piece_list<true>(ctx, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA,
+                                gr->rank_of.as<int32_t>(), n_atoms, 1,
+                                gr->rank_atoms.as<int32_t>(), ps->am)) != CQ_OK ||
+         (st = piece_list<false>(ctx, gr->n_h, gr->gj, gr->h_atoms.as<int32_t>(), pB,
+                                 gr->rank_of.as<int32_t>(), n_atoms, 1,
+                                 gr->rank_atoms.as<int32_t>(), ps->bm)) != CQ_OK))
+        return st;
+    if ((st = piece_list<true>(ctx, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA,
+                               gr->tg_of.as<int32_t>(), gr->n_tau, gr->tg,
+                               gr->tg_atoms.as<int32_t>(), ps->at)) != CQ_OK ||
+        (st = piece_list<false>(ctx, gr->n_h, gr->gj, gr->h_atoms.as<int32_t>(), pB,
+                                gr->tg_of.as<int32_t>(), gr->n_tau, gr->tg,
+                                gr->tg_atoms.as<int32_t>(), ps->bt)) != CQ_OK)
+        return st;
+    if ((st = cq_alloc(ctx, ps->zero, E_AMAIN)) != CQ_OK) return st;
+    cudaMemsetAsync(ps->zero.ptr, 0, E_AMAIN, ctx->stream);
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "pieces")) != CQ_OK) return st;
+    *out = ps;
+    ctx->aux[key] = ps;
+    return CQ_OK;
+}
+
+// The plan of a product of kind SPLIT_KIND or EMU_KIND; a_main_b / a_tail_b are the bytes of
+// one A main / tail piece of that kind (batch sizing).
+constexpr int SPLIT_KIND = 3, EMU_KIND = 4;
+
+cq_status get_piece_plan(cq_ctx *ctx, int kind, const cq_pattern *pA, const cq_pattern *pB,
                          const cq_pattern *pC, const Groups *gr, PiecePlan **out)
 {
-    auto key = std::make_tuple(3, pA->id, pB->id, pC->id);
+    auto key = std::make_tuple(kind, pA->id, pB->id, pC->id);
     auto it = ctx->aux.find(key);
     if (it != ctx->aux.end()) {
         *out = static_cast<PiecePlan *>(it->second.get());
@@ -1051,44 +893,27 @@ cq_status get_piece_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB
     }
     cudaStream_t s = ctx->stream;
     auto pl = std::make_shared<PiecePlan>();
-    const bool mains = pC->geo->uniform_nb == 9;
+    const bool mains = pC->geo->uniform_nb == 9, emu = kind == EMU_KIND;
+    const int64_t a_main_b = emu ? E_AMAIN : A_MAIN, a_tail_b = emu ? E_ATAIL : A_TAIL;
     const int n_atoms = pA->geo->n_atoms;
     cq_status st;
-    // piece lists: main pieces per (atom group, K atom), tail pieces per (atom group, tail group)
-    if (mains &&
-        ((st = piece_list<true>(ctx, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA,
-                                gr->rank_of.as<int32_t>(), n_atoms, 1,
-                                gr->rank_atoms.as<int32_t>(), pl->am)) != CQ_OK ||
-         (st = piece_list<false>(ctx, gr->n_h, gr->gj, gr->h_atoms.as<int32_t>(), pB,
-                                 gr->rank_of.as<int32_t>(), n_atoms, 1,
-                                 gr->rank_atoms.as<int32_t>(), pl->bm)) != CQ_OK))
-        return st;
-    if ((st = piece_list<true>(ctx, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA,
-                               gr->tg_of.as<int32_t>(), gr->n_tau, gr->tg,
-                               gr->tg_atoms.as<int32_t>(), pl->at)) != CQ_OK ||
-        (st = piece_list<false>(ctx, gr->n_h, gr->gj, gr->h_atoms.as<int32_t>(), pB,
-                                gr->tg_of.as<int32_t>(), gr->n_tau, gr->tg,
-                                gr->tg_atoms.as<int32_t>(), pl->bt)) != CQ_OK)
-        return st;
-    if ((st = cq_alloc(ctx, pl->zero, A_MAIN)) != CQ_OK) return st;
-    cudaMemsetAsync(pl->zero.ptr, 0, A_MAIN, s);
+    if ((st = get_pieces(ctx, pA, pB, pC, gr, &pl->ps)) != CQ_OK) return st;
+    const PieceSet &ps = *pl->ps;
     std::vector<int2> tiles;
     if ((st = tile_list(ctx, pC, gr, tiles)) != CQ_OK) return st;
     pl->n_tiles = (int)tiles.size();
     if (tiles.empty()) {
-        if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "split plan")) != CQ_OK) return st;
         *out = pl.get();
         ctx->aux[key] = pl;
         return CQ_OK;
     }
-    // bytes of the A pieces of M groups [g0, g1]
-    auto nm_of = [&](int g) { return mains ? pl->am.ptr_host[g] : (int64_t)0; };
-    auto a_bytes = [&](int g0, int g1) {
-        return (nm_of(g1 + 1) - nm_of(g0)) * (int64_t)A_MAIN +
-               (pl->at.ptr_host[g1 + 1] - pl->at.ptr_host[g0]) * (int64_t)A_TAIL;
-    };
-    // batches of whole M groups (tiles are sorted by g) whose A pieces fit A_PANEL_CAP
+    // batches of whole M groups (tiles are sorted by g) whose A pieces fit A_PIECE_CAP
     {
+        auto nm_of = [&](int g) { return mains ? ps.am.ptr_host[g] : (int64_t)0; };
+        auto a_bytes = [&](int g0, int g1) {  // A pieces of M groups [g0, g1]
+            return (nm_of(g1 + 1) - nm_of(g0)) * a_main_b +
+                   (ps.at.ptr_host[g1 + 1] - ps.at.ptr_host[g0]) * a_tail_b;
+        };
         int t0 = 0;
         while (t0 < pl->n_tiles) {
             const int g0 = tiles[t0].x;
@@ -1096,19 +921,19 @@ cq_status get_piece_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB
             while (t1 < pl->n_tiles) {
                 const int g = tiles[t1].x;
                 if (g != g1) {  // the next M group starts; keep it only if its pieces still fit
-                    if (a_bytes(g0, g) > (int64_t)A_PANEL_CAP) break;
+                    if (a_bytes(g0, g) > (int64_t)A_PIECE_CAP) break;
                     g1 = g;
                 }
                 ++t1;
             }
-            pl->batches.push_back({t0, t1, nm_of(g0), nm_of(g1 + 1), pl->at.ptr_host[g0],
-                                   pl->at.ptr_host[g1 + 1]});
+            pl->batches.push_back({t0, t1, nm_of(g0), nm_of(g1 + 1), ps.at.ptr_host[g0],
+                                   ps.at.ptr_host[g1 + 1]});
             t0 = t1;
         }
     }
     if ((st = upload(ctx, pl->tiles, tiles.data(), sizeof(int2) * tiles.size())) != CQ_OK) return st;
     // K atoms and tail groups of every tile (temporaries), then the K-step table
-    DevBuf ka_start, tile_rank, kt_start, tile_tau;
+    DevBuf ka_start, tile_rank, kt_start, tile_tau, cnt;
     std::vector<int64_t> ka, kt;
     if (mains) {
         if ((st = tile_keys(ctx, pl->tiles, pl->n_tiles, gr, pA, pB, gr->rank_of.as<int32_t>(),
@@ -1124,14 +949,28 @@ cq_status get_piece_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB
                         gr->n_tau, kt_start, tile_tau, kt)) != CQ_OK)
         return st;
     std::vector<int64_t> step_start((size_t)pl->n_tiles + 1, 0);
-    std::vector<int32_t> nmain((size_t)pl->n_tiles);
-    for (int b = 0; b < pl->n_tiles; ++b) {
-        const int64_t nm = (ka[b + 1] - ka[b] + 1) / 2, nt = kt[b + 1] - kt[b];
-        nmain[b] = (int32_t)nm;
-        step_start[b + 1] = step_start[b] + nm + nt;
+    std::vector<int32_t> nmain((size_t)pl->n_tiles, 0);
+    if (!emu) {
+        for (int b = 0; b < pl->n_tiles; ++b) {
+            const int64_t nm = (ka[b + 1] - ka[b] + 1) / 2, nt = kt[b + 1] - kt[b];
+            nmain[b] = (int32_t)nm;
+            step_start[b + 1] = step_start[b] + nm + nt;
+        }
+    } else {  // per tail group: its atoms' pairs, then its tail step
+        if ((st = cq_alloc(ctx, cnt, 8 * ((size_t)pl->n_tiles + 1))) != CQ_OK) return st;
+        k_emu_steps<false><<<(pl->n_tiles + 127) / 128, 128, 0, s>>>(
+            pl->n_tiles, gr->tg, pl->tiles.as<int2>(), ka_start.as<int64_t>(),
+            tile_rank.as<int32_t>(), kt_start.as<int64_t>(), tile_tau.as<int32_t>(), nullptr,
+            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+            cnt.as<int64_t>(), nullptr, nullptr);
+        cq_count_launch();
+        std::vector<int64_t> c((size_t)pl->n_tiles);
+        cudaMemcpyAsync(c.data(), cnt.ptr, 8 * c.size(), cudaMemcpyDeviceToHost, s);
+        if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "emu steps")) != CQ_OK) return st;
+        for (int b = 0; b < pl->n_tiles; ++b) step_start[b + 1] = step_start[b] + c[b];
     }
     pl->n_steps = step_start[pl->n_tiles];
-    pl->mma_flops = (double)pl->n_steps * 6.0 * 2.0 * MT * NT * 16;
+    pl->mma_flops = (double)pl->n_steps * (emu ? E_MMAS : 6) * 2.0 * MT * NT * 16;
     for (const PieceBatch &bt : pl->batches)
         pl->batch_steps.push_back(step_start[bt.tile1] - step_start[bt.tile0]);
     if ((st = upload(ctx, pl->kstart, step_start.data(), 8 * step_start.size())) != CQ_OK ||
@@ -1139,20 +978,31 @@ cq_status get_piece_plan(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB
         (st = cq_alloc(ctx, pl->steps, sizeof(int4) * (size_t)(pl->n_steps + 1))) != CQ_OK ||
         (st = cq_alloc(ctx, pl->cidx, 4 * ((size_t)pl->n_tiles * gr->gi * gr->gj + 1))) != CQ_OK)
         return st;
-    k_tile_steps<<<pl->n_tiles, 256, 0, s>>>(
-        pl->tiles.as<int2>(), ka_start.as<int64_t>(), tile_rank.as<int32_t>(),
-        kt_start.as<int64_t>(), tile_tau.as<int32_t>(), pl->kstart.as<int64_t>(),
-        pl->am.ptr.as<int64_t>(), pl->am.key.as<int32_t>(), pl->bm.ptr.as<int64_t>(),
-        pl->bm.key.as<int32_t>(), pl->at.ptr.as<int64_t>(), pl->at.key.as<int32_t>(),
-        pl->bt.ptr.as<int64_t>(), pl->bt.key.as<int32_t>(), pl->steps.as<int4>());
+    if (!emu) {
+        k_tile_steps<<<pl->n_tiles, 256, 0, s>>>(
+            pl->tiles.as<int2>(), ka_start.as<int64_t>(), tile_rank.as<int32_t>(),
+            kt_start.as<int64_t>(), tile_tau.as<int32_t>(), pl->kstart.as<int64_t>(),
+            ps.am.ptr.as<int64_t>(), ps.am.key.as<int32_t>(), ps.bm.ptr.as<int64_t>(),
+            ps.bm.key.as<int32_t>(), ps.at.ptr.as<int64_t>(), ps.at.key.as<int32_t>(),
+            ps.bt.ptr.as<int64_t>(), ps.bt.key.as<int32_t>(), pl->steps.as<int4>());
+    } else {
+        if ((st = cq_alloc(ctx, pl->meta, (size_t)pl->n_steps + 16)) != CQ_OK) return st;
+        k_emu_steps<true><<<(pl->n_tiles + 127) / 128, 128, 0, s>>>(
+            pl->n_tiles, gr->tg, pl->tiles.as<int2>(), ka_start.as<int64_t>(),
+            tile_rank.as<int32_t>(), kt_start.as<int64_t>(), tile_tau.as<int32_t>(),
+            ps.am.ptr.as<int64_t>(), ps.am.key.as<int32_t>(), ps.bm.ptr.as<int64_t>(),
+            ps.bm.key.as<int32_t>(), ps.at.ptr.as<int64_t>(), ps.at.key.as<int32_t>(),
+            ps.bt.ptr.as<int64_t>(), ps.bt.key.as<int32_t>(), pl->kstart.as<int64_t>(), nullptr,
+            pl->steps.as<int4>(), pl->meta.as<uint8_t>());
+    }
     k_tile_cidx<<<pl->n_tiles, 256, 0, s>>>(
         pl->tiles.as<int2>(), gr->gi, gr->gj, gr->g_atoms.as<int32_t>(),
         gr->h_atoms.as<int32_t>(), pC->row_ptr.as<int64_t>(), pC->col.as<int32_t>(),
         pl->cidx.as<int32_t>());
     cq_count_launch(2);
-    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "split plan")) != CQ_OK) return st;
+    if ((st = cq_check_cuda(ctx, cudaGetLastError(), "piece plan")) != CQ_OK) return st;
     // the temporaries are freed on return: let the kernels that read them finish
-    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "split plan")) != CQ_OK) return st;
+    if ((st = cq_check_cuda(ctx, cudaStreamSynchronize(s), "piece plan")) != CQ_OK) return st;
     *out = pl.get();
     ctx->aux[key] = pl;
     return CQ_OK;
@@ -1164,6 +1014,7 @@ cq_status run_split(cq_ctx *ctx, const PiecePlan *pl, const Groups *gr, double a
                     const double *B, double beta, const cq_pattern *pC, double *C, double flops)
 {
     cudaStream_t s = ctx->stream;
+    const PieceSet &ps = *pl->ps;
     cq_status st;
     size_t am_bytes = 0, at_bytes = 0;
     for (const PieceBatch &b : pl->batches) {
@@ -1174,8 +1025,8 @@ cq_status run_split(cq_ctx *ctx, const PiecePlan *pl, const Groups *gr, double a
     void *vam, *vat, *vbm, *vbt;
     if ((st = cq_scratch(ctx, "split_Am", am_bytes + A_TAIL, &vam)) != CQ_OK ||
         (st = cq_scratch(ctx, "split_At", at_bytes + A_TAIL, &vat)) != CQ_OK ||
-        (st = cq_scratch(ctx, "split_Bm", (size_t)pl->bm.n() * B_MAIN + A_TAIL, &vbm)) != CQ_OK ||
-        (st = cq_scratch(ctx, "split_Bt", (size_t)pl->bt.n() * B_TAIL + A_TAIL, &vbt)) != CQ_OK)
+        (st = cq_scratch(ctx, "split_Bm", (size_t)ps.bm.n() * B_MAIN + A_TAIL, &vbm)) != CQ_OK ||
+        (st = cq_scratch(ctx, "split_Bt", (size_t)ps.bt.n() * B_TAIL + A_TAIL, &vbt)) != CQ_OK)
         return st;
     // the shared-memory limit is a per-device attribute: set it once per device, on the
     // first split product there (which runs eagerly: building its plan synchronises)
@@ -1194,26 +1045,26 @@ cq_status run_split(cq_ctx *ctx, const PiecePlan *pl, const Groups *gr, double a
         attr_set[dev] = true;
     }
     auto blocks = [](int64_t n, int rows) { return (unsigned)((n * rows + 255) / 256); };
-    if (pl->bm.n() > 0) {
-        k_pack_main<NB, false><<<blocks(pl->bm.n(), NT), 256, 0, s>>>(
-            0, pl->bm.n(), pl->bm.index.as<int32_t>(), B, pB->uniform, (uint8_t *)vbm);
+    if (ps.bm.n() > 0) {
+        k_pack_main<NB, false><<<blocks(ps.bm.n(), NT), 256, 0, s>>>(
+            0, ps.bm.n(), ps.bm.index.as<int32_t>(), B, pB->uniform, (uint8_t *)vbm);
         cq_count_launch();
     }
-    if (pl->bt.n() > 0) {
-        k_pack_tail<NB, false><<<blocks(pl->bt.n(), NT), 256, 0, s>>>(
-            0, pl->bt.n(), pl->bt.index.as<int32_t>(), B, pB->uniform, (uint8_t *)vbt);
+    if (ps.bt.n() > 0) {
+        k_pack_tail<NB, false><<<blocks(ps.bt.n(), NT), 256, 0, s>>>(
+            0, ps.bt.n(), ps.bt.index.as<int32_t>(), B, pB->uniform, (uint8_t *)vbt);
         cq_count_launch();
     }
     for (size_t q = 0; q < pl->batches.size(); ++q) {
         const PieceBatch &b = pl->batches[q];
         if (b.am1 > b.am0) {
             k_pack_main<NB, true><<<blocks(b.am1 - b.am0, MT), 256, 0, s>>>(
-                b.am0, b.am1 - b.am0, pl->am.index.as<int32_t>(), A, pA->uniform, (uint8_t *)vam);
+                b.am0, b.am1 - b.am0, ps.am.index.as<int32_t>(), A, pA->uniform, (uint8_t *)vam);
             cq_count_launch();
         }
         if (b.at1 > b.at0) {
             k_pack_tail<NB, true><<<blocks(b.at1 - b.at0, MT), 256, 0, s>>>(
-                b.at0, b.at1 - b.at0, pl->at.index.as<int32_t>(), A, pA->uniform, (uint8_t *)vat);
+                b.at0, b.at1 - b.at0, ps.at.index.as<int32_t>(), A, pA->uniform, (uint8_t *)vat);
             cq_count_launch();
         }
         SplitArgs a;
@@ -1228,7 +1079,7 @@ cq_status run_split(cq_ctx *ctx, const PiecePlan *pl, const Groups *gr, double a
         a.at0 = b.at0;
         a.b_main = (const uint8_t *)vbm;
         a.b_tail = (const uint8_t *)vbt;
-        a.zero = pl->zero.as<uint8_t>();
+        a.zero = ps.zero.as<uint8_t>();
         a.C = C;
         a.c_stride = pC->uniform;
         a.alpha = alpha;
@@ -1249,21 +1100,43 @@ cq_status run_split(cq_ctx *ctx, const PiecePlan *pl, const Groups *gr, double a
 }
 
 template <int NB>
-cq_status run_emu(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double alpha,
+cq_status run_emu(cq_ctx *ctx, PiecePlan *pl, const Groups *gr, double alpha,
                   const cq_pattern *pA, const double *A, const cq_pattern *pB, const double *B,
                   double beta, const cq_pattern *pC, double *C, double flops)
 {
     cudaStream_t s = ctx->stream;
+    PieceSet &ps = *pl->ps;
     cq_status st;
-    size_t a_bytes = 0;
-    for (const Batch &b : pl->batches) a_bytes = std::max(a_bytes, (size_t)(b.e1 - b.e0) * E_APANEL);
-    void *va, *vb, *ra, *sa, *rb, *sb;
-    if ((st = cq_scratch(ctx, "emu_A", a_bytes, &va)) != CQ_OK ||
-        (st = cq_scratch(ctx, "emu_B", (size_t)pl->n_hb * E_BPANEL, &vb)) != CQ_OK ||
-        (st = cq_scratch(ctx, "emu_ra", 2 * (size_t)pl->n_ga * MT + 2, &ra)) != CQ_OK ||
-        (st = cq_scratch(ctx, "emu_sa", 2 * (size_t)pl->n_ga * MT + 2, &sa)) != CQ_OK ||
-        (st = cq_scratch(ctx, "emu_rb", 2 * (size_t)pl->n_hb * NT + 2, &rb)) != CQ_OK ||
-        (st = cq_scratch(ctx, "emu_sb", 2 * (size_t)pl->n_hb * NT + 2, &sb)) != CQ_OK)
+    auto blocks = [](int64_t n, int rows) { return (unsigned)((n * rows + 255) / 256); };
+    // tail entry of every main entry (once per piece set)
+    if (ps.am.n() > 0 && !ps.am_tail.ptr) {
+        if ((st = cq_alloc(ctx, ps.am_tail, 4 * (size_t)ps.am.n())) != CQ_OK ||
+            (st = cq_alloc(ctx, ps.bm_tail, 4 * (size_t)ps.bm.n() + 4)) != CQ_OK)
+            return st;
+        k_emu_main_tail<<<blocks(ps.am.n(), 1), 256, 0, s>>>(
+            ps.am.n(), gr->tg, ps.am.group.as<int32_t>(), ps.am.key.as<int32_t>(),
+            ps.at.ptr.as<int64_t>(), ps.at.key.as<int32_t>(), ps.am_tail.as<int32_t>());
+        cq_count_launch();
+        if (ps.bm.n() > 0) {
+            k_emu_main_tail<<<blocks(ps.bm.n(), 1), 256, 0, s>>>(
+                ps.bm.n(), gr->tg, ps.bm.group.as<int32_t>(), ps.bm.key.as<int32_t>(),
+                ps.bt.ptr.as<int64_t>(), ps.bt.key.as<int32_t>(), ps.bm_tail.as<int32_t>());
+            cq_count_launch();
+        }
+    }
+    size_t am_bytes = 0, at_bytes = 0;
+    for (const PieceBatch &b : pl->batches) {
+        am_bytes = std::max(am_bytes, (size_t)(b.am1 - b.am0) * E_AMAIN);
+        at_bytes = std::max(at_bytes, (size_t)(b.at1 - b.at0) * E_ATAIL);
+    }
+    // one spare piece of room at the end of each piece array
+    void *vam, *vat, *vbm, *vbt, *sa, *sb;
+    if ((st = cq_scratch(ctx, "emu_Am", am_bytes + E_ATAIL, &vam)) != CQ_OK ||
+        (st = cq_scratch(ctx, "emu_At", at_bytes + E_ATAIL, &vat)) != CQ_OK ||
+        (st = cq_scratch(ctx, "emu_Bm", (size_t)ps.bm.n() * E_BMAIN + E_ATAIL, &vbm)) != CQ_OK ||
+        (st = cq_scratch(ctx, "emu_Bt", (size_t)ps.bt.n() * E_BTAIL + E_ATAIL, &vbt)) != CQ_OK ||
+        (st = cq_scratch(ctx, "emu_sa", 2 * (size_t)ps.at.n() * MT + 16, &sa)) != CQ_OK ||
+        (st = cq_scratch(ctx, "emu_sb", 2 * (size_t)ps.bt.n() * NT + 16, &sb)) != CQ_OK)
         return st;
     // the shared-memory limit is a per-device attribute: set it once per device
     static bool attr_set[64] = {};
@@ -1280,44 +1153,54 @@ cq_status run_emu(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double alp
             return st;
         attr_set[dev] = true;
     }
-    // group exponents and digit planes of B, then of A (all entries: a scale group's
-    // entries may fall in different packing batches)
-    if (pl->n_hb > 0) {
-        k_emu_rowexp_b<NB><<<(unsigned)pl->n_hb, NT, 0, s>>>(pl->hb_index.as<int32_t>(), B,
-                                                              pB->uniform, (int16_t *)rb);
-        k_emu_group_scale<<<(unsigned)pl->n_hb, NT, 0, s>>>(
-            NT, pl->hb_ptr.as<int64_t>(), pl->hb_kappa.as<int32_t>(), pl->hb_group.as<int32_t>(),
-            (const int16_t *)rb, (int16_t *)sb);
-        k_pack_b_emu<NB><<<(unsigned)pl->n_hb, 256, 0, s>>>(
-            pl->hb_index.as<int32_t>(), (const int16_t *)sb, B, pB->uniform, (uint8_t *)vb);
-        cq_count_launch(3);
-    }
-    if (pl->n_ga > 0) {
-        k_emu_rowexp_a<NB><<<(unsigned)pl->n_ga, MT, 0, s>>>(pl->ga_index.as<int32_t>(), A,
-                                                              pA->uniform, (int16_t *)ra);
-        k_emu_group_scale<<<(unsigned)pl->n_ga, MT, 0, s>>>(
-            MT, pl->ga_ptr.as<int64_t>(), pl->ga_kappa.as<int32_t>(), pl->ga_group.as<int32_t>(),
-            (const int16_t *)ra, (int16_t *)sa);
+    // group exponents (every tail entry: the groups of one M group may fall in different
+    // packing batches), then the digit planes of B and of each batch of A
+    if (ps.bt.n() > 0) {
+        k_emu_rowexp<NB, false><<<blocks(ps.bt.n(), NT), 256, 0, s>>>(
+            ps.bt.n(), ps.bt.index.as<int32_t>(), B, pB->uniform, (int16_t *)sb);
+        k_pack_tail_emu<NB, false><<<blocks(ps.bt.n(), NT), 256, 0, s>>>(
+            0, ps.bt.n(), ps.bt.index.as<int32_t>(), (const int16_t *)sb, B, pB->uniform,
+            (uint8_t *)vbt);
         cq_count_launch(2);
     }
-    const double mma_flops = (double)pl->n_chunks * KSTEPS * E_MMAS * 2.0 * MT * NT * 16;
+    if (ps.bm.n() > 0) {
+        k_pack_main_emu<NB, false><<<blocks(ps.bm.n(), NT), 256, 0, s>>>(
+            0, ps.bm.n(), ps.bm.index.as<int32_t>(), ps.bm_tail.as<int32_t>(),
+            (const int16_t *)sb, B, pB->uniform, (uint8_t *)vbm);
+        cq_count_launch();
+    }
+    if (ps.at.n() > 0) {
+        k_emu_rowexp<NB, true><<<blocks(ps.at.n(), MT), 256, 0, s>>>(
+            ps.at.n(), ps.at.index.as<int32_t>(), A, pA->uniform, (int16_t *)sa);
+        cq_count_launch();
+    }
     for (size_t q = 0; q < pl->batches.size(); ++q) {
-        const Batch &b = pl->batches[q];
-        if (b.e1 > b.e0) {
-            k_pack_a_emu<NB><<<(unsigned)(b.e1 - b.e0), 256, 0, s>>>(
-                b.e0, pl->ga_index.as<int32_t>(), (const int16_t *)sa, A, pA->uniform,
-                (uint8_t *)va);
+        const PieceBatch &b = pl->batches[q];
+        if (b.am1 > b.am0) {
+            k_pack_main_emu<NB, true><<<blocks(b.am1 - b.am0, MT), 256, 0, s>>>(
+                b.am0, b.am1 - b.am0, ps.am.index.as<int32_t>(), ps.am_tail.as<int32_t>(),
+                (const int16_t *)sa, A, pA->uniform, (uint8_t *)vam);
+            cq_count_launch();
+        }
+        if (b.at1 > b.at0) {
+            k_pack_tail_emu<NB, true><<<blocks(b.at1 - b.at0, MT), 256, 0, s>>>(
+                b.at0, b.at1 - b.at0, ps.at.index.as<int32_t>(), (const int16_t *)sa, A,
+                pA->uniform, (uint8_t *)vat);
             cq_count_launch();
         }
         EmuArgs a;
         a.n_tiles = b.tile1 - b.tile0;
         a.kstart = pl->kstart.as<int64_t>() + b.tile0;
-        a.chunks = pl->chunks.as<int2>();
+        a.steps = pl->steps.as<int4>();
         a.meta = pl->meta.as<uint8_t>();
         a.cidx = pl->cidx.as<int32_t>() + (int64_t)b.tile0 * gr->gi * gr->gj;
-        a.panel_a = (const uint8_t *)va;
-        a.ea0 = b.e0;
-        a.panel_b = (const uint8_t *)vb;
+        a.a_main = (const uint8_t *)vam;
+        a.am0 = b.am0;
+        a.a_tail = (const uint8_t *)vat;
+        a.at0 = b.at0;
+        a.b_main = (const uint8_t *)vbm;
+        a.b_tail = (const uint8_t *)vbt;
+        a.zero = ps.zero.as<uint8_t>();
         a.scale_a = (const int16_t *)sa;
         a.scale_b = (const int16_t *)sb;
         a.C = C;
@@ -1326,9 +1209,9 @@ cq_status run_emu(cq_ctx *ctx, const SplitPlan *pl, const Groups *gr, double alp
         a.beta = beta;
         a.flag = ctx->flag.as<int32_t>();
         const double share =
-            pl->n_chunks > 0 ? (double)pl->batch_chunks[q] / (double)pl->n_chunks : 0.0;
+            pl->n_steps > 0 ? (double)pl->batch_steps[q] / (double)pl->n_steps : 0.0;
         const int grid = std::min(a.n_tiles, ctx->num_sms);
-        cq_timing_begin(ctx, flops * share, mma_flops * share);
+        cq_timing_begin(ctx, flops * share, pl->mma_flops * share);
         k_bsmm_emu<NB><<<grid, ST, SMEM_E, s>>>(a);
         cq_timing_end(ctx);
         cq_count_launch();
@@ -1349,18 +1232,11 @@ cq_status cq_bsmm_emu(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_pa
                        "emulated-FP64 product: needs a uniform basis of 4 or 9 orbitals per atom");
     if (pC->n_blocks == 0) return CQ_OK;
     Groups *gr;
-    SplitPlan *pl;
+    PiecePlan *pl;
     cq_status st = get_groups(ctx, pC, &gr);
     if (st != CQ_OK) return st;
-    if ((st = get_plan(ctx, pA, pB, pC, gr, &pl)) != CQ_OK) return st;
+    if ((st = get_piece_plan(ctx, EMU_KIND, pA, pB, pC, gr, &pl)) != CQ_OK) return st;
     if (pl->n_tiles == 0) return CQ_OK;
-    if (!pl->meta.ptr) {  // scale-period flags, built once per pattern triple
-        if ((st = cq_alloc(ctx, pl->meta, (size_t)pl->n_chunks + 16)) != CQ_OK) return st;
-        k_emu_periods<<<pl->n_tiles, 256, 0, ctx->stream>>>(
-            pl->kstart.as<int64_t>(), pl->tile_kappa.as<int32_t>(), pl->meta.as<uint8_t>());
-        cq_count_launch();
-        if ((st = cq_check_cuda(ctx, cudaGetLastError(), "emu periods")) != CQ_OK) return st;
-    }
     return nb == 9 ? run_emu<9>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops)
                    : run_emu<4>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops);
 }
@@ -1378,7 +1254,7 @@ cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_
     PiecePlan *pl;
     cq_status st = get_groups(ctx, pC, &gr);
     if (st != CQ_OK) return st;
-    if ((st = get_piece_plan(ctx, pA, pB, pC, gr, &pl)) != CQ_OK) return st;
+    if ((st = get_piece_plan(ctx, SPLIT_KIND, pA, pB, pC, gr, &pl)) != CQ_OK) return st;
     if (pl->n_tiles == 0) return CQ_OK;
     return nb == 9 ? run_split<9>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops)
                    : run_split<4>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops);
