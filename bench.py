@@ -39,6 +39,11 @@ BF16_FALLBACK_TFLOPS = 1900.0
 # 4096-atom cell, from one ncu capture of the current kernel
 # (profiles/bsmm_f64_traffic_si4096.md)
 FP64_TRAFFIC_PER_LAUNCH = 90.66e9
+# The same for the split-BF16 and the emulated-FP64 tile kernels (one ncu pass over one LNV
+# step of each leg; profiles/bsmm_split_ncu_si1728.md, profiles/bsmm_emu_ncu_si1728.md)
+SPLIT_TRAFFIC_PER_LAUNCH = 157.85e9
+EMU_TRAFFIC_PER_LAUNCH = 374.46e9
+TRAFFIC_SOURCE = "ncu dram bytes per launch, one LNV step of this cell"
 
 
 METRIC = ("block-sparse GEMM GFLOP/s (useful FP64 flops) & s per LNV step, Si SZP; "
@@ -124,6 +129,13 @@ def parse():
     ap.add_argument("--converge", action="store_true",
                     help="time full minimisations (plain FP64 vs learned guess + split-BF16 + "
                          "FP64 refinement) instead of the step benchmark")
+    ap.add_argument("--products", default=None,
+                    help="comma-separated product types of an LNV step to time one by one on "
+                         "the cell with seeded random operands instead of the step benchmark: "
+                         "X (L.S -> P_X), U (S.X -> P_U), R (U.X -> P_L); one untimed product, "
+                         "then --steps timed ones (for kernel profiling)")
+    ap.add_argument("--prec", default="split", choices=["fp64", "split", "emu"],
+                    help="with --products: the product's precision")
     return ap.parse_args()
 
 
@@ -182,12 +194,13 @@ def run_batch(args, dev, rep):
     steps = 2
 
     def timed_steps(graphs):
-        """`steps` timed steps from the PM start, after two untimed ones (eager once, then
-        captured when graphs are on)."""
+        """`steps` timed steps from the PM start, after four untimed ones (a graph phase runs
+        eagerly on its first use and is captured on its second, so the untimed steps let the
+        phases the timed steps use be captured first)."""
         L.copy_(L_start)
         ctx.set_graphs(graphs)
         lnv = ctx.lnv_cells(pS, S, H, pL, L, [2 * x for x in n_occ])
-        for _ in range(2):
+        for _ in range(4):
             lnv.step()
         n0 = cq.kernel_launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -569,7 +582,8 @@ def run_cq(args, rank, world, local_rank):
                               "useful_tflops": kern_flops / (kern_ms * 1e-3) / 1e12 if kern_ms else None,
                               "launches": n_launch, "kernel_ms": kern_ms,
                               "kernel_share": kern_ms / r["ms"] if r["ms"] else None,
-                              "traffic": None},
+                              "traffic": SPLIT_TRAFFIC_PER_LAUNCH if cell.n_atoms == 4096 else None,
+                              "traffic_source": TRAFFIC_SOURCE},
                  "clocks": r["clk"], "gpu_launches": int(r["launches"]),
                  "lnv": [{k: x[k] for k in ("energy", "n_elec", "gnorm", "n_corr")}
                          for x in r["reps"]]}
@@ -607,7 +621,8 @@ def run_cq(args, rank, world, local_rank):
                             "useful_tflops": kern_flops / (kern_ms * 1e-3) / 1e12 if kern_ms else None,
                             "launches": n_launch, "kernel_ms": kern_ms,
                             "kernel_share": kern_ms / r["ms"] if r["ms"] else None,
-                            "traffic": None},
+                            "traffic": EMU_TRAFFIC_PER_LAUNCH if cell.n_atoms == 4096 else None,
+                            "traffic_source": TRAFFIC_SOURCE},
                "clocks": r["clk"], "gpu_launches": int(r["launches"])}
         emu["roofline"]["frac"] = (emu["roofline"]["achieved"] / emu["roofline"]["peak"]
                                    if emu["roofline"]["achieved"] else None)
@@ -657,7 +672,7 @@ def run_cq(args, rank, world, local_rank):
                          "achieved": achieved, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
                          "frac": (achieved / (peak_fp64 / 1e12)) if achieved else None,
                          "traffic": FP64_TRAFFIC_PER_LAUNCH if cell.n_atoms == 4096 else None,
-                         "traffic_source": "ncu dram bytes per launch, one LNV step of this cell",
+                         "traffic_source": TRAFFIC_SOURCE,
                          "peak_source": "in-library FP64 probe (best of FMA and DMMA chains)",
                          "launches": n_launch, "kernel_ms": kern_ms,
                          "kernel_share": kern_ms / ms if ms > 0 else None},
@@ -1045,6 +1060,61 @@ def run_sweep(args, dev):
                       "r_S 14, r_L 16", "rows": rows}), flush=True)
 
 
+PRODUCTS = {"X": ("r_L", "r_S", "r_X"), "U": ("r_S", "r_X", "r_U"), "R": ("r_U", "r_X", "r_L")}
+
+
+def run_products(args, dev):
+    """Kernel time of single block products of the LNV step's three kinds on the Si SZP cell,
+    operands seeded N(0,1) blocks decaying with distance (inputs.random_blocks); only the
+    matrices of the named products are made.  One untimed product per kind (it builds the
+    plan), then --steps timed ones, timed by the library around its product kernels."""
+    import torch
+
+    from paper_2205_08941_gb300 import build as B
+    B.build()
+    from paper_2205_08941_gb300 import cq
+    from paper_2205_08941_gb300 import inputs as I
+    torch.cuda.set_device(dev)
+    prec = {"fp64": cq.CQ_FP64, "split": cq.CQ_SPLIT_BF16X3, "emu": cq.CQ_FP64_EMU}[args.prec]
+    kinds = [k.strip() for k in args.products.split(",") if k.strip()]
+    cell = I.diamond_cell(args.ncell, a=WORKLOAD["a_bohr"], sigma=WORKLOAD["sigma_bohr"],
+                          seed=WORKLOAD["seed"], norb=9)
+    ctx = cq.Context(dev)
+    t = lambda a, dt: torch.tensor(a, dtype=dt, device=f"cuda:{dev}")
+    pos, nb = t(cell.pos, torch.float64), t(cell.nb, torch.int32)
+    radii = sorted({WORKLOAD[r] for k in kinds for r in PRODUCTS[k]})
+    pats = {r: ctx.pattern(pos, cell.box, nb, r) for r in radii}
+    vals = {}
+    for k in kinds:
+        for r in PRODUCTS[k][:2]:
+            rr = WORKLOAD[r]
+            if rr not in vals:
+                pb = I.random_blocks(cell, rr, int(rr), symmetric=False)
+                vals[rr] = ctx.scatter(pats[rr], t(pb.i, torch.int32), t(pb.j, torch.int32),
+                                       t(pb.off, torch.int64), t(pb.values, torch.float64))
+    out = {"mode": "products", "workload": workload_name(cell.n_atoms), "prec": args.prec,
+           "steps": args.steps}
+    for k in kinds:
+        ra, rb, rc = (WORKLOAD[r] for r in PRODUCTS[k])
+        C = ctx.zeros(pats[rc])
+        ctx.bsmm(1.0, pats[ra], vals[ra], pats[rb], vals[rb], 0.0, pats[rc], C, prec=prec)
+        ctx.sync()
+        ctx.set_timing(True)
+        ctx.kernel_stats()
+        for _ in range(args.steps):
+            ctx.bsmm(1.0, pats[ra], vals[ra], pats[rb], vals[rb], 0.0, pats[rc], C, prec=prec)
+        n, ms, fl, mma = ctx.kernel_stats()
+        ctx.set_timing(False)
+        out[k] = {"kernel_ms": ms / args.steps, "launches": n,
+                  "useful_tflops": fl / (ms * 1e-3) / 1e12 if ms else None,
+                  "issued_tflops": mma / (ms * 1e-3) / 1e12 if ms and mma else None}
+        del C
+        if prec != cq.CQ_FP64:
+            ctx.release_cache()  # the next kind's plan and pieces start from free memory
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.sweep:
@@ -1055,6 +1125,9 @@ def main():
         return
     if args.solvers:
         run_solvers(args, int(os.environ.get("LOCAL_RANK", 0)))
+        return
+    if args.products:
+        run_products(args, int(os.environ.get("LOCAL_RANK", 0)))
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -246,7 +246,7 @@ cq_status cq_trace_prod(cq_ctx *ctx, const cq_pattern *pA, const double *A,
  * static description.
  *
  * The first call on a device looks up the array's device address with that device current
- * (cudaGetSymbolAddress); make that first call before any stream capture.  Every call
+ * (cudaGetSymbolAddress, a synchronising runtime call); later calls reuse it.  Every call
  * shares the one array and leaves its contents behind; each call overwrites the rows it
  * reads, but calls that overlap on the GPU (different streams or host threads) race on the
  * array and must be serialised by the caller.
@@ -430,10 +430,18 @@ cq_status cq_guess_set_scale(cq_guess *g, const float *in_mean_host, const float
 cq_status cq_guess_params(cq_guess *g, float *w_host, float *b_host, int64_t *n_w,
                           int64_t *n_b, int32_t set);
 /* One Adam step on a minibatch of rows samples (raw targets; lr = 0: loss and gradients
- * only).  Optional host outputs: mean-square loss of the normalised targets, gradients. */
+ * only).  Optional host outputs: mean-square loss of the normalised targets, gradients; the
+ * call synchronises only when it fills one of them (else it is asynchronous on the context
+ * stream).  Every step also adds its squared-error sum and its row count to the device-side
+ * running sums that cq_guess_loss_sum reads. */
 cq_status cq_guess_train_step(cq_guess *g, const float *desc_dev, const float *targets_dev,
                               int64_t rows, float lr, float *loss_host, float *grad_w_host,
                               float *grad_b_host);
+/* The running sums of the training steps since the last reset: *sq_sum_host = sum of the
+ * squared errors of the normalised targets (81 per row), *rows_host = rows; synchronises.
+ * reset != 0 sets both to zero after reading.  The mean-square loss over those steps is
+ * sq_sum / (81 rows). */
+cq_status cq_guess_loss_sum(cq_guess *g, double *sq_sum_host, int64_t *rows_host, int32_t reset);
 /* Normalised network outputs (rows x 81). */
 cq_status cq_guess_forward(cq_guess *g, const float *desc_dev, int64_t rows, float *out_dev);
 /* L on pL from the network: every block predicted, rotated back, (j, i) = (i, j)^T. */

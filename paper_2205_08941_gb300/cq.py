@@ -103,6 +103,8 @@ SIGNATURES = {
     "cq_guess_params": (_st, [_vp, _vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _i32]),
     "cq_guess_train_step": (_st, [_vp, _vp, _vp, _i64, ctypes.c_float,
                                   ctypes.POINTER(ctypes.c_float), _vp, _vp]),
+    "cq_guess_loss_sum": (_st, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                ctypes.c_int32]),
     "cq_guess_forward": (_st, [_vp, _vp, _i64, _vp]),
     "cq_guess_apply": (_st, [_vp, _vp, _vp]),
     "cq_ctx_set_test_wait": (_st, [_vp, _i64]),
@@ -506,17 +508,30 @@ class Guess:
         b = np.ascontiguousarray(b, dtype=np.float32)
         self.ctx._check(lib().cq_guess_params(self.h, w.ctypes.data, b.ctypes.data, None, None, 1))
 
-    def train_step(self, desc, targets, lr, grads=False):
+    def train_step(self, desc, targets, lr, grads=False, loss=True):
+        """One Adam step; returns the batch loss (and the gradients with grads=True).  With
+        loss=False and grads=False nothing is read back and the step stays asynchronous."""
         import numpy as np
-        loss = ctypes.c_float()
+        lv = ctypes.c_float()
         gw = gb = None
         if grads:
             w, b = self.params()
             gw, gb = np.zeros_like(w), np.zeros_like(b)
         self.ctx._check(lib().cq_guess_train_step(
-            self.h, _ptr(desc), _ptr(targets), int(desc.shape[0]), float(lr), ctypes.byref(loss),
+            self.h, _ptr(desc), _ptr(targets), int(desc.shape[0]), float(lr),
+            ctypes.byref(lv) if (loss or grads) else None,
             None if gw is None else gw.ctypes.data, None if gb is None else gb.ctypes.data))
-        return (float(loss.value), gw, gb) if grads else float(loss.value)
+        if grads:
+            return float(lv.value), gw, gb
+        return float(lv.value) if loss else None
+
+    def loss_sum(self, reset=True):
+        """(squared-error sum, rows) of the training steps since the last reset."""
+        sq = ctypes.c_double()
+        rows = ctypes.c_int64()
+        self.ctx._check(lib().cq_guess_loss_sum(self.h, ctypes.byref(sq), ctypes.byref(rows),
+                                                1 if reset else 0))
+        return float(sq.value), int(rows.value)
 
     def forward(self, desc):
         out = torch.empty((max(desc.shape[0], 1), self.N_OUT), dtype=torch.float32,

@@ -384,6 +384,23 @@ __global__ void k_mse(int64_t n, const float *Y, const float *T, float *dY, floa
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
+// adds the 256 block partials of k_mse (fixed order) and the batch's row count to the
+// running sums acc[0], acc[1] (one CTA of 256 threads)
+__global__ void k_loss_accum(const float *part, int64_t rows, double *acc)
+{
+    __shared__ double sh[256];
+    sh[threadIdx.x] = (double)part[threadIdx.x];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        acc[0] += sh[0];
+        acc[1] += (double)rows;
+    }
+}
+
 // sum of `parts` partial matrices (deterministic order) + column sums for bias gradients
 __global__ void k_sum_parts(int64_t n, int parts, int64_t stride, const float *src, float *dst)
 {
@@ -477,6 +494,7 @@ struct cq_guess {
     // layer inputs, of dZ and the transposes H^T, dZ^T of the backward pass
     DevBuf wt, actb;
     int64_t actb_rows = 0;
+    DevBuf loss_acc;                  // running squared-error sum and row count (2 doubles)
 };
 
 namespace {
@@ -823,7 +841,13 @@ extern "C" cq_status cq_guess_train_step(cq_guess *g, const float *desc, const f
     k_norm_out<<<blocks_for(rows * NOUT), 256, 0, s>>>(rows * NOUT, targets, g->mean.as<float>(),
                                                       g->scale.as<float>(), (float *)vt);
     k_mse<<<256, 256, 0, s>>>(rows, H[L], (float *)vt, dY, (float *)vloss);
-    cq_count_launch(2);
+    if (!g->loss_acc.ptr) {
+        CQ_TRY(cq_alloc(ctx, g->loss_acc, 2 * sizeof(double)));
+        CQ_TRY(cq_check_cuda(ctx, cudaMemsetAsync(g->loss_acc.ptr, 0, 2 * sizeof(double), s),
+                             "loss sums"));
+    }
+    k_loss_accum<<<1, 256, 0, s>>>((const float *)vloss, rows, g->loss_acc.as<double>());
+    cq_count_launch(3);
     // dY holds dLoss/dZ_L (output layer is linear)
     float *dZ = dY;
     const bool tc = !g->fp32_weights;
@@ -904,7 +928,25 @@ extern "C" cq_status cq_guess_train_step(cq_guess *g, const float *desc, const f
         cudaMemcpyAsync(grad_w_host, g->gw.ptr, 4 * g->n_w, cudaMemcpyDeviceToHost, s);
     if (grad_b_host)
         cudaMemcpyAsync(grad_b_host, g->gb.ptr, 4 * g->n_b, cudaMemcpyDeviceToHost, s);
+    if (!loss_host && !grad_w_host && !grad_b_host)
+        return cq_check_cuda(ctx, cudaGetLastError(), "train step");
     return cq_check_cuda(ctx, cudaStreamSynchronize(s), "train step");
+}
+
+extern "C" cq_status cq_guess_loss_sum(cq_guess *g, double *sq_sum_host, int64_t *rows_host,
+                                       int32_t reset)
+{
+    if (!g) return CQ_ERR_INVALID;
+    cq_ctx *ctx = g->ctx;
+    double v[2] = {0.0, 0.0};
+    if (g->loss_acc.ptr) {
+        cudaMemcpyAsync(v, g->loss_acc.ptr, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream);
+        if (reset) cudaMemsetAsync(g->loss_acc.ptr, 0, sizeof(v), ctx->stream);
+        CQ_TRY(cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "loss sums"));
+    }
+    if (sq_sum_host) *sq_sum_host = v[0];
+    if (rows_host) *rows_host = (int64_t)v[1];
+    return CQ_OK;
 }
 
 // Predict every block of P_L: descriptors -> MLP -> un-normalise -> rotate to the global

@@ -29,17 +29,17 @@ def train(guess: cq.Guess, desc, targets, epochs=40, batch=8192, lr=2e-3, seed=0
     gen.manual_seed(seed)
     hist = []
     rate = lr
+    guess.loss_sum(reset=True)
     for _ in range(epochs):
         perm = torch.randperm(n, device=desc.device, generator=gen)
-        tot, cnt = 0.0, 0
         for s in range(0, n, batch):
             idx = perm[s:s + batch]
             if idx.numel() < 64:
                 continue
-            loss = guess.train_step(desc[idx].contiguous(), targets[idx].contiguous(), rate)
-            tot += loss * idx.numel()
-            cnt += idx.numel()
-        hist.append(tot / max(cnt, 1))
+            # asynchronous: the epoch's loss is read once, from the device-side sums
+            guess.train_step(desc[idx].contiguous(), targets[idx].contiguous(), rate, loss=False)
+        sq, rows = guess.loss_sum(reset=True)
+        hist.append(sq / max(rows * cq.Guess.N_OUT, 1))
         rate *= lr_decay
     return hist
 

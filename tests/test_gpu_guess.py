@@ -105,6 +105,26 @@ def test_network_bf16_mode_within_bf16_tolerance(ctx):
     g.close()
 
 
+def test_loss_sums_of_asynchronous_steps_match_the_step_losses(ctx):
+    """Steps that read nothing back still add their squared-error sums and rows on the
+    device: with lr = 0 (weights fixed) the running sums of three such steps equal the
+    losses the same batches report one by one, and a reset starts them again at zero."""
+    g, X, T, _, _, _ = _net_case(ctx, True)
+    Xg, Tg = torch.tensor(X, device="cuda:0"), torch.tensor(T, device="cuda:0")
+    cuts = [(0, 100), (100, 220), (220, 300)]
+    g.loss_sum(reset=True)
+    want = sum(g.train_step(Xg[a:b].contiguous(), Tg[a:b].contiguous(), 0.0) * (b - a) * 81
+               for a, b in cuts)
+    g.loss_sum(reset=True)
+    for a, b in cuts:
+        assert g.train_step(Xg[a:b].contiguous(), Tg[a:b].contiguous(), 0.0, loss=False) is None
+    sq, rows = g.loss_sum(reset=True)
+    assert rows == 300
+    assert sq == pytest.approx(want, rel=1e-5)
+    assert g.loss_sum(reset=False) == (0.0, 0)
+    g.close()
+
+
 # ---------------------------------------------------------------- training and gain
 
 def _solve(ctx, cell, steps=40, start=None, guess=None, gtol=1e-6):
