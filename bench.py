@@ -11,7 +11,11 @@ S.  Patterns, task lists, the inverse and the start are built before the timed r
 
 The FP64 leg (value, e2e, roofline) times K steps after W warm-up steps; the split leg
 restarts from the same L and times K split-BF16 steps, and reports the energy and L
-differences between the two trajectories.  Prints one JSON line (rank 0).  Under torchrun
+differences between the two trajectories; the emulated-FP64 leg does the same with digit-
+plane products.  The converge leg (N = 1) times the target criterion: seconds until the
+energy stays within 1e-6 Ha/atom of the FP64 solution, plain FP64 LNV from the
+Palser-Manolopoulos start against the learned start with split-BF16 steps and FP64
+refinement.  Prints one JSON line (rank 0).  Under torchrun
 (N > 1) every rank solves its own replica of the cell ("replicas only": the path has no
 exchange step).
 """
@@ -105,6 +109,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-emu", action="store_true",
                     help="skip the emulated-FP64 (digit planes on tensor cores) leg")
+    ap.add_argument("--no-converge", action="store_true",
+                    help="skip the convergence leg (learned start + split-BF16 + FP64 against "
+                         "plain FP64, to within 1e-6 Ha/atom)")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip the split-vs-oracle check on the 512-atom SZP cell")
     ap.add_argument("--sweep", default=None,
@@ -134,6 +141,11 @@ def parse():
                          "the cell with seeded random operands instead of the step benchmark: "
                          "X (L.S -> P_X), U (S.X -> P_U), R (U.X -> P_L); one untimed product, "
                          "then --steps timed ones (for kernel profiling)")
+    ap.add_argument("--batch-c4", action="store_true",
+                    help="the batched workload at its full shape (32 cells of 500-8000 atoms, "
+                         "mixed 5/9/13-orbital species) in sub-batches, split-BF16 LNV steps")
+    ap.add_argument("--c4-atoms", type=int, default=9000,
+                    help="with --batch-c4: atoms per sub-batch at most")
     ap.add_argument("--prec", default="split", choices=["fp64", "split", "emu"],
                     help="with --products: the product's precision")
     return ap.parse_args()
@@ -193,13 +205,13 @@ def run_batch(args, dev, rep):
     L_start = L.clone()
     steps = 2
 
-    def timed_steps(graphs):
+    def timed_steps(graphs, prec=cq.CQ_FP64):
         """`steps` timed steps from the PM start, after four untimed ones (a graph phase runs
         eagerly on its first use and is captured on its second, so the untimed steps let the
         phases the timed steps use be captured first)."""
         L.copy_(L_start)
         ctx.set_graphs(graphs)
-        lnv = ctx.lnv_cells(pS, S, H, pL, L, [2 * x for x in n_occ])
+        lnv = ctx.lnv_cells(pS, S, H, pL, L, [2 * x for x in n_occ], prec=prec)
         for _ in range(4):
             lnv.step()
         n0 = cq.kernel_launches()
@@ -226,8 +238,172 @@ def run_batch(args, dev, rep):
            "energy_per_atom": [r["energy"] / c.n_atoms for r, c in zip(reps[-1], cells)],
            "gnorm": [r["gnorm"] for r in reps[-1]]}
     lnv.close()
+    # the same steps with split-BF16 products on the mixed bases (graphs on)
+    lnv_s, reps_s, ms_s, launches_s = timed_steps(True, cq.CQ_SPLIT_BF16X3)
+    ms_s = rep.max(ms_s)
+    flops_s = rep.sum(sum(r[0]["flops"] for r in reps_s))
+    out["split"] = {"value": flops_s / (ms_s * 1e-3) / 1e9, "unit": "GFLOP/s",
+                    "dtype": "bf16x3 split, fp32 accumulate, fp64 traces",
+                    "ms_per_step": ms_s / steps, "speedup_vs_fp64_step": ms / ms_s,
+                    "gpu_launches": int(launches_s),
+                    "energy_diff_per_atom_vs_fp64": [
+                        abs(a["energy"] - b["energy"]) / c.n_atoms
+                        for a, b, c in zip(reps_s[-1], reps[-1], cells)]}
+    lnv_s.close()
     ctx.close()
     return out
+
+
+def c4_cells(n=32, seed0=3):
+    """The batched workload's cells: cell k from seed seed0 + k -- atoms uniform in
+    [500, 8000] (diamond lattices of 8 nx ny nz atoms near that count), density uniform in
+    0.03-0.06 atoms/A^3, r_L uniform in 12-16 bohr (r_S = r_L - 2), species 5/9/13 per atom."""
+    from paper_2205_08941_gb300 import inputs as I
+    out = []
+    for k in range(n):
+        rng = np.random.default_rng(seed0 + k)
+        target = rng.uniform(500, 8000)
+        dens = rng.uniform(0.03, 0.06)
+        rl = rng.uniform(12.0, 16.0)
+        m = target / 8.0
+        nz = max(1, int(np.floor(m ** (1.0 / 3.0))))
+        ny = max(1, int(round(np.sqrt(m / nz))))
+        nx = max(1, int(round(m / (ny * nz))))
+        out.append((I.mixed_cell((nx, ny, nz), dens, 0.1, seed0 + k), dens, rl))
+    return out
+
+
+def _c4_inputs(k):
+    """Cell k of the batched workload with its S and H pair blocks (host only, no CUDA; run
+    in a spawned worker)."""
+    from paper_2205_08941_gb300 import inputs as I
+    cell, dens, rl = c4_cells()[k]
+    S, H = I.overlap_hamiltonian_species(cell, I.silicon_model(rl - 2.0))
+    return cell, dens, rl, S, H
+
+
+def run_batch_c4(args, dev):
+    """The batched workload at its full shape, split-BF16 LNV steps: the 32 cells of
+    c4_cells in sub-batches of consecutive cells of at most --c4-atoms atoms (one batch of
+    cells fits in HBM; the whole workload would need about 1.5 TB of FP64 matrices); per
+    sub-batch the patterns, a 10-step Hotelling inverse and the PM start (untimed), then two
+    untimed and two timed LNV steps of all its cells, LNV phases replayed as CUDA graphs.
+    The first sub-batch is also timed with FP64 products.  Reports the seconds of one LNV
+    step of all 32 cells (the sum over sub-batches) and the useful GFLOP/s."""
+    import torch
+
+    from paper_2205_08941_gb300 import build as B
+    B.build()
+    from paper_2205_08941_gb300 import cq
+    from paper_2205_08941_gb300 import inputs as I
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    t0 = time.perf_counter()
+    cells = c4_cells()
+    # S and H of the cells built by spawned host workers ahead of the GPU work
+    pool = cf.ProcessPoolExecutor(max_workers=max(1, min(16, (os.cpu_count() or 2) - 1)),
+                                  mp_context=mp.get_context("spawn"))
+    futures = [pool.submit(_c4_inputs, k) for k in range(len(cells))]
+    torch.cuda.set_device(dev)
+    t = lambda a, dt: torch.tensor(a, dtype=dt, device=f"cuda:{dev}")
+    subs, cur, n_cur = [], [], 0
+    for k, c in enumerate(cells):
+        if cur and n_cur + c[0].n_atoms > args.c4_atoms:
+            subs.append(cur)
+            cur, n_cur = [], 0
+        cur.append(k)
+        n_cur += c[0].n_atoms
+    subs.append(cur)
+    rows, t_gen = [], 0.0
+    for q, ks in enumerate(subs):
+        tg = time.perf_counter()
+        got = [futures[k].result() for k in ks]
+        t_gen += time.perf_counter() - tg  # time the GPU waited for inputs
+        sub = [(x[0], x[1], x[2]) for x in got]
+        SH = [(x[3], x[4]) for x in got]
+        del got
+        cl = [c[0] for c in sub]
+        pos, nb, start, boxes = I.concat_cells(cl)
+        stream = torch.cuda.Stream(dev)
+        torch.cuda.synchronize()
+        ctx = cq.Context(dev, stream=stream)
+        pS = ctx.pattern_batch(t(pos, torch.float64), start, boxes, t(nb, torch.int32),
+                               [c[2] - 2.0 for c in sub])
+        pL = ctx.pattern_batch(t(pos, torch.float64), start, boxes, t(nb, torch.int32),
+                               [c[2] for c in sub])
+
+        def up(pairs_list):
+            i = np.concatenate([pb.i + start[k] for k, pb in enumerate(pairs_list)]).astype(np.int32)
+            j = np.concatenate([pb.j + start[k] for k, pb in enumerate(pairs_list)]).astype(np.int32)
+            sizes = np.concatenate([np.diff(pb.off) for pb in pairs_list])
+            off = np.zeros(sizes.shape[0] + 1, dtype=np.int64)
+            np.cumsum(sizes, out=off[1:])
+            v = np.concatenate([pb.values for pb in pairs_list])
+            return ctx.scatter(pS, t(i, torch.int32), t(j, torch.int32), t(off, torch.int64),
+                               t(v, torch.float64))
+
+        S, H = up([x[0] for x in SH]), up([x[1] for x in SH])
+        del SH
+        T = ctx.zeros(pL)
+        ctx.hotelling_init(pS, S, pL, T)
+        for _ in range(10):
+            ctx.hotelling_step(pS, S, pL, T)
+        n_occ = [2.0 * c.n_atoms for c in cl]
+        L = ctx.zeros(pL)
+        ctx.pm_guess_cells(pS, S, H, pL, T, pL, L, n_occ)
+        del T
+        ctx.release_cache()  # the set-up's FP64 task lists: the split steps need none
+        L0 = L.clone()
+        row = {"cells": len(sub), "atoms": int(sum(c.n_atoms for c in cl)),
+               "orbitals": int(sum(int(c.nb.sum()) for c in cl))}
+        precs = [("split", cq.CQ_SPLIT_BF16X3)] + ([("fp64", cq.CQ_FP64)] if q == 0 else [])
+        for name, prec in precs:
+            L.copy_(L0)
+            ctx.set_graphs(True)
+            lnv = ctx.lnv_cells(pS, S, H, pL, L, [2 * x for x in n_occ], prec=prec)
+            for _ in range(2):
+                lnv.step()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream.synchronize()
+            e0.record(stream)
+            reps = [lnv.step() for _ in range(2)]
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / 2
+            flops = sum(r[0]["flops"] for r in reps) / 2
+            row[name] = {"s_per_step": ms / 1e3, "gflops": flops / (ms * 1e-3) / 1e9,
+                         "energy_per_atom": [r["energy"] / c.n_atoms
+                                             for r, c in zip(reps[-1], cl)]}
+            lnv.close()
+            if name == "fp64":
+                ctx.release_cache()
+        ctx.close()
+        del S, H, L, L0, pS, pL
+        torch.cuda.empty_cache()
+        rows.append(row)
+        print(json.dumps({"sub_batch": q, **{k: v for k, v in row.items()
+                                             if k in ("cells", "atoms", "orbitals")},
+                          "split_s_per_step": row["split"]["s_per_step"]}), flush=True)
+    s_all = sum(r["split"]["s_per_step"] for r in rows)
+    f_all = sum(r["split"]["gflops"] * r["split"]["s_per_step"] for r in rows)
+    first = rows[0]
+    print(json.dumps({
+        "mode": "batch_c4",
+        "workload": "32 cells of 500-8000 atoms (seeds 3-34), densities 0.03-0.06 atoms/A^3, "
+                    "r_L 12-16 bohr, species 5/9/13 mixed per atom",
+        "cells": len(cells), "atoms": int(sum(c[0].n_atoms for c in cells)),
+        "sub_batches": len(rows), "sub_batch_atoms_max": args.c4_atoms,
+        "split": {"s_per_step_all_cells": s_all, "gflops": f_all / s_all,
+                  "dtype": "bf16x3 split, fp32 accumulate, fp64 traces", "graphs": True},
+        "first_sub_batch": {"atoms": first["atoms"], "split_s_per_step": first["split"]["s_per_step"],
+                            "fp64_s_per_step": first["fp64"]["s_per_step"],
+                            "speedup": first["fp64"]["s_per_step"] / first["split"]["s_per_step"],
+                            "energy_diff_per_atom_max": max(
+                                abs(a - b) for a, b in zip(first["split"]["energy_per_atom"],
+                                                           first["fp64"]["energy_per_atom"]))},
+        "rows": rows, "input_wait_seconds": t_gen, "seconds": time.perf_counter() - t0}),
+        flush=True)
+    pool.shutdown()
 
 
 def make_inputs(ncell):
@@ -652,6 +828,10 @@ def run_cq(args, rank, world, local_rank):
     if split is not None and rank == 0 and world == 1 and not args.no_oracle_check:
         split["oracle_check"] = split_oracle_check(dev)
 
+    conv = None
+    if rank == 0 and world == 1 and not args.no_converge and not args.only_split:
+        conv = converge_quick(args, dev)
+
     if rank == 0:
         main = res.get("fp64") or res.get("split")
         n_launch, kern_ms, kern_flops, mma_flops = main["stats"]
@@ -688,6 +868,8 @@ def run_cq(args, rank, world, local_rank):
             line["roofline"] = split["roofline"]
         if emu is not None:
             line["fp64_emu"] = emu
+        if conv is not None:
+            line["converge"] = conv
         if split is not None:
             # last, and compact, so that a reader of the line's tail sees the mixed leg
             split.pop("lnv", None)
@@ -701,21 +883,25 @@ def run_cq(args, rank, world, local_rank):
 
 # ---------------------------------------------------------------------- convergence criteria
 
-def run_until(lnv, gtol, cap, trace=None, t0=0.0, fp64=True, stall=None):
+def run_until(lnv, gtol, cap, trace=None, t0=0.0, fp64=True, stall=None, de_tol=None):
     """LNV steps until the RMS gradient is <= gtol (at most cap steps), or, with stall, until
     it has fallen by less than the factor stall over two steps -- split-BF16 gradients stop
-    improving near their rounding floor (about 1e-6 RMS on the 4096-atom cell).  trace gets
-    (seconds since t0, energy, RMS gradient, whether the step's products were FP64) per
-    step.  Returns (steps, last report)."""
+    improving near their rounding floor (about 1e-6 RMS on the 4096-atom cell) -- or, with
+    de_tol, until the energy changes by less than de_tol in one step.  trace gets (seconds
+    since t0, energy, RMS gradient, whether the step's products were FP64) per step.
+    Returns (steps, last report)."""
     it, st = 0, lnv.state()
     hist = [st["gnorm"]]
     while st["gnorm"] > gtol and it < cap:
+        e_prev = st["energy"]
         st = lnv.step()
         it += 1
         hist.append(st["gnorm"])
         if trace is not None:
             trace.append((time.perf_counter() - t0, st["energy"], st["gnorm"], fp64))
         if stall is not None and len(hist) >= 3 and hist[-1] > stall * hist[-3]:
+            break
+        if de_tol is not None and abs(st["energy"] - e_prev) < de_tol:
             break
     return it, st
 
@@ -740,24 +926,10 @@ def de_stop(trace, tol):
     return None, None
 
 
-def run_converge(args, dev):
-    """Full minimisations on the 4096-atom cell, both to RMS gradient 1e-8:
-    (a) plain: PM start, FP64 LNV;
-    (b) learned: network trained on converged 216-atom cells (thermal jitter 0.1-0.3 bohr),
-        guarded learned start, split-BF16 LNV to RMS gradient 1e-6 (or until it stops
-        improving: less than 10% over two steps), FP64 refinement.
-    Reported for three criteria: RMS gradient 1e-8; energy settled within 1e-6 Ha/atom of
-    the converged FP64 energy (FP64-product energies only); the intrinsic rule "FP64 energy
-    change per step below 1e-7 Ha/atom".  Times exclude pattern/task-list construction
-    (shared, cached) and the one-off training."""
+def cell_setup(ctx, dev):
+    """setup(cell, S pair blocks, H pair blocks, hsteps) on ctx: patterns P_S, P_L, S and H
+    on the device, and T ~ S^-1 from hsteps Hotelling steps."""
     import torch
-
-    from paper_2205_08941_gb300 import build as B
-    B.build()
-    from paper_2205_08941_gb300 import cq, learned
-    from paper_2205_08941_gb300 import inputs as I
-    torch.cuda.set_device(dev)
-    ctx = cq.Context(dev)
     t = lambda a, dt: torch.tensor(a, dtype=dt, device=f"cuda:{dev}")
     rS, rL = WORKLOAD["r_S"], WORKLOAD["r_L"]
 
@@ -772,32 +944,36 @@ def run_converge(args, dev):
         for _ in range(hsteps):
             ctx.hotelling_step(pS, S, pL, T)
         return pS, pL, S, H, T
+    return setup
 
-    def rel(x, ref):
-        return float(torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref))
 
-    def run(lnv, gtol, cap, trace=None, t0=0.0, fp64=True, stall=None):
-        return run_until(lnv, gtol, cap, trace, t0, fp64, stall)
+def train_guess(ctx, setup, train_cells, train_ncell, train_split):
+    """The learned start's network trained on converged L of small thermally displaced
+    cells; returns (guess, description of the training)."""
+    import torch
 
+    from paper_2205_08941_gb300 import cq, learned
+    from paper_2205_08941_gb300 import inputs as I
+    rS = WORKLOAD["r_S"]
     # training set: converged L of small thermally displaced cells (seeds 1000 + k, jitter
     # sigma ~ U[0.1, 0.3] bohr), solved in FP64 to RMS 1e-7 or, with --train-split, by
     # split-BF16 steps to RMS 1e-6 (the targets only have to make a good start)
     t0 = time.perf_counter()
     rng = np.random.default_rng(1000)
     samples, keep = [], []
-    train_prec = cq.CQ_SPLIT_BF16X3 if args.train_split else cq.CQ_FP64
-    for k in range(args.train_cells):
-        c = I.diamond_cell(args.train_ncell, a=WORKLOAD["a_bohr"],
+    train_prec = cq.CQ_SPLIT_BF16X3 if train_split else cq.CQ_FP64
+    for k in range(train_cells):
+        c = I.diamond_cell(train_ncell, a=WORKLOAD["a_bohr"],
                            sigma=float(rng.uniform(0.1, 0.3)), seed=1000 + k, norb=9)
         s_, h_ = I.overlap_hamiltonian(c, I.silicon_model(rS))
         pS, pL, S, H, T = setup(c, s_, h_)
         L = ctx.zeros(pL)
         ctx.pm_guess(pS, S, H, pL, T, pL, L, 2.0 * c.n_atoms)
         lnv = ctx.lnv(pS, S, H, pL, L, 4.0 * c.n_atoms, prec=train_prec)
-        if args.train_split:
-            run(lnv, 1e-6, 80, stall=0.9)
+        if train_split:
+            run_until(lnv, 1e-6, 80, stall=0.9)
         else:
-            run(lnv, 1e-7, 80)
+            run_until(lnv, 1e-7, 80)
         lnv.close()
         samples.append((pL, L))
         del pS, S, H, T
@@ -820,15 +996,108 @@ def run_converge(args, dev):
     mlp_tflops = 3.0 * fwd * n_samples * epochs / t_fit / 1e12
     peaks = measured_peaks()
     bf16 = (peaks or {}).get("bf16_tflops")
-    training = {"cells": args.train_cells, "atoms_per_cell": 8 * args.train_ncell ** 3,
-                "solver": "split-BF16 to RMS 1e-6" if args.train_split else "FP64 to RMS 1e-7",
+    training = {"cells": train_cells, "atoms_per_cell": 8 * train_ncell ** 3,
+                "solver": "split-BF16 to RMS 1e-6" if train_split else "FP64 to RMS 1e-7",
                 "samples": n_samples, "epochs": epochs, "seconds": t_train,
                 "data_seconds": t_data, "fit_seconds": t_fit,
                 "loss_first_last": [hist[0], hist[-1]],
                 "mlp_tflops": mlp_tflops,
                 "mlp_frac_of_bf16_peak": mlp_tflops / bf16 if bf16 else None}
     del samples, keep, desc, targ
+    return guess, training
 
+
+def converge_quick(args, dev):
+    """The target criterion on the 4096-atom cell in the default bench: seconds until the
+    energy stays within 1e-6 Ha/atom of the FP64 solution,
+    (a) plain: PM start, FP64 LNV until the energy changes by less than 1e-7 Ha/atom in one
+        step -- its final energy is the reference (6e-8 Ha/atom from the RMS-1e-8 solution);
+    (b) learned start (network trained on six 216-atom cells), split-BF16 LNV to its
+        rounding floor, then FP64 steps to the same stop rule.
+    Times exclude patterns, the Hotelling inverse and the one-off training."""
+    import torch
+
+    from paper_2205_08941_gb300 import cq, learned
+    ctx = cq.Context(dev)
+    setup = cell_setup(ctx, dev)
+    guess, training = train_guess(ctx, setup, 6, 3, False)
+    ctx.release_cache()
+    cell, Spb, Hpb = make_inputs(args.ncell)
+    n_at = cell.n_atoms
+    n_e = 4.0 * n_at
+    pS, pL, S, H, T = setup(cell, Spb, Hpb, args.hotelling_steps)
+    de = 1e-7 * n_at
+    L = ctx.zeros(pL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.pm_guess(pS, S, H, pL, T, pL, L, n_e / 2.0)
+    lnv = ctx.lnv(pS, S, H, pL, L, n_e)
+    tr_a = []
+    it_a, st_a = run_until(lnv, 1e-8, 120, tr_a, t0, de_tol=de)
+    torch.cuda.synchronize()
+    t_a = time.perf_counter() - t0
+    lnv.close()
+    L2 = ctx.zeros(pL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lnv, used, info = learned.guarded_start(ctx, guess, pS, S, H, pL, T, pL, L2, n_e,
+                                            prec=cq.CQ_SPLIT_BF16X3)
+    tr_b = []
+    it_b1, st_b1 = run_until(lnv, 1e-6, 120, tr_b, t0, fp64=False, stall=0.9)
+    lnv.set_precision(cq.CQ_FP64)
+    it_b2, st_b2 = run_until(lnv, 1e-8, 60, tr_b, t0, de_tol=de)
+    torch.cuda.synchronize()
+    t_b = time.perf_counter() - t0
+    lnv.close()
+    e_ref = st_a["energy"]
+    ta6, tb6 = settled(tr_a, e_ref, 1e-6 * n_at), settled(tr_b, e_ref, 1e-6 * n_at)
+    out = {"criterion": "energy within 1e-6 Ha/atom of the FP64 solution (plain FP64 LNV "
+                        "stopped when its energy changes by < 1e-7 Ha/atom per step)",
+           "plain_fp64_seconds": ta6, "learned_split_seconds": tb6,
+           "speedup": (ta6 / tb6) if ta6 and tb6 else None,
+           "plain_fp64": {"seconds_to_stop": t_a, "steps": it_a, "gnorm": st_a["gnorm"]},
+           "learned_split_then_fp64": {"seconds_to_stop": t_b, "split_steps": it_b1,
+                                       "fp64_steps": it_b2, "gnorm": st_b2["gnorm"],
+                                       "energy_diff_per_atom":
+                                           abs(st_b2["energy"] - e_ref) / n_at,
+                                       "learned_start_used": used,
+                                       "gnorm_start": info["gnorm_learned"],
+                                       "gnorm_pm_start": info["gnorm_pm"]},
+           "training": {k: training[k] for k in ("cells", "atoms_per_cell", "samples",
+                                                 "seconds", "loss_first_last")}}
+    guess.close()
+    ctx.close()
+    return out
+
+
+def run_converge(args, dev):
+    """Full minimisations on the 4096-atom cell, both to RMS gradient 1e-8:
+    (a) plain: PM start, FP64 LNV;
+    (b) learned: network trained on converged 216-atom cells (thermal jitter 0.1-0.3 bohr),
+        guarded learned start, split-BF16 LNV to RMS gradient 1e-6 (or until it stops
+        improving: less than 10% over two steps), FP64 refinement.
+    Reported for three criteria: RMS gradient 1e-8; energy settled within 1e-6 Ha/atom of
+    the converged FP64 energy (FP64-product energies only); the intrinsic rule "FP64 energy
+    change per step below 1e-7 Ha/atom".  Times exclude pattern/task-list construction
+    (shared, cached) and the one-off training."""
+    import torch
+
+    from paper_2205_08941_gb300 import build as B
+    B.build()
+    from paper_2205_08941_gb300 import cq, learned
+    from paper_2205_08941_gb300 import inputs as I
+    torch.cuda.set_device(dev)
+    ctx = cq.Context(dev)
+    setup = cell_setup(ctx, dev)
+
+    def rel(x, ref):
+        return float(torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref))
+
+    def run(lnv, gtol, cap, trace=None, t0=0.0, fp64=True, stall=None):
+        return run_until(lnv, gtol, cap, trace, t0, fp64, stall)
+
+    guess, training = train_guess(ctx, setup, args.train_cells, args.train_ncell,
+                                  args.train_split)
     cell, Spb, Hpb = make_inputs(args.ncell)
     n_e = 4.0 * cell.n_atoms
     pS, pL, S, H, T = setup(cell, Spb, Hpb, args.hotelling_steps)
@@ -1128,6 +1397,9 @@ def main():
         return
     if args.products:
         run_products(args, int(os.environ.get("LOCAL_RANK", 0)))
+        return
+    if args.batch_c4:
+        run_batch_c4(args, int(os.environ.get("LOCAL_RANK", 0)))
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -165,8 +165,9 @@ __device__ void bitmap_emit(const uint32_t *bits, int words, int64_t *count, int
     }
 }
 
-// Keys of each atom group (one CTA per group): the key (key_of: Morton rank or tail group)
-// of every column of a row of the group's atoms in pattern (rp, col).
+// Keys of each atom group (one CTA per group): the key (key_of: Morton rank or tail group;
+// atoms with a negative key are left out) of every column of a row of the group's atoms in
+// pattern (rp, col).
 template <bool FILL>
 __global__ void __launch_bounds__(256)
 k_group_keys(int gsize, const int32_t *atoms, const int64_t *rp, const int32_t *col,
@@ -182,7 +183,7 @@ k_group_keys(int gsize, const int32_t *atoms, const int64_t *rp, const int32_t *
         if (i < 0) continue;
         for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) {
             const int kk = key_of[col[e]];
-            atomicOr(&bits[kk >> 5], 1u << (kk & 31));
+            if (kk >= 0) atomicOr(&bits[kk >> 5], 1u << (kk & 31));
         }
     }
     __syncthreads();
@@ -223,7 +224,7 @@ k_tile_keys(int n_atoms, const int2 *tiles, int gi, int gj, const int32_t *g_ato
             const int bit = __ffs(v) - 1;
             v &= v - 1;
             const int kk = key_of[w * 32 + bit];
-            atomicOr(&bk[kk >> 5], 1u << (kk & 31));
+            if (kk >= 0) atomicOr(&bk[kk >> 5], 1u << (kk & 31));
         }
     }
     __syncthreads();
@@ -415,8 +416,13 @@ struct SplitArgs {
     double alpha, beta;
     int32_t *flag;
     long long test_wait_cycles;  // > 0: test mode, the MMA thread's first wait runs out
+    // mixed basis only (bsmm_mixed.cuh): tiles of this launch, row tables, C block offsets
+    const int2 *tiles;
+    const int32_t *g_row, *h_col;
+    const int64_t *c_off;
 };
 
+#include "bsmm_mixed.cuh"
 #include "bsmm_split_kernel.cuh"
 #include "bsmm_emu_kernel.cuh"
 
@@ -600,6 +606,11 @@ struct Groups {
     // K atoms by Morton rank, tail groups of tg consecutive ranks
     int tg = 0, n_tau = 0;
     DevBuf rank_atoms, rank_of, tg_atoms, tg_of;
+    // mixed basis (bsmm_mixed.cuh): groups of varying slot counts and their row tables,
+    // tail groups of varying atom counts and their position maps; rank_of is -1 for atoms
+    // without a main piece
+    bool mixed = false;
+    DevBuf g_row, h_col, tg_map;
 };
 
 // Piece entries of one operand kind (A or B, main or tail): per atom group, ascending keys
@@ -637,7 +648,8 @@ struct PiecePlan {
     std::shared_ptr<PieceSet> ps;
 };
 
-// Morton order of the atoms (positions quantised to 1024 per box edge).
+// Morton order of the atoms (positions quantised to 1024 per box edge), cell by cell for a
+// batch of cells.
 std::vector<int32_t> spatial_order(const Geometry &g)
 {
     auto spread = [](uint64_t v) {
@@ -648,15 +660,20 @@ std::vector<int32_t> spatial_order(const Geometry &g)
         x = (x | (x << 2)) & 0x9249249;
         return x;
     };
+    // a batch keeps its cells apart: the cell index leads the key, each cell in its own box
+    const bool batch = g.n_cells > 1 && (int)g.cell_start.size() == g.n_cells + 1;
     std::vector<uint64_t> key(g.n_atoms);
+    int cell = 0;
     for (int i = 0; i < g.n_atoms; ++i) {
+        while (batch && i >= g.cell_start[cell + 1]) ++cell;
+        const double *box = batch ? &g.boxes[3 * cell] : g.box;
         uint64_t c[3];
         for (int d = 0; d < 3; ++d) {
-            double f = g.pos_host[3 * i + d] / g.box[d];
+            double f = g.pos_host[3 * i + d] / box[d];
             f -= std::floor(f);
             c[d] = (uint64_t)std::min(1023.0, std::max(0.0, f * 1024.0));
         }
-        key[i] = spread(c[0]) | (spread(c[1]) << 1) | (spread(c[2]) << 2);
+        key[i] = ((uint64_t)cell << 30) | spread(c[0]) | (spread(c[1]) << 1) | (spread(c[2]) << 2);
     }
     std::vector<int32_t> order(g.n_atoms);
     std::iota(order.begin(), order.end(), 0);
@@ -675,6 +692,113 @@ cq_status upload(cq_ctx *ctx, DevBuf &buf, const void *host, size_t bytes)
     return st;
 }
 
+// Groups of a mixed basis (any orbital counts from 1 to 24; bsmm_mixed.cuh): in the
+// spatial order, M groups of consecutive atoms filling at most 128 rows and GI_MIX slots, N
+// groups 64 rows and GJ_MIX slots, tail groups of at most TG_MIX atoms whose tails fill at
+// most 16 K values; no group spans two cells of a batch.
+cq_status mixed_groups(cq_ctx *ctx, const Geometry &g, Groups &gr)
+{
+    const int n = g.n_atoms;
+    for (int i = 0; i < n; ++i)
+        if (g.nb_host[i] < 1 || g.nb_host[i] > 24)
+            return cq_fail(ctx, CQ_ERR_INVALID,
+                           "split-BF16 product: atoms need 1 to 24 orbitals");
+    const bool batch = g.n_cells > 1 && (int)g.cell_start.size() == g.n_cells + 1;
+    auto cell_of = [&](int atom) {
+        if (!batch) return 0;
+        return (int)(std::upper_bound(g.cell_start.begin(), g.cell_start.end(), atom) -
+                     g.cell_start.begin()) - 1;
+    };
+    auto tw = [&](int atom) { const int b = g.nb_host[atom]; return b >= 8 ? b - 8 : b; };
+    std::vector<int32_t> order = spatial_order(g);
+    gr.mixed = true;
+    gr.gi = GI_MIX;
+    gr.gj = GJ_MIX;
+    gr.tg = TG_MIX;
+    // greedy groups over the order: a new group when the rows (or tail values) would not fit,
+    // the slots are full or the cell changes
+    auto make = [&](int cap_rows, int cap_slots, std::vector<int32_t> &atoms,
+                    std::vector<int32_t> &rows, std::vector<int32_t> &of) {
+        of.assign(n, 0);
+        int ng = 0, used = 0, slots = 0, cell = -1;
+        std::vector<std::vector<int32_t>> grp;
+        for (int r = 0; r < n; ++r) {
+            const int a = order[r], b = g.nb_host[a], c = cell_of(a);
+            if (grp.empty() || used + b > cap_rows || slots == cap_slots || c != cell) {
+                grp.emplace_back();
+                ++ng;
+                used = slots = 0;
+                cell = c;
+            }
+            grp.back().push_back(a);
+            used += b;
+            ++slots;
+            of[a] = ng - 1;
+        }
+        atoms.assign((size_t)ng * cap_slots, -1);
+        rows.assign((size_t)ng * cap_rows, -1);
+        for (int q = 0; q < ng; ++q) {
+            int row = 0;
+            for (int sl = 0; sl < (int)grp[q].size(); ++sl) {
+                const int a = grp[q][sl], b = g.nb_host[a];
+                atoms[(size_t)q * cap_slots + sl] = a;
+                for (int o = 0; o < b; ++o)
+                    rows[(size_t)q * cap_rows + row++] = (sl << 16) | (b << 8) | o;
+            }
+        }
+        return ng;
+    };
+    std::vector<int32_t> ga, gro, gof, ha, hco, hof;
+    gr.n_g = make(MT, GI_MIX, ga, gro, gof);
+    gr.n_h = make(NT, GJ_MIX, ha, hco, hof);
+    // ranks (main pieces for atoms of 8 orbitals or more) and tail groups
+    std::vector<int32_t> rof(n), tof(n), ta, tmap;
+    {
+        int nt = 0, used = 0, cnt = 0, cell = -1;
+        std::vector<std::vector<int32_t>> grp;
+        for (int r = 0; r < n; ++r) {
+            const int a = order[r], w = tw(a), c = cell_of(a);
+            rof[a] = g.nb_host[a] >= 8 ? r : -1;
+            if (grp.empty() || used + w > 16 || cnt == TG_MIX || c != cell) {
+                grp.emplace_back();
+                ++nt;
+                used = cnt = 0;
+                cell = c;
+            }
+            grp.back().push_back(a);
+            used += w;
+            ++cnt;
+            tof[a] = nt - 1;
+        }
+        gr.n_tau = nt;
+        ta.assign((size_t)nt * TG_MIX, -1);
+        tmap.assign((size_t)nt * TG_MIX, -1);
+        for (int q = 0; q < nt; ++q) {
+            int pos = 0;
+            for (int u = 0; u < (int)grp[q].size(); ++u) {
+                const int a = grp[q][u], m0 = g.nb_host[a] >= 8 ? 8 : 0;
+                ta[(size_t)q * TG_MIX + u] = a;
+                for (int m = 0; m < tw(a); ++m)
+                    tmap[(size_t)q * TG_MIX + pos++] = (u << 8) | (m0 + m);
+            }
+        }
+    }
+    cq_status st;
+    if ((st = upload(ctx, gr.g_atoms, ga.data(), 4 * ga.size())) != CQ_OK ||
+        (st = upload(ctx, gr.h_atoms, ha.data(), 4 * ha.size())) != CQ_OK ||
+        (st = upload(ctx, gr.g_of, gof.data(), 4 * gof.size())) != CQ_OK ||
+        (st = upload(ctx, gr.h_of, hof.data(), 4 * hof.size())) != CQ_OK ||
+        (st = upload(ctx, gr.g_row, gro.data(), 4 * gro.size())) != CQ_OK ||
+        (st = upload(ctx, gr.h_col, hco.data(), 4 * hco.size())) != CQ_OK ||
+        (st = upload(ctx, gr.rank_atoms, order.data(), 4 * order.size())) != CQ_OK ||
+        (st = upload(ctx, gr.rank_of, rof.data(), 4 * rof.size())) != CQ_OK ||
+        (st = upload(ctx, gr.tg_atoms, ta.data(), 4 * ta.size())) != CQ_OK ||
+        (st = upload(ctx, gr.tg_of, tof.data(), 4 * tof.size())) != CQ_OK ||
+        (st = upload(ctx, gr.tg_map, tmap.data(), 4 * tmap.size())) != CQ_OK)
+        return st;
+    return cq_check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "groups");
+}
+
 cq_status get_groups(cq_ctx *ctx, const cq_pattern *p, Groups **out)
 {
     auto key = std::make_tuple(1, p->geo->id, (uint64_t)0, (uint64_t)0);
@@ -686,6 +810,13 @@ cq_status get_groups(cq_ctx *ctx, const cq_pattern *p, Groups **out)
     const Geometry &g = *p->geo;
     auto gr = std::make_shared<Groups>();
     const int nb = g.uniform_nb;
+    if (nb != 9 && nb != 4) {
+        cq_status st = mixed_groups(ctx, g, *gr);
+        if (st != CQ_OK) return st;
+        *out = gr.get();
+        ctx->aux[key] = gr;
+        return CQ_OK;
+    }
     gr->gi = MT / nb;
     gr->gj = NT / nb;
     gr->n_g = (g.n_atoms + gr->gi - 1) / gr->gi;
@@ -855,7 +986,7 @@ cq_status get_pieces(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
     cq_status st;
     // main pieces per (atom group, K atom) for 9-orbital atoms, tail pieces per (atom
     // group, tail group)
-    if (pC->geo->uniform_nb == 9 &&
+    if (pC->geo->uniform_nb != 4 &&
         ((st = piece_list<true>(ctx, gr->n_g, gr->gi, gr->g_atoms.as<int32_t>(), pA,
                                 gr->rank_of.as<int32_t>(), n_atoms, 1,
                                 gr->rank_atoms.as<int32_t>(), ps->am)) != CQ_OK ||
@@ -893,7 +1024,7 @@ cq_status get_piece_plan(cq_ctx *ctx, int kind, const cq_pattern *pA, const cq_p
     }
     cudaStream_t s = ctx->stream;
     auto pl = std::make_shared<PiecePlan>();
-    const bool mains = pC->geo->uniform_nb == 9, emu = kind == EMU_KIND;
+    const bool mains = pC->geo->uniform_nb != 4, emu = kind == EMU_KIND;
     const int64_t a_main_b = emu ? E_AMAIN : A_MAIN, a_tail_b = emu ? E_ATAIL : A_TAIL;
     const int n_atoms = pA->geo->n_atoms;
     cq_status st;
@@ -1040,33 +1171,59 @@ cq_status run_split(cq_ctx *ctx, const PiecePlan *pl, const Groups *gr, double a
                                                           SMEM), "split attribute")) != CQ_OK ||
             (st = cq_check_cuda(ctx, cudaFuncSetAttribute(k_bsmm_split<4>,
                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          SMEM), "split attribute")) != CQ_OK ||
+            (st = cq_check_cuda(ctx, cudaFuncSetAttribute(k_bsmm_split<0>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                           SMEM), "split attribute")) != CQ_OK)
             return st;
         attr_set[dev] = true;
     }
     auto blocks = [](int64_t n, int rows) { return (unsigned)((n * rows + 255) / 256); };
-    if (ps.bm.n() > 0) {
-        k_pack_main<NB, false><<<blocks(ps.bm.n(), NT), 256, 0, s>>>(
-            0, ps.bm.n(), ps.bm.index.as<int32_t>(), B, pB->uniform, (uint8_t *)vbm);
+    const int32_t *nbd = pA->geo->nb.as<int32_t>();
+    // main and tail pieces of entries [e0, e0 + n) of one side (LEFT: A)
+    auto pack = [&](bool left, bool main, int64_t e0, int64_t n, const PieceList &pl_,
+                    const double *X, const cq_pattern *pX, void *out) {
+        if (n <= 0) return;
+        const int rows = left ? MT : NT;
+        if constexpr (NB > 0) {
+            if (left && main)
+                k_pack_main<NB, true><<<blocks(n, rows), 256, 0, s>>>(
+                    e0, n, pl_.index.as<int32_t>(), X, pX->uniform, (uint8_t *)out);
+            else if (left)
+                k_pack_tail<NB, true><<<blocks(n, rows), 256, 0, s>>>(
+                    e0, n, pl_.index.as<int32_t>(), X, pX->uniform, (uint8_t *)out);
+            else if (main)
+                k_pack_main<NB, false><<<blocks(n, rows), 256, 0, s>>>(
+                    e0, n, pl_.index.as<int32_t>(), X, pX->uniform, (uint8_t *)out);
+            else
+                k_pack_tail<NB, false><<<blocks(n, rows), 256, 0, s>>>(
+                    e0, n, pl_.index.as<int32_t>(), X, pX->uniform, (uint8_t *)out);
+        } else {
+            const int32_t *tab = left ? gr->g_row.as<int32_t>() : gr->h_col.as<int32_t>();
+            const int64_t *off = pX->val_off.as<int64_t>();
+            if (main) {
+                auto k = left ? k_pack_main_mixed<true> : k_pack_main_mixed<false>;
+                k<<<blocks(n, rows), 256, 0, s>>>(e0, n, pl_.index.as<int32_t>(),
+                                                  pl_.group.as<int32_t>(), pl_.key.as<int32_t>(),
+                                                  gr->rank_atoms.as<int32_t>(), tab, nbd, off, X,
+                                                  (uint8_t *)out);
+            } else {
+                auto k = left ? k_pack_tail_mixed<true> : k_pack_tail_mixed<false>;
+                k<<<blocks(n, rows), 256, 0, s>>>(e0, n, pl_.index.as<int32_t>(),
+                                                  pl_.group.as<int32_t>(), pl_.key.as<int32_t>(),
+                                                  gr->tg_atoms.as<int32_t>(),
+                                                  gr->tg_map.as<int32_t>(), tab, nbd, off, X,
+                                                  (uint8_t *)out);
+            }
+        }
         cq_count_launch();
-    }
-    if (ps.bt.n() > 0) {
-        k_pack_tail<NB, false><<<blocks(ps.bt.n(), NT), 256, 0, s>>>(
-            0, ps.bt.n(), ps.bt.index.as<int32_t>(), B, pB->uniform, (uint8_t *)vbt);
-        cq_count_launch();
-    }
+    };
+    pack(false, true, 0, ps.bm.n(), ps.bm, B, pB, vbm);
+    pack(false, false, 0, ps.bt.n(), ps.bt, B, pB, vbt);
     for (size_t q = 0; q < pl->batches.size(); ++q) {
         const PieceBatch &b = pl->batches[q];
-        if (b.am1 > b.am0) {
-            k_pack_main<NB, true><<<blocks(b.am1 - b.am0, MT), 256, 0, s>>>(
-                b.am0, b.am1 - b.am0, ps.am.index.as<int32_t>(), A, pA->uniform, (uint8_t *)vam);
-            cq_count_launch();
-        }
-        if (b.at1 > b.at0) {
-            k_pack_tail<NB, true><<<blocks(b.at1 - b.at0, MT), 256, 0, s>>>(
-                b.at0, b.at1 - b.at0, ps.at.index.as<int32_t>(), A, pA->uniform, (uint8_t *)vat);
-            cq_count_launch();
-        }
+        pack(true, true, b.am0, b.am1 - b.am0, ps.am, A, pA, vam);
+        pack(true, false, b.at0, b.at1 - b.at0, ps.at, A, pA, vat);
         SplitArgs a;
         a.n_tiles = b.tile1 - b.tile0;
         a.kstart = pl->kstart.as<int64_t>() + b.tile0;
@@ -1086,6 +1243,10 @@ cq_status run_split(cq_ctx *ctx, const PiecePlan *pl, const Groups *gr, double a
         a.beta = beta;
         a.flag = ctx->flag.as<int32_t>();
         a.test_wait_cycles = ctx->test_wait_cycles;
+        a.tiles = pl->tiles.as<int2>() + b.tile0;
+        a.g_row = gr->g_row.as<int32_t>();
+        a.h_col = gr->h_col.as<int32_t>();
+        a.c_off = pC->val_off.as<int64_t>();
         // this launch's share of the product's useful and tensor-core flops
         const double share =
             pl->n_steps > 0 ? (double)pl->batch_steps[q] / (double)pl->n_steps : 0.0;
@@ -1245,10 +1406,7 @@ cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_
                         const double *A, const cq_pattern *pB, const double *B, double beta,
                         const cq_pattern *pC, double *C)
 {
-    const int nb = pC->geo->uniform_nb;
-    if (nb != 9 && nb != 4)
-        return cq_fail(ctx, CQ_ERR_INVALID,
-                       "split-BF16 product: needs a uniform basis of 4 or 9 orbitals per atom");
+    const int nb = pC->geo->uniform_nb;  // 4 and 9: uniform kernels; otherwise the mixed path
     if (pC->n_blocks == 0) return CQ_OK;
     Groups *gr;
     PiecePlan *pl;
@@ -1256,6 +1414,7 @@ cq_status cq_bsmm_split(cq_ctx *ctx, const TaskList *tl, double alpha, const cq_
     if (st != CQ_OK) return st;
     if ((st = get_piece_plan(ctx, SPLIT_KIND, pA, pB, pC, gr, &pl)) != CQ_OK) return st;
     if (pl->n_tiles == 0) return CQ_OK;
-    return nb == 9 ? run_split<9>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops)
-                   : run_split<4>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops);
+    if (nb == 9) return run_split<9>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops);
+    if (nb == 4) return run_split<4>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops);
+    return run_split<0>(ctx, pl, gr, alpha, pA, A, pB, B, beta, pC, C, tl->flops);
 }

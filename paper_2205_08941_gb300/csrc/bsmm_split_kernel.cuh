@@ -110,7 +110,7 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_
 // Epilogue of one drain thread: accumulator row arow = (atom of M slot si, orbital a),
 // columns 32*HALF .. +31 = (atom of N slot, orbital); cid[u] is the P_C block of slot pair
 // (si, J0 + u) or -1; each present block gets beta*C + alpha*(hi + lo).
-template <int NB> __host__ __device__ constexpr int epi_slots() { return 32 / NB + 2; }
+template <int NB> __host__ __device__ constexpr int epi_slots() { return 32 / (NB ? NB : 32) + 2; }
 
 template <int NB, int HALF>
 __device__ __forceinline__ void write_rows(const SplitArgs &p, const int32_t (&cid)[epi_slots<NB>()],
@@ -136,10 +136,11 @@ __device__ __forceinline__ void write_rows(const SplitArgs &p, const int32_t (&c
     }
 }
 
+// NB = 0: mixed basis (groups, rows and columns through the tables of bsmm_mixed.cuh)
 template <int NB>
 __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
 {
-    constexpr int GI = MT / NB, GJ = NT / NB;
+    constexpr int GI = NB ? MT / NB : GI_MIX, GJ = NB ? NT / NB : GJ_MIX;
     extern __shared__ __align__(1024) uint8_t smem[];
     Bars *bars = reinterpret_cast<Bars *>(smem + NS * STAGE);
     volatile int *abort_flag = &bars->abort_flag;
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
             // this row's C blocks, loaded now and used after the tile's last period
             constexpr int NJ = epi_slots<NB>();
             int32_t cid[NJ];
-            {
+            if constexpr (NB > 0) {
                 const int si = arow / NB, j0 = (half * 32) / NB;
 #pragma unroll
                 for (int u = 0; u < NJ; ++u)
@@ -370,10 +371,14 @@ __global__ void __launch_bounds__(ST, 1) k_bsmm_split(const SplitArgs p)
                 bar_arrive(smem_u32(&bars->acc_empty[b]));
             }
             if (!ok) break;
-            if (half == 0)
-                write_rows<NB, 0>(p, cid, arow, hi, lo);
-            else
-                write_rows<NB, 1>(p, cid, arow, hi, lo);
+            if constexpr (NB > 0) {
+                if (half == 0)
+                    write_rows<NB, 0>(p, cid, arow, hi, lo);
+                else
+                    write_rows<NB, 1>(p, cid, arow, hi, lo);
+            } else {
+                write_rows_mixed(p, tile, arow, half, hi, lo);
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -104,6 +104,32 @@ def test_batch_product_matches_cellwise_oracle(ctx, cells):
     assert t[0] == pytest.approx(ref, rel=1e-12)
 
 
+def test_batch_split_product_matches_cellwise_oracle(ctx, cells):
+    """Split-BF16 products on the batch (mixed 5/9/13-orbital species, cells of different
+    sizes) against the FP64 oracle cell by cell, to the split's error model: every block
+    within 1e-5 of sum_k ||A_ik|| ||B_kj||, RMS 1e-6 (tests/test_gpu_split.py)."""
+    cl = [c[0] for c in cells]
+    A_ = BatchOracle(ctx, cl, _ranges(cells, 2.0))
+    B_ = BatchOracle(ctx, cl, _ranges(cells, 0.0))
+    C_ = BatchOracle(ctx, cl, [r + r0 for r, r0 in zip(_ranges(cells, 2.0), _ranges(cells, 0.0))])
+    As = [O.scatter(po, I.random_blocks(c, r, 10 + k, symmetric=False))
+          for k, (c, po, r) in enumerate(zip(cl, A_.o, _ranges(cells, 2.0)))]
+    Bs = [O.scatter(po, I.random_blocks(c, r, 20 + k, symmetric=False))
+          for k, (c, po, r) in enumerate(zip(cl, B_.o, _ranges(cells, 0.0)))]
+    Cs = [O.scatter(po, I.random_blocks(c, r, 30 + k, symmetric=False))
+          for k, (c, po, r) in enumerate(zip(cl, C_.o, [x + y for x, y in zip(
+              _ranges(cells, 2.0), _ranges(cells, 0.0))]))]
+    Cg = C_.up(Cs)
+    ctx.bsmm(-0.7, A_.g, A_.up(As), B_.g, B_.up(Bs), 1.3, C_.g, Cg, prec=cq.CQ_SPLIT_BF16X3)
+    for k, got in enumerate(C_.down(Cg)):
+        ref = O.bsmm(-0.7, A_.o[k], As[k], B_.o[k], Bs[k], 1.3, C_.o[k], Cs[k].copy())
+        err, _ = block_errors(C_.o[k], got, ref)
+        rel = err / np.maximum(0.7 * natural_scale(A_.o[k], As[k], B_.o[k], Bs[k], C_.o[k]),
+                               1e-300)
+        assert rel.max() <= 1e-5, (k, rel.max())
+        assert np.sqrt(np.mean(rel ** 2)) <= 1e-6, k
+
+
 def _oracle_cell_lnv(cell, Spb, Hpb, rs, steps):
     rl = rs + 2.0
     pS, pL = O.Pattern.of_cell(cell, rs), O.Pattern.of_cell(cell, rl)
@@ -147,6 +173,35 @@ def test_batch_lnv_matches_cellwise_oracle(ctx, cells):
             assert reps[k]["energy"] == pytest.approx(ro["E"], abs=1e-10 * cl[k].n_atoms), (s, k)
             assert (reps[k]["restart"], reps[k]["fallback"], reps[k]["n_corr"]) == (
                 int(ro["restart"]), int(ro["fallback"]), ro["n_corr"]), (s, k)
+
+
+def test_batch_split_lnv_tracks_cellwise_oracle(ctx, cells):
+    """Batched LNV with split-BF16 products (mixed species) follows the FP64 oracle run cell
+    by cell: every cell's energy within 2e-5 Ha/atom of the oracle's at each of 8 steps (the
+    split's FP32-class product error), and its electron count within 1e-5 relative."""
+    cl = [c[0] for c in cells]
+    rs = [c[3] for c in cells]
+    pS = BatchOracle(ctx, cl, rs)
+    pL = BatchOracle(ctx, cl, [r + 2.0 for r in rs])
+    S_g = pS.up([O.scatter(po, c[1]) for po, c in zip(pS.o, cells)])
+    H_g = pS.up([O.scatter(po, c[2]) for po, c in zip(pS.o, cells)])
+    T_g = torch.zeros(pL.n_values, dtype=torch.float64, device="cuda:0")
+    ctx.hotelling_init(pS.g, S_g, pL.g, T_g)
+    for _ in range(10):
+        ctx.hotelling_step(pS.g, S_g, pL.g, T_g)
+    n_occ = [2.0 * c.n_atoms for c in cl]
+    L_g = torch.zeros(pL.n_values, dtype=torch.float64, device="cuda:0")
+    ctx.pm_guess_cells(pS.g, S_g, H_g, pL.g, T_g, pL.g, L_g, n_occ)
+    steps = 8
+    refs = [_oracle_cell_lnv(c[0], c[1], c[2], c[3], steps) for c in cells]
+    lg = ctx.lnv_cells(pS.g, S_g, H_g, pL.g, L_g, [2 * x for x in n_occ],
+                       prec=cq.CQ_SPLIT_BF16X3)
+    for s in range(steps):
+        reps = lg.step()
+        for k in range(len(cl)):
+            ro = refs[k][2][s]
+            assert abs(reps[k]["energy"] - ro["E"]) <= 2e-5 * cl[k].n_atoms, (s, k)
+            assert abs(reps[k]["n_elec"] - 2 * n_occ[k]) <= 1e-5 * 2 * n_occ[k], (s, k)
 
 
 def test_batch_equals_cells_solved_alone(ctx, cells):

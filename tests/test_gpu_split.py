@@ -144,14 +144,17 @@ def test_split_carries_out_of_range_values_as_nan(ctx):
         assert np.isfinite(got[~row1]).all(), bad
 
 
-def test_split_rejects_mixed_basis(ctx):
-    cell = I.diamond_cell(1, a=10.26, sigma=0.1, seed=3, norb=4)
-    cell.nb = np.array([4, 9] * 4, dtype=np.int32)
-    p = gpu_pattern(ctx, cell, 6.0)
-    A = ctx.zeros(p)
-    with pytest.raises(cq.CQError) as e:
-        ctx.bsmm(1.0, p, A, p, A.clone(), 0.0, p, ctx.zeros(p), prec=cq.CQ_SPLIT_BF16X3)
-    assert e.value.status == 1
+@pytest.mark.parametrize("species,ranges", [((5, 9, 13), (12.0, 10.0, 22.0)),
+                                            ((5, 9, 13), (22.0, 22.0, 12.0)),
+                                            ((4, 9), (12.0, 10.0, 12.0)),
+                                            ((13,), (12.0, 10.0, 22.0))])
+def test_split_parity_mixed_basis(ctx, species, ranges):
+    """Atoms of different orbital counts, and uniform counts other than 4 and 9, take the
+    mixed path (atom groups of varying slot counts, tails of 1 to 5 values packed into
+    16-value tail groups): same error model as the uniform products, on a 216-atom cell
+    whose groups and tail groups end ragged."""
+    cell = I.mixed_cell((3, 3, 3), 0.05, 0.1, 41, species=species)
+    _check_split(ctx, cell, ranges, alpha=-0.7, beta=1.3)
 
 
 def test_split_lnv_then_fp64_refinement(ctx):
