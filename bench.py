@@ -141,6 +141,9 @@ def parse():
                          "the cell with seeded random operands instead of the step benchmark: "
                          "X (L.S -> P_X), U (S.X -> P_U), R (U.X -> P_L); one untimed product, "
                          "then --steps timed ones (for kernel profiling)")
+    ap.add_argument("--converge-emu", action="store_true",
+                    help="the cell minimised to RMS gradient 1e-8 with FP64 products and with "
+                         "emulated-FP64 tensor-core products only, from the same start")
     ap.add_argument("--batch-c4", action="store_true",
                     help="the batched workload at its full shape (32 cells of 500-8000 atoms, "
                          "mixed 5/9/13-orbital species) in sub-batches, split-BF16 LNV steps")
@@ -1064,7 +1067,8 @@ def converge_quick(args, dev):
                                        "gnorm_start": info["gnorm_learned"],
                                        "gnorm_pm_start": info["gnorm_pm"]},
            "training": {k: training[k] for k in ("cells", "atoms_per_cell", "samples",
-                                                 "seconds", "loss_first_last")}}
+                                                 "seconds", "fit_seconds", "mlp_tflops",
+                                                 "mlp_frac_of_bf16_peak", "loss_first_last")}}
     guess.close()
     ctx.close()
     return out
@@ -1183,6 +1187,50 @@ def run_converge(args, dev):
             "training": training}
     print(json.dumps(line), flush=True)
     guess.close()
+    ctx.close()
+
+
+def run_converge_emu(args, dev):
+    """N1 end to end: the 4096-atom cell minimised to RMS gradient 1e-8 from the same PM start
+    (a) with FP64 products and (b) with emulated-FP64 products on the tensor cores only (no
+    FP64-pipe product anywhere in the solve).  Reports steps, seconds, the energies and
+    their difference, and the relative difference of the two density matrices."""
+    import torch
+
+    from paper_2205_08941_gb300 import build as B
+    B.build()
+    from paper_2205_08941_gb300 import cq
+    torch.cuda.set_device(dev)
+    ctx = cq.Context(dev)
+    setup = cell_setup(ctx, dev)
+    cell, Spb, Hpb = make_inputs(args.ncell)
+    n_at, n_e = cell.n_atoms, 4.0 * cell.n_atoms
+    pS, pL, S, H, T = setup(cell, Spb, Hpb, args.hotelling_steps)
+    L0 = ctx.zeros(pL)
+    ctx.pm_guess(pS, S, H, pL, T, pL, L0, n_e / 2.0)
+    del T
+    out = {"mode": "converge_emu", "workload": workload_name(n_at), "gradient_target_rms": 1e-8}
+    Ls = {}
+    for name, prec in (("fp64", cq.CQ_FP64), ("emu", cq.CQ_FP64_EMU)):
+        if prec != cq.CQ_FP64:
+            ctx.release_cache()  # the FP64 task lists: the emulated steps need none
+        L = L0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lnv = ctx.lnv(pS, S, H, pL, L, n_e, prec=prec)
+        tr = []
+        it, st = run_until(lnv, 1e-8, 80, tr, t0, fp64=True)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "steps": it, "energy": st["energy"],
+                     "gnorm": st["gnorm"], "n_elec": st["n_elec"],
+                     "gnorm_trace": [x[2] for x in tr]}
+        lnv.close()
+        Ls[name] = L
+    out["energy_diff_per_atom"] = abs(out["emu"]["energy"] - out["fp64"]["energy"]) / n_at
+    out["L_rel_diff"] = float(torch.linalg.vector_norm(Ls["emu"] - Ls["fp64"]) /
+                              torch.linalg.vector_norm(Ls["fp64"]))
+    out["speedup"] = out["fp64"]["seconds"] / out["emu"]["seconds"]
+    print(json.dumps(out), flush=True)
     ctx.close()
 
 
@@ -1400,6 +1448,9 @@ def main():
         return
     if args.batch_c4:
         run_batch_c4(args, int(os.environ.get("LOCAL_RANK", 0)))
+        return
+    if args.converge_emu:
+        run_converge_emu(args, int(os.environ.get("LOCAL_RANK", 0)))
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
