@@ -76,3 +76,47 @@ def test_run_until_needs_two_steps_before_judging_a_stall(n):
     g = [1e-3] + [1e-3] * 4
     it, _ = bench.run_until(ScriptedLnv(g), 1e-9, n, stall=0.9)
     assert it == n
+
+
+class EnergyLnv:
+    """Scripted energies with a gradient that never meets its target."""
+
+    def __init__(self, energies):
+        self.e = list(energies)
+        self.k = 0
+
+    def state(self):
+        return {"gnorm": 1.0, "energy": self.e[0]}
+
+    def step(self):
+        self.k += 1
+        return {"gnorm": 1.0, "energy": self.e[self.k]}
+
+
+def test_run_until_stops_when_the_energy_settles():
+    """The energy-change stop of the default converge leg: the first step whose energy
+    differs from the previous one by less than de_tol ends the run."""
+    lnv = EnergyLnv([-1.0, -2.0, -2.5, -2.6, -2.6000001, -2.7])
+    it, st = bench.run_until(lnv, 1e-8, 50, de_tol=1e-6)
+    assert it == 4 and st["energy"] == -2.6000001
+    it, _ = bench.run_until(EnergyLnv([-1.0, -2.0, -3.0, -4.0]), 1e-8, 3, de_tol=1e-6)
+    assert it == 3  # the step cap still holds
+
+
+def test_batched_recipe_cells():
+    """The 32 cells of the batched workload: seeded (the same cells every call), 500-8000
+    atoms each within lattice rounding, densities 0.03-0.06 atoms/A^3, r_L 12-16 bohr,
+    species 5/9/13 only."""
+    import numpy as np
+    a, b = bench.c4_cells(), bench.c4_cells()
+    assert len(a) == 32
+    for (ca, da, ra), (cb, db, rb) in zip(a, b):
+        assert ca.n_atoms == cb.n_atoms and np.array_equal(ca.nb, cb.nb)
+        assert np.allclose(ca.pos, cb.pos) and da == db and ra == rb
+        assert 500 <= ca.n_atoms <= 8000
+        assert 0.03 <= da <= 0.06 and 12.0 <= ra <= 16.0
+        assert set(np.unique(ca.nb)) <= {5, 9, 13}
+        # the lattice constant realises the drawn density
+        vol_a3 = np.prod(ca.box) / 1.8897261254578281 ** 3
+        assert ca.n_atoms / vol_a3 == pytest.approx(da, rel=1e-9)
+    assert 100000 < sum(c.n_atoms for c, _, _ in a) < 200000
