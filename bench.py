@@ -608,6 +608,14 @@ def split_oracle_check(dev, steps=3):
             "L_rel_err": rows[-1]["L_rel_err"]}
 
 
+def bench_config(cell, args, world):
+    """The workload of the bench line, the same for both arms."""
+    return dict(WORKLOAD, workload=workload_name(cell.n_atoms), ncell=args.ncell,
+                n_atoms=cell.n_atoms, n_electrons=4 * cell.n_atoms,
+                parallelism=f"replicas x{world}",
+                l2="inputs larger than L2 (U, Z 6.9 GB each)")
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -626,8 +634,7 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": dict(WORKLOAD, workload=workload_name(cell.n_atoms), ncell=args.ncell,
-                           n_atoms=cell.n_atoms, n_electrons=4 * cell.n_atoms, parallelism="cpu oracle"),
+            "config": bench_config(cell, args, world),
             "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": sample[0],
                              "kind": "oracle", "sample": sample[1]},
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
@@ -847,10 +854,8 @@ def run_cq(args, rank, world, local_rank):
             "s_per_lnv_step": ms / args.steps / 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if "fp64" in res else "bf16x3", "data": "synthetic",
-            "config": dict(WORKLOAD, workload=workload_name(cell.n_atoms), ncell=args.ncell,
-                           n_atoms=cell.n_atoms, n_electrons=4 * cell.n_atoms, parallelism=f"replicas x{world}",
-                           l2="inputs larger than L2 (U, Z 6.9 GB each)",
-                           hotelling_resid=resid[-1] if resid else None),
+            "config": bench_config(cell, args, world),
+            "hotelling_resid": resid[-1] if resid else None,
             "roofline": {"bound": "alu", "kernel": "k_bsmm_f64_uniform",
                          "achieved": achieved, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
                          "frac": (achieved / (peak_fp64 / 1e12)) if achieved else None,
