@@ -43,16 +43,21 @@ __device__ __forceinline__ void tc_stage(uint8_t *dst, int rows, const __nv_bflo
     for (int e = threadIdx.x; e < rows * groups; e += blockDim.x) {
         const int r = e / groups, g = e % groups;
         const int64_t k = k0 + 8 * g;
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
         if (r0 + r < rmax) {
             const __nv_bfloat16 *p = src + (int64_t)(r0 + r) * ld + k;
+            if (k + 8 <= kend && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+                w = __ldg(reinterpret_cast<const uint4 *>(p));  // eight values in one load
+            } else {
+                uint32_t u[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (k + q < kend)
-                    w[q >> 1] |= (uint32_t)__bfloat16_as_ushort(p[q]) << (16 * (q & 1));
+                for (int q = 0; q < 8; ++q)
+                    if (k + q < kend)
+                        u[q >> 1] |= (uint32_t)__bfloat16_as_ushort(p[q]) << (16 * (q & 1));
+                w = make_uint4(u[0], u[1], u[2], u[3]);
+            }
         }
-        *reinterpret_cast<uint4 *>(dst + (r >> 3) * TC_SBO + g * 128 + (r & 7) * 16) =
-            make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(dst + (r >> 3) * TC_SBO + g * 128 + (r & 7) * 16) = w;
     }
 }
 
