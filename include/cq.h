@@ -179,9 +179,11 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  * With beta == 0 the old C is not read.  The (i, k, j) task list of each (P_A, P_B, P_C)
  * triple is built on the device on first use and cached in the context.  C must not alias
  * A or B.  prec selects FP64 FMAs or the split-BF16 tensor-core product.  The split product
- * needs a uniform basis of 4 or 9 orbitals per atom (else CQ_ERR_INVALID); it packs both
- * operands into context-owned scratch before every call (up to about 2x the FP64 size of
- * the operands, the A side in batches of at most 12 GB), and its accuracy is FP32-class:
+ * takes uniform bases of 4 or 9 orbitals per atom on its uniform kernels and any other
+ * basis, mixed counts included (batches of cells too), on its mixed path; atoms of more
+ * than 24 orbitals give CQ_ERR_INVALID.  It packs both operands into context-owned scratch
+ * before every call (up to about 2x the FP64 size of the operands, the A side in batches of
+ * at most 12 GB), and its accuracy is FP32-class:
  * about 1e-7 relative per block, with FP32 partial sums drained to double-float.  Each value
  * is split to about 2^-27 relative for 2^-74 <= |x| < (2 - 2^-8) 2^127 (coarser below,
  * zero under 2^-126); larger values, infinities and NaNs give NaN in every C value they
@@ -202,10 +204,10 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  * method's matrices) that is the FP64 product bound
  * ||dC_ij|| <= 1e-12 max(||C_ij||, 1e-3 sum_k ||A_ik|| ||B_kj||); terms must lie between
  * about 2^-70 and 2^120 in magnitude (FP32's range holds the drained sums).
- * Same basis requirement as the split (4 or 9 orbitals); its packed operands take about
- * 2.7x the split's scratch (eight BF16 planes per value).  Infinities and NaNs poison their scale
- * group: they give NaN in every C value of the rows (of A) or columns (of B) that group
- * reaches.
+ * It needs a uniform basis of 4 or 9 orbitals per atom (else CQ_ERR_INVALID); its packed
+ * operands take about 2.7x the split's scratch (eight BF16 planes per value).  Infinities
+ * and NaNs poison their scale group: they give NaN in every C value of the rows (of A) or
+ * columns (of B) that group reaches.
  *
  * The tensor-core calls are asynchronous on the context stream; if a bounded wait inside the split kernel ran out (a
  * tensor-core completion not seen within about two seconds), the next synchronising call on
