@@ -561,9 +561,10 @@ void gemm_tc(cq_ctx *ctx, int M, int N, const __nv_bfloat16 *A, int64_t lda,
              int64_t c_stride_z)
 {
     const int64_t chunk = parts > 1 ? pad16((K + parts - 1) / parts) : K;
-    dim3 grid((unsigned)((M + TC_MT - 1) / TC_MT), 1, (unsigned)parts);
-    k_gemm_tc<<<grid, 128, TC_SMEM, ctx->stream>>>(M, N, (int)pad16(N), A, lda, Bt, ldb, C, ldc,
-                                                   0, K, c_stride_z, chunk, ctx->flag.as<int32_t>());
+    dim3 grid((unsigned)((M + TC_MT - 1) / TC_MT), (unsigned)((N + TC_NT - 1) / TC_NT),
+              (unsigned)parts);
+    k_gemm_tc<<<grid, 128, TC_SMEM, ctx->stream>>>(M, N, A, lda, Bt, ldb, C, ldc, 0, K,
+                                                   c_stride_z, chunk, ctx->flag.as<int32_t>());
     cq_count_launch();
 }
 
@@ -866,8 +867,11 @@ extern "C" cq_status cq_guess_train_step(cq_guess *g, const float *desc, const f
         const int64_t chunk = ((rows + parts - 1) / parts + 15) / 16 * 16;
         if (tc) {
             // tensor cores: dW = (H^T)(dZ^T)^T from BF16 transposes (rows padded to 16)
-            k_to_bf16_mat<<<blocks_for(rows * K), 256, 0, s>>>(rows, K, H[l - 1], Ht, 1, rp);
-            k_to_bf16_mat<<<blocks_for(rows * N), 256, 0, s>>>(rows, N, dZ, dZt, 1, rp);
+            const dim3 tb(32, 8);
+            k_to_bf16_t<<<dim3((K + 31) / 32, (unsigned)((rows + 31) / 32)), tb, 0, s>>>(
+                rows, K, H[l - 1], Ht, rp);
+            k_to_bf16_t<<<dim3((N + 31) / 32, (unsigned)((rows + 31) / 32)), tb, 0, s>>>(
+                rows, N, dZ, dZt, rp);
             cq_count_launch(2);
             gemm_tc(ctx, K, N, Ht, rp, dZt, rp, (float *)vpart, N, rows, parts, (int64_t)K * N);
         } else {

@@ -5,18 +5,19 @@
 //
 // C[m][n] = sum_{k in the CTA's K range} A[m][k] Bt[n][k] for m < M, n < N.  A (M x K) and
 // Bt (N x K) are row-major BF16 with leading dimensions lda, ldb (elements).  One CTA of 128
-// threads owns 128 rows of C and all N <= 256 columns (one MMA of N_pad = N rounded up to
-// 16); K runs in chunks of up to 256 staged in shared memory in the canonical no-swizzle
-// K-major layout (core matrices of 8 rows x 16 bytes, adjacent along K, 8-row groups 4 KB
-// apart).  Blocks along z take consecutive K ranges of k_chunk and write their own partial
+// threads owns 128 rows and 64 columns of C (blockIdx.y picks the column tile; one MMA of the
+// tile's width rounded up to 16); K runs in chunks of up to 256 staged in shared memory in
+// the canonical no-swizzle K-major layout (core matrices of 8 rows x 16 bytes, adjacent
+// along K, 8-row groups 4 KB apart); two CTAs fit one SM.  Blocks along z take consecutive K ranges of k_chunk and write their own partial
 // C (c_stride_z apart), summed later in a fixed order, so results are deterministic.
 //
 // The MMA completion wait is bounded (about two seconds); a CTA that gives up sets bit 16
 // of the flag word, frees its tensor memory and returns.
 constexpr int TC_MT = 128;      // rows of C per CTA
+constexpr int TC_NT = 64;       // columns of C per CTA
 constexpr int TC_KC = 256;      // K values per staged chunk
 constexpr int TC_SBO = (TC_KC / 8) * 128;
-constexpr int TC_SMEM = TC_MT * TC_KC * 2 + 256 * TC_KC * 2 + 64;
+constexpr int TC_SMEM = TC_MT * TC_KC * 2 + TC_NT * TC_KC * 2 + 64;
 constexpr long long TC_WAIT = 4000000000LL;
 
 __device__ __forceinline__ uint32_t tc_smem_u32(const void *p)
@@ -61,14 +62,14 @@ __device__ __forceinline__ void tc_stage(uint8_t *dst, int rows, const __nv_bflo
     }
 }
 
-__global__ void __launch_bounds__(128, 1)
-k_gemm_tc(int M, int N, int Npad, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *Bt,
+__global__ void __launch_bounds__(128, 2)
+k_gemm_tc(int M, int N, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *Bt,
           int64_t ldb, float *C, int64_t ldc, int64_t k0, int64_t k1, int64_t c_stride_z,
           int64_t k_chunk, int32_t *flag)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sa = smem, *sb = smem + TC_MT * TC_KC * 2;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sb + 256 * TC_KC * 2);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sb + TC_NT * TC_KC * 2);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     if (t == 0) {
@@ -78,14 +79,15 @@ k_gemm_tc(int M, int N, int Npad, const __nv_bfloat16 *A, int64_t lda, const __n
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          tc_smem_u32(tslot)),
-                     "r"(256));
+                     "r"(TC_NT));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    const int m0 = blockIdx.x * TC_MT;
+    const int m0 = blockIdx.x * TC_MT, n0 = blockIdx.y * TC_NT;
+    const int Npad = ((min(TC_NT, N - n0) + 15) / 16) * 16;  // this tile's MMA width
     const int64_t kb = k0 + (int64_t)blockIdx.z * k_chunk;
     const int64_t ke = min(k1, kb + k_chunk);
     // kind::f16: D = F32, A = B = BF16, both K-major, N = Npad, M = 128
@@ -97,7 +99,7 @@ k_gemm_tc(int M, int N, int Npad, const __nv_bfloat16 *A, int64_t lda, const __n
         const int kn = (int)min((int64_t)TC_KC, ke - kc);
         const int kn16 = (kn + 15) & ~15;
         tc_stage(sa, TC_MT, A, lda, m0, M, kc, ke, kn16);
-        tc_stage(sb, Npad, Bt, ldb, 0, N, kc, ke, kn16);
+        tc_stage(sb, Npad, Bt, ldb, n0, N, kc, ke, kn16);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (t == 0) {
@@ -160,7 +162,7 @@ k_gemm_tc(int M, int N, int Npad, const __nv_bfloat16 *A, int64_t lda, const __n
             if (row < M) {
 #pragma unroll
                 for (int x = 0; x < 16; ++x)
-                    if (cb + x < N) Cz[(int64_t)row * ldc + cb + x] = __uint_as_float(v[x]);
+                    if (n0 + cb + x < N) Cz[(int64_t)row * ldc + n0 + cb + x] = __uint_as_float(v[x]);
             }
         }
     } else if (t == 0) {
@@ -170,7 +172,7 @@ k_gemm_tc(int M, int N, int Npad, const __nv_bfloat16 *A, int64_t lda, const __n
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_NT));
     }
 }
 
@@ -188,4 +190,26 @@ __global__ void k_to_bf16_mat(int64_t rows, int cols, const float *src, __nv_bfl
         dst[(int64_t)c * ld_t + r] = v;
     else
         dst[e] = v;
+}
+
+// Transposed BF16 copy of a row-major FP32 matrix (rows x cols) into a cols x ld_t matrix,
+// through 32 x 32 shared-memory tiles so that reads and writes both run along rows (one CTA
+// of 32 x 8 threads per tile).
+__global__ void __launch_bounds__(256)
+k_to_bf16_t(int64_t rows, int cols, const float *src, __nv_bfloat16 *dst, int64_t ld_t)
+{
+    __shared__ float tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32;
+    const int c0 = blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int64_t r = r0 + y;
+        const int c = c0 + threadIdx.x;
+        tile[y][threadIdx.x] = (r < rows && c < cols) ? src[r * cols + c] : 0.f;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int c = c0 + y;
+        const int64_t r = r0 + threadIdx.x;
+        if (c < cols && r < rows) dst[(int64_t)c * ld_t + r] = __float2bfloat16(tile[threadIdx.x][y]);
+    }
 }
