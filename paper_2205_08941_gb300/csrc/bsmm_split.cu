@@ -34,9 +34,11 @@
 // issues the MMAs, eight warps drain the accumulators (bsmm_split_kernel.cuh).  A pieces
 // are packed in batches of M groups so that their scratch stays below A_PIECE_CAP bytes.
 //
-// The emulated-FP64 product (bsmm_emu_kernel.cuh) uses the same pieces with eight digit
-// planes instead of three BF16 terms; its K steps come grouped by tail group, which is its
-// scale group.
+// Bases other than uniform 4 or 9 orbitals (mixed counts, batches of cells) use the same
+// pieces and tile kernel with atom groups and tail groups of varying size described by
+// tables (bsmm_mixed.cuh).  The emulated-FP64 product (bsmm_emu_kernel.cuh) uses the same
+// pieces with eight digit planes instead of three BF16 terms; its K steps come grouped by
+// tail group, which is its scale group.
 #include <cuda_bf16.h>
 
 #include <algorithm>
