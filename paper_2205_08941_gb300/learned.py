@@ -44,6 +44,14 @@ def train(guess: cq.Guess, desc, targets, epochs=40, batch=8192, lr=2e-3, seed=0
     return hist
 
 
+def accept_learned(s_learned, s_pm, n_electrons, ratio=10.0) -> bool:
+    """The guard of the learned start: its RMS gradient (after the electron-number
+    corrections) at most `ratio` times the PM start's, and its electron count within 1 % of
+    n_electrons.  A NaN in either state fails the test."""
+    return bool(s_learned["gnorm"] <= ratio * s_pm["gnorm"]
+                and abs(s_learned["n_elec"] - n_electrons) <= 0.01 * n_electrons)
+
+
 def guarded_start(ctx: cq.Context, guess: cq.Guess, pS, S, H, pT, T, pL, L, n_electrons,
                   prec=cq.CQ_FP64, ratio=10.0):
     """LNV object started from the learned guess, unless its RMS gradient after the
@@ -61,8 +69,7 @@ def guarded_start(ctx: cq.Context, guess: cq.Guess, pS, S, H, pT, T, pL, L, n_el
     guess.apply(pL, L)
     lnv = ctx.lnv(pS, S, H, pL, L, n_electrons, prec)
     s_ml = lnv.state()
-    ok = (s_ml["gnorm"] <= ratio * s_pm["gnorm"]
-          and abs(s_ml["n_elec"] - n_electrons) <= 0.01 * n_electrons)
+    ok = accept_learned(s_ml, s_pm, n_electrons, ratio)
     info = {"gnorm_pm": s_pm["gnorm"], "gnorm_learned": s_ml["gnorm"],
             "E_pm": s_pm["energy"], "E_learned": s_ml["energy"]}
     if ok:
