@@ -118,8 +118,10 @@ cq_status cq_ctx_set_test_wait(cq_ctx *ctx, int64_t cycles);
 /* Lanes per C row the FP64 product of this triple uses, and whether the autotuner chose it. */
 cq_status cq_bsmm_config(cq_ctx *ctx, const cq_pattern *pA, const cq_pattern *pB,
                          const cq_pattern *pC, int32_t *lane_split_host, int32_t *tuned_host);
-/* Measure the device's FP64 FMA throughput (flop/s, an FMA counted as 2) with a register-
- * resident chain of independent FMAs filling every SM: the FP64 roofline denominator. */
+/* Measure the device's FP64 throughput (flop/s, an FMA counted as 2): the better of two
+ * register-resident probes filling every SM, a chain of independent FP64 FMAs and a chain of
+ * FP64 tensor-core MMAs (m8n8k4), each timed over five launches after a warm-up launch.  The
+ * FP64 roofline denominator.  Synchronises the context stream; takes about a second. */
 cq_status cq_peak_fp64(cq_ctx *ctx, double *flops_per_s_host);
 /* Number of CUDA kernels this library has launched in the process. */
 int64_t cq_kernel_launches(void);

@@ -120,3 +120,37 @@ def test_batched_recipe_cells():
         vol_a3 = np.prod(ca.box) / 1.8897261254578281 ** 3
         assert ca.n_atoms / vol_a3 == pytest.approx(da, rel=1e-9)
     assert 100000 < sum(c.n_atoms for c, _, _ in a) < 200000
+
+
+class _DoneProcess:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _sampled(lines):
+    s = bench.ClockSampler(0)
+    s.proc = _DoneProcess()
+    s.lines = lines
+    return s.stop()
+
+
+def test_clock_samples_give_the_median_and_every_active_reason():
+    idle = "Not Active"
+    rows = [f"0, {mhz}, 2070, 900.5, 0x0, {idle}, {idle}, {idle}, {cap}"
+            for mhz, cap in ((2070, idle), (1980, "Active"), (2070, idle), (2025, idle))]
+    rows.insert(1, "0, [N/A], 2070, 0, 0x0, , , , ")   # unreadable sample: skipped
+    rows.append("garbage")                               # short line: skipped
+    c = _sampled(rows)
+    assert c["samples"] == 4
+    assert c["sm_mhz"] == 2047.5 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    hot = f"0, 1500, 2070, 1400, 0x48, {idle}, Active, Active, {idle}"
+    assert _sampled([hot])["reasons"] == ["hw_thermal_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_sampler_without_nvidia_smi_says_so():
+    c = bench.ClockSampler(0).stop()
+    assert c["sm_mhz"] is None and c["reasons"] == ["nvidia-smi unavailable"]
