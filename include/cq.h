@@ -95,8 +95,8 @@ int64_t cq_ctx_mem_used(const cq_ctx *ctx);
  * context's stream (for roofline reporting; off by default). */
 cq_status cq_ctx_set_timing(cq_ctx *ctx, int on);
 /* Totals since the last call (then reset): product kernel launches, their summed device
- * time in ms, their useful flops (sum 2 n_i n_k n_j) and the tensor-core flops the split
- * products issued (0 for FP64 products).  Synchronises. */
+ * time in ms, their useful flops (sum 2 n_i n_k n_j) and the tensor-core flops the split and
+ * emulated products issued, padding included (0 for FP64 products).  Synchronises. */
 cq_status cq_ctx_kernel_stats(cq_ctx *ctx, int64_t *launches_host, double *ms_host,
                               double *flops_host, double *mma_flops_host);
 /* Autotuner (off by default): on the first FP64 product of each (P_A, P_B, P_C) triple, time
@@ -180,10 +180,10 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  * P_B (the sparse matrix multiplication of the paper's Background and Exascale sections).
  * With beta == 0 the old C is not read.  The (i, k, j) task list of each (P_A, P_B, P_C)
  * triple is built on the device on first use and cached in the context.  C must not alias
- * A or B.  prec selects FP64 FMAs or the split-BF16 tensor-core product.  The split product
- * takes uniform bases of 4 or 9 orbitals per atom on its uniform kernels and any other
- * basis, mixed counts included (batches of cells too), on its mixed path; atoms of more
- * than 24 orbitals give CQ_ERR_INVALID.  It packs both operands into context-owned scratch
+ * A or B.  prec selects FP64 FMAs or one of the tensor-core products.  The split product
+ * takes uniform bases of 4 or 9 orbitals per atom on its uniform kernels and every other
+ * basis a pattern can hold (1 to 16 orbitals per atom, mixed counts and batches of cells
+ * included) on its mixed path.  It packs both operands into context-owned scratch
  * before every call (up to about 2x the FP64 size of the operands, the A side in batches of
  * at most 12 GB), and its accuracy is FP32-class:
  * about 1e-7 relative per block, with FP32 partial sums drained to double-float.  Each value
@@ -211,10 +211,10 @@ cq_status cq_pattern_scatter(cq_ctx *ctx, const cq_pattern *p, int64_t n_pairs,
  * and NaNs poison their scale group: they give NaN in every C value of the rows (of A) or
  * columns (of B) that group reaches.
  *
- * The tensor-core calls are asynchronous on the context stream; if a bounded wait inside the split kernel ran out (a
- * tensor-core completion not seen within about two seconds), the next synchronising call on
- * the context (cq_ctx_sync, a trace, a dot, an LNV or Hotelling step) returns
- * CQ_ERR_TIMEOUT and C is incomplete.
+ * The tensor-core calls are asynchronous on the context stream; if a bounded wait inside a
+ * tensor-core kernel (split or emulated) ran out (a copy or MMA completion not seen within
+ * about two seconds), the next synchronising call on the context (cq_ctx_sync, a trace, a
+ * dot, an LNV or Hotelling step) returns CQ_ERR_TIMEOUT and C is incomplete.
  */
 cq_status cq_bsmm(cq_ctx *ctx, double alpha, const cq_pattern *pA, const double *A,
                   const cq_pattern *pB, const double *B, double beta,
