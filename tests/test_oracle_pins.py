@@ -492,3 +492,28 @@ def test_cg_inverse_beats_the_truncated_hotelling_fixed_point(si64):
     T, resid, _ = O.overlap_inverse_cg(pS, S, pT, T0, pV, 40)
     assert resid[-1] < r_hot                               # best T on the same pattern
     assert np.array_equal(O.gather(pT, T, pT, transpose=True), T)   # stays exactly symmetric
+
+
+# ------------------------------------------------------------------ degenerate cells
+
+def test_single_atom_cell_reduces_to_dense_algebra():
+    """One atom: every pattern, whatever its range (below, near or beyond the box), is the
+    self pair alone, and the product, trace and Hotelling iteration are those of one dense
+    9 x 9 block."""
+    pos, box, nb = np.array([[1.0, 2.0, 3.0]]), np.array([7.0, 7.0, 7.0]), np.array([9])
+    rng = np.random.default_rng(5)
+    for r in (0.5, 3.0, 20.0):
+        p = O.Pattern(pos, box, nb, r)
+        assert p.nnzb == 1 and list(p.col) == [0] and list(p.off) == [0, 81]
+    A, B, C = (rng.standard_normal((9, 9)) for _ in range(3))
+    got = O.bsmm(0.7, p, A.ravel(), p, B.ravel(), 1.3, p, C.ravel().copy())
+    np.testing.assert_allclose(got.reshape(9, 9), 0.7 * A @ B + 1.3 * C, rtol=0, atol=1e-13)
+    assert abs(O.trace_prod(p, A.ravel(), p, B.ravel()) - np.trace(A @ B)) < 1e-12
+    M = rng.standard_normal((9, 9))
+    S = np.eye(9) + 0.05 * (M @ M.T)
+    T = O.hotelling_init(p, S.ravel(), p)
+    for _ in range(40):
+        R0 = np.eye(9) - S @ T.reshape(9, 9)
+        T, _ = O.hotelling_step(p, S.ravel(), p, T, p)
+        np.testing.assert_allclose(np.eye(9) - S @ T.reshape(9, 9), R0 @ R0, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(T.reshape(9, 9), sl.inv(S), rtol=0, atol=1e-12)
