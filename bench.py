@@ -796,11 +796,16 @@ def run_cq(args, rank, world, local_rank):
         n_launch, kern_ms, kern_flops, mma_flops = r["stats"]
         peaks = measured_peaks()
         bf16 = (peaks or {}).get("bf16_tflops")
-        fp64_step_ms = res["fp64"]["ms"] / args.steps if "fp64" in res else None
+        # FP64 time of the same work over the emulated time: the two legs' useful-flop rates
+        # (the emulated leg times at most three steps from L0, the FP64 leg all K, and early
+        # steps run more products than late ones, so their times per step do not compare)
+        fp64_rate = (res["fp64"]["flops_all"] / res["fp64"]["ms"]
+                     if "fp64" in res and res["fp64"]["ms"] > 0 else None)
         emu = {"value": r["flops_all"] / (r["ms"] * 1e-3) / 1e9, "unit": "GFLOP/s",
                "dtype": "f64 emulated: 8 bf16 digit planes, exact level sums", "steps": k_emu,
                "s_per_lnv_step": r["ms"] / k_emu / 1e3,
-               "speedup_vs_fp64_step": (fp64_step_ms / (r["ms"] / k_emu)) if fp64_step_ms else None,
+               "speedup_vs_fp64_step": ((r["flops_all"] / r["ms"]) / fp64_rate
+                                        if fp64_rate and r["ms"] > 0 else None),
                "roofline": {"bound": "tensor", "kernel": "k_bsmm_emu",
                             "achieved": mma_flops / (kern_ms * 1e-3) / 1e12 if kern_ms else None,
                             "peak": bf16 or BF16_FALLBACK_TFLOPS, "unit": "TFLOP/s",
